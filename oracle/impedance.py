@@ -25,9 +25,12 @@ dkappa.  Then
 
 The Airy functions are scipy's exponentially scaled ones (a library
 primitive), so Bi does not overflow.  The sum is taken term by term while
-u_p < 1e3 and the rest is added in closed form from the large-u behaviour
-Ai'Bi' + u Ai Bi = 3/(16 pi) u^(-5/2) (1 + 105/32 u^(-3) + ...), whose
-p-sums are Hurwitz zeta values; Ai'^2 + u Ai^2 is exponentially small there.
+u_p < 60 and the rest is added in closed form from the large-u behaviour
+Ai'Bi' + u Ai Bi = 3/(16 pi) u^(-5/2) (1 + 105/32 u^(-3) + 75075/2048 u^(-6)
++ O(u^-9)) (relative error below 1e-13 for u >= 60), whose p-sums are Hurwitz
+zeta values; Ai'^2 + u Ai^2 < exp(-600) there.  The crossover is low because
+in double precision Ai'Bi' + u Ai Bi cancels two O(sqrt u) terms down to
+O(u^-5/2): scipy's terms lose about 1e-16 u^3 relative accuracy.
 """
 from __future__ import annotations
 
@@ -49,8 +52,8 @@ def zhat_free_space(kappa):
 
 def _pp_sum(a: float) -> complex:
     """sum_{p>=0} F(a (2p+1)^2) for one a = pi^2 2^(-2/3) (Pi/kappa)^(4/3)."""
-    # exact terms while u_p < 1e3 (possibly none); the remainder in closed form
-    pmax = max(0, int(math.ceil(0.5 * (math.sqrt(1.0e3 / a) - 1.0))))
+    # exact terms while u_p < 60 (possibly none); the remainder in closed form
+    pmax = max(0, int(math.ceil(0.5 * (math.sqrt(60.0 / a) - 1.0))))
     s = (2.0 * np.arange(pmax, dtype=np.float64) + 1.0)
     u = a * s * s
     eai, eaip, ebi, ebip = airye(u)
@@ -61,7 +64,9 @@ def _pp_sum(a: float) -> complex:
     # closed-form remainder p >= pmax: sum (2p+1)^-s = 2^-s zeta(s, pmax + 1/2)
     h5 = 2.0 ** -5 * zeta(5.0, pmax + 0.5)
     h11 = 2.0 ** -11 * zeta(11.0, pmax + 0.5)
-    tail = 3.0 / (16.0 * math.pi) * (a ** -2.5 * h5 + 105.0 / 32.0 * a ** -5.5 * h11)
+    h17 = 2.0 ** -17 * zeta(17.0, pmax + 0.5)
+    tail = 3.0 / (16.0 * math.pi) * (a ** -2.5 * h5 + 105.0 / 32.0 * a ** -5.5 * h11
+                                     + 75075.0 / 2048.0 * a ** -8.5 * h17)
     # add small terms first
     return complex(float(np.sum(re[::-1])), float(np.sum(im[::-1])) - tail)
 

@@ -118,8 +118,8 @@ def test_parallel_plates_limits():
 def test_parallel_plates_against_mpmath():
     """Independent evaluation with mpmath's Airy functions at 30 digits:
     term-by-term sum with its own remainder estimate from mpmath's Hurwitz
-    zeta.  Agreement to 1e-9: in double precision Ai'Bi' + u Ai Bi cancels two
-    O(sqrt u) terms down to O(u^-5/2), losing about four digits near u ~ 16."""
+    zeta.  Agreement to 1e-10: in double precision Ai'Bi' + u Ai Bi cancels two
+    O(sqrt u) terms down to O(u^-5/2), losing about 1e-16 u^3 relative."""
     mp.mp.dps = 30
 
     def zpp(kappa, Pi, P=400):
@@ -135,18 +135,19 @@ def test_parallel_plates_against_mpmath():
         s -= 1j * tail
         return complex(8 * mp.pi ** 2 * mp.cbrt(2) * Pi ** (mp.mpf(2) / 3) * kappa ** (-mp.mpf(1) / 3) * s)
 
-    for kap, Pi in [(1.0, 2.0), (5.0, 1.0), (40.0, 1.0), (12.0, 3.0)]:
+    for kap, Pi in [(1.0, 2.0), (5.0, 1.0), (40.0, 1.0), (12.0, 3.0), (0.2, 3.0)]:
         ref = zpp(kap, Pi)
         got = I.zhat_parallel_plates([kap], Pi)[0]
-        assert abs(got - ref) < 1e-9 * abs(ref), (kap, Pi, got, ref)
+        assert abs(got - ref) < 1e-10 * abs(ref), (kap, Pi, got, ref)
 
 
 def test_airy_large_argument_expansion():
     """The closed-form remainder uses Ai'Bi' + u Ai Bi = 3/(16 pi) u^{-5/2}
-    (1 + 105/32 u^{-3} + O(u^{-6})); check it against mpmath."""
+    (1 + 105/32 u^{-3} + 75075/2048 u^{-6} + O(u^{-9})); check it against mpmath."""
     mp.mp.dps = 40
-    for u in (30, 100, 1000):
+    for u in (30, 60, 100, 1000):
         u = mp.mpf(u)
         g = mp.airyai(u, 1) * mp.airybi(u, 1) + u * mp.airyai(u) * mp.airybi(u)
-        approx = 3 / (16 * mp.pi) * u ** -2.5 * (1 + mp.mpf(105) / 32 / u ** 3)
-        assert abs(g / approx - 1) < 50 / u ** 6
+        approx = 3 / (16 * mp.pi) * u ** -2.5 * (1 + mp.mpf(105) / 32 / u ** 3
+                                                  + mp.mpf(75075) / 2048 / u ** 6)
+        assert abs(g / approx - 1) < 1000 / u ** 9
