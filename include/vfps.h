@@ -1,0 +1,192 @@
+/*
+ * vfps.h -- C ABI of the B300 (sm_103a) Vlasov-Fokker-Planck phase-space stepper.
+ *
+ * The library advances the longitudinal phase-space density psi(q, p) of an
+ * electron bunch by time steps of the normalised Vlasov-Fokker-Planck
+ * equation (Schoenfeldt et al., "A Parallelized Vlasov-Fokker-Planck-Solver
+ * for Desktop PCs", Sec. II.A, Eq. VFP):
+ *
+ *     d psi/d theta + dH/dp d psi/dq - dH/dq d psi/dp = beta d/dp (p psi + d psi/dp),
+ *     H = (q^2 + p^2)/2 + collective term,  beta = 1/(f_s tau_d).
+ *
+ * One time step is (Sec. III.B: f = f_rot + f_kick + f_damp,diff):
+ *   1. bunch profile rho(q) = int psi dp and charge                 (Sec. II.B)
+ *   2. wake V(q) = int Z(k) rho~(k) e^{ikq} dk by FFT, and the CSR
+ *      power P = dkappa sum 2 Re(Z_k) |rho~_k|^2                     (Eq. wakepotential, Sec. IV.C)
+ *   3. RotationMap: semi-Lagrangian rotation by 2 pi/steps_per_period
+ *      with 2-D Lagrange interpolation on N_I x N_I nodes            (Sec. III.A-B)
+ *   4. WakeKickMap: 1-D interpolated shift of each q column along p
+ *      by dp = -S_csr V(q) * 2 pi/steps_per_period                   (Sec. III.B)
+ *   5. FokkerPlanckMap: explicit step of beta (psi + p psi' + psi'')
+ *      with the cubic derivative of Eq. cubic diff                   (Sec. III.B)
+ *   6. renormalisation of the charge to 1 (not in the paper; optional)
+ *
+ * Grid: q_i = -L + i*Delta, p_j = -L + j*Delta, Delta = 2L/(n-1), i, j = 0..n-1.
+ * psi is exchanged as n*n row-major doubles, index [i*n + j] = psi(q_i, p_j)
+ * (p contiguous; the paper's flattened index z = N_y x + y, Sec. III.B).
+ *
+ * Conventions of every call:
+ *  - returns 0 (VFPS_OK) or a negative VFPS_E* code; nothing else escapes;
+ *  - host pointers are read or written before the call returns and stay
+ *    owned by the caller; the library owns every device allocation;
+ *  - a handle is not thread-safe; work is queued on the handle's stream;
+ *  - calls that return data to the host synchronise that stream.
+ */
+#ifndef VFPS_H
+#define VFPS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VFPS_OK 0
+#define VFPS_EINVAL (-1)   /* bad argument or parameter combination          */
+#define VFPS_ENOMEM (-2)   /* device or host allocation failed               */
+#define VFPS_ECUDA (-3)    /* a CUDA runtime call failed                     */
+#define VFPS_ETIMEOUT (-4) /* a bounded device wait ran out                  */
+#define VFPS_ENAN (-5)     /* non-finite or non-positive charge detected     */
+#define VFPS_EBUSY (-6)    /* capacity exhausted (batch slots, HBM budget)   */
+
+#define VFPS_IMPEDANCE_NONE 0            /* no collective effect                      */
+#define VFPS_IMPEDANCE_FREE_SPACE 1      /* CSR in free space (Sec. II.B)             */
+#define VFPS_IMPEDANCE_PARALLEL_PLATES 2 /* CSR shielded by parallel plates (Sec. II.B) */
+#define VFPS_IMPEDANCE_TABLE 3           /* caller-supplied table                     */
+
+typedef struct vfps_params {
+    int32_t n;                /* grid points per axis, 8..2048                            */
+    int32_t steps_per_period; /* time steps per synchrotron period, >= 2                  */
+    int32_t interp_points;    /* N_I in {2, 3, 4}; 4 = cubic (default)                    */
+    int32_t clamp;            /* 1: clamped interpolation (Eq. clamping); default 0       */
+    int32_t fp_derivative;    /* 1: cubic derivative of Eq. cubic diff (default);
+                                 0: central difference                                    */
+    int32_t pad_factor;       /* zero padding: FFT length M = smallest power of two
+                                 >= pad_factor*n; 2..64, pad_factor*n <= 16384; default 2 */
+    int32_t precision;        /* 0: FP32 psi with FP64 sums (default); 1: FP64 throughout */
+    int32_t renormalize;      /* 1: rescale the charge to 1 after every step (default)    */
+    double half_width;        /* L: q, p in [-L, L]; default 6                            */
+    double beta;              /* 1/(f_s tau_d) >= 0 (Eq. VFP); default 0                  */
+} vfps_params;
+
+typedef struct vfps_handle vfps_handle;
+
+/* Fill *p with the defaults listed above (n = 256, steps_per_period = 1000). */
+void vfps_params_default(vfps_params* p);
+
+/* Create one simulation.
+ *   psi0:  host, n*n doubles, [q][p] row-major, non-negative; NULL = the unit
+ *          Gaussian exp(-(q^2+p^2)/2).  The library normalises it to charge
+ *          Delta^2 sum psi = 1 before upload.
+ *   cuda_stream: a cudaStream_t to queue work on, or NULL for a library-owned
+ *          stream.
+ * The impedance starts as VFPS_IMPEDANCE_NONE with S_csr = 0.
+ * Errors: EINVAL (parameters out of range, negative or all-zero psi0),
+ * ENOMEM, ECUDA. */
+int vfps_create(const vfps_params* params, const double* psi0, void* cuda_stream,
+                vfps_handle** out);
+
+/* Select the collective wake (Sec. II.B) and its strength.
+ *   model: VFPS_IMPEDANCE_*;  Pi: shielding parameter R^(1/2) sigma_z / g^(3/2)
+ *          of the parallel plates (model 2, > 0);
+ *   S_csr: normalised bunch current I_n R^(1/3) / sigma_z^(4/3) (any sign);
+ *   table_re_im: model 3 only, host, (M/2+1) interleaved (re, im) doubles of
+ *          the dimensionless impedance at kappa_k = 2 pi k/(M Delta).
+ * The impedance is tabulated on the host in FP64 once per call.  Recomputes
+ * the wake of the current state.  Errors: EINVAL, ECUDA. */
+int vfps_set_impedance(vfps_handle* h, int model, double Pi, double S_csr,
+                       const double* table_re_im);
+
+/* Advance by nsteps >= 0 time steps (asynchronous on the handle's stream).
+ * Errors: EINVAL, ECUDA, ENAN (reported by the next synchronising call). */
+int vfps_step(vfps_handle* h, int64_t nsteps);
+
+/* rho_out (host, n doubles): profile rho(q_i) = Delta sum_j psi_ij of the
+ * current state.  Synchronises.  Errors: EINVAL, ECUDA, ENAN. */
+int vfps_profile(vfps_handle* h, double* rho_out);
+
+/* Drain the CSR-power series: out[k] = P(psi_t) for the steps t taken since
+ * the last drain, oldest first (P of the state each step started from).
+ * Writes min(cap, pending) values and *n_written; values beyond cap stay
+ * queued.  Synchronises.  Errors: EINVAL, ECUDA, ENAN. */
+int vfps_csr_power(vfps_handle* h, double* out, int64_t cap, int64_t* n_written);
+
+/* Drain the series of the charge before renormalisation (one per step, same
+ * order and rules as vfps_csr_power): the per-step charge leakage. */
+int vfps_charge_series(vfps_handle* h, double* out, int64_t cap, int64_t* n_written);
+
+/* Copy the current psi (normalised, n*n doubles) to host memory.  Synchronises. */
+int vfps_get_state(vfps_handle* h, double* psi_out);
+
+/* Replace psi by host psi (n*n doubles, normalised to charge 1 by the
+ * library) and recompute its wake; the step counter is kept.  Errors: EINVAL. */
+int vfps_set_state(vfps_handle* h, const double* psi);
+
+/* Number of steps taken so far. */
+int vfps_steps_done(vfps_handle* h, int64_t* steps);
+
+/* Free every resource of the handle (NULL is accepted). */
+int vfps_destroy(vfps_handle* h);
+
+/* Static description of an error code. */
+const char* vfps_strerror(int code);
+
+/* Host-only (needs no device): the library's FP64 impedance table for a grid,
+ * the values vfps_set_impedance uploads.  out_re_im: (M/2+1) interleaved
+ * (re, im) doubles at kappa_k = 2 pi k/(M Delta), M = pad_factor*n.
+ * model: VFPS_IMPEDANCE_NONE, _FREE_SPACE or _PARALLEL_PLATES (Pi > 0).
+ * Errors: EINVAL. */
+int vfps_impedance_table(int model, int32_t n, double half_width, int32_t pad_factor,
+                         double Pi, double* out_re_im);
+
+/* ---------------------------------------------------------------------------
+ * Batch: many independent simulations of possibly different grid sizes that
+ * advance together, one fused kernel launch per grid-size class per step.
+ * Each slot behaves exactly like a handle with the same parameters: its
+ * results do not depend on the other slots (no floating-point atomics; fixed
+ * reduction order per slot).
+ * ------------------------------------------------------------------------- */
+typedef struct vfps_batch vfps_batch;
+
+/* max_slots: slot capacity (>= 1).  budget_bytes: device-memory cap for the
+ * slots' state (0 = no cap; admission also checks the free device memory).
+ * cuda_stream: as in vfps_create.  Errors: EINVAL, ENOMEM, ECUDA. */
+int vfps_batch_create(int32_t max_slots, int64_t budget_bytes, void* cuda_stream,
+                      vfps_batch** out);
+
+/* Add a simulation that will run nsteps steps.  Arguments as in vfps_create
+ * and vfps_set_impedance.  *slot receives its id.
+ * Errors: EINVAL, EBUSY (no free slot or over the memory budget), ENOMEM. */
+int vfps_batch_add(vfps_batch* b, const vfps_params* params, const double* psi0,
+                   int model, double Pi, double S_csr, const double* table_re_im,
+                   int64_t nsteps, int32_t* slot);
+
+/* Bytes of device memory a slot with these parameters needs (for admission). */
+int64_t vfps_batch_slot_bytes(const vfps_params* params);
+
+/* Advance every unfinished slot by up to chunk_steps steps (asynchronous).
+ * A slot stops exactly at its own nsteps. */
+int vfps_batch_run(vfps_batch* b, int64_t chunk_steps);
+
+/* Synchronise; list the finished slots not yet removed.  Writes up to cap ids. */
+int vfps_batch_poll(vfps_batch* b, int32_t* done_slots, int32_t cap, int32_t* n_done);
+
+/* Results of one slot (finished or not): psi_out (n*n, may be NULL), rho_out
+ * (n, may be NULL), CSR-power series (all steps so far, up to power_cap
+ * values, may be NULL), *n_power, *steps_done.  Synchronises. */
+int vfps_batch_take(vfps_batch* b, int32_t slot, double* psi_out, double* rho_out,
+                    double* power_out, int64_t power_cap, int64_t* n_power,
+                    int64_t* steps_done);
+
+/* Free a slot (its memory returns to the budget). */
+int vfps_batch_remove(vfps_batch* b, int32_t slot);
+
+/* Number of active slots and device bytes they hold. */
+int vfps_batch_usage(vfps_batch* b, int32_t* active, int64_t* bytes);
+
+int vfps_batch_destroy(vfps_batch* b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VFPS_H */

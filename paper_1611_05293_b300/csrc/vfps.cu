@@ -1,0 +1,1073 @@
+// vfps.cu -- runtime and C ABI of the B300 VFP phase-space stepper.
+//
+// Host side: parameter checks, one device allocation per simulation carved
+// into its buffers, the impedance table (FP64 on the host, once per
+// vfps_set_impedance), launch groups (instances that share precision,
+// interpolation order and CTA width advance in one launch per step), CUDA
+// graphs of GRAPH_STEPS launches for long runs, the CSR-power ring drain,
+// and the batch/slot bookkeeping.  The per-step work runs in the kernels of
+// vfps_kernels.cuh; nothing of the step is computed on the host.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "../../include/vfps.h"
+#include "vfps_kernels.cuh"
+
+namespace vfps {
+void impedance_table(int model, int M, double delta, double Pi, std::vector<std::complex<double>>& z);
+}
+
+using namespace vfps;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kRingDefault = 1 << 15;  // CSR-power ring entries per simulation
+constexpr int kGraphSteps = 32;        // launches per captured CUDA graph
+constexpr size_t kAlign = 256;
+
+#define CU(call)                                   \
+    do {                                           \
+        cudaError_t e_ = (call);                   \
+        if (e_ != cudaSuccess) return VFPS_ECUDA;  \
+    } while (0)
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+
+int ilog2(int v)
+{
+    int r = 0;
+    while ((1 << r) < v) ++r;
+    return r;
+}
+
+int check_params(const vfps_params* p)
+{
+    if (!p) return VFPS_EINVAL;
+    if (p->n < 8 || p->n > 2048) return VFPS_EINVAL;
+    if (p->steps_per_period < 2) return VFPS_EINVAL;
+    if (p->interp_points < 2 || p->interp_points > 4) return VFPS_EINVAL;
+    if (p->clamp != 0 && p->clamp != 1) return VFPS_EINVAL;
+    if (p->fp_derivative != 0 && p->fp_derivative != 1) return VFPS_EINVAL;
+    if (p->precision != 0 && p->precision != 1) return VFPS_EINVAL;
+    if (p->renormalize != 0 && p->renormalize != 1) return VFPS_EINVAL;
+    if (!(p->half_width > 0.0) || !std::isfinite(p->half_width)) return VFPS_EINVAL;
+    if (!(p->beta >= 0.0) || !std::isfinite(p->beta)) return VFPS_EINVAL;
+    if (p->pad_factor < 2 || p->pad_factor > 64) return VFPS_EINVAL;
+    if ((long long)p->pad_factor * p->n > 16384) return VFPS_EINVAL;
+    return VFPS_OK;
+}
+
+// FFT length: the smallest power of two >= pad_factor * n.
+int fft_length(const vfps_params* p)
+{
+    int m = 1;
+    while (m < p->pad_factor * p->n) m <<= 1;
+    return m;
+}
+
+// Column halo of the staged slab: 2 nodes of the cubic stencil plus the
+// largest source displacement c (|cos phi - 1| + |sin phi|), plus one.
+int halo_for(const vfps_params* p)
+{
+    double phi = 2.0 * kPi / p->steps_per_period;
+    double c = 0.5 * (p->n - 1);
+    double cm1 = std::fabs(-2.0 * std::sin(0.5 * phi) * std::sin(0.5 * phi));
+    double dmax = c * (cm1 + std::fabs(std::sin(phi)));
+    return 3 + (int)std::ceil(dmax);
+}
+
+int elem_size(const vfps_params* p) { return p->precision ? 8 : 4; }
+
+size_t step_smem(const vfps_params* p, int W)
+{
+    size_t es = elem_size(p);
+    int h = halo_for(p);
+    size_t slab = (size_t)(W + 2 * h) * (p->n + 4) * es;
+    size_t cols = (size_t)W * p->n * es;
+    int M = fft_length(p);
+    size_t fin = (size_t)(M + M / 2) * 2 * es + (size_t)W * 32 * 8;
+    return align_up(std::max(slab + cols, fin), 16);
+}
+
+int g_max_smem = -1;
+
+int device_smem_limit()
+{
+    if (g_max_smem < 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
+        g_max_smem = v;
+    }
+    return g_max_smem;
+}
+
+// CTA width: the widest of 8, 4, 2 columns whose shared memory fits.
+int choose_width(const vfps_params* p)
+{
+    int lim = device_smem_limit();
+    for (int W : {8, 4, 2})
+        if ((long long)step_smem(p, W) <= lim) return W;
+    return 0;
+}
+
+// ----------------------------------------------------------------------------
+// One simulation: a single device allocation holding every buffer.
+struct Instance {
+    vfps_params p{};
+    int n = 0, ld = 0, M = 0, W = 0, ntiles = 0, ring = kRingDefault;
+    double delta = 0, phi = 0;
+    int model = 0;
+    double Pi = 0, S = 0;
+    void* dmem = nullptr;
+    size_t dbytes = 0;
+    void* psi[2] = {nullptr, nullptr};
+    void* zhat = nullptr;
+    void* tw = nullptr;
+    double* colsum = nullptr;
+    double* rho = nullptr;
+    void* kick = nullptr;
+    double* pring = nullptr;
+    double* qring = nullptr;
+    DevState* st = nullptr;
+    unsigned char hdesc[sizeof(Desc<double>)];  // host copy of the descriptor
+    void* ddesc = nullptr;                       // device copy
+    int2* dtiles = nullptr;                      // this instance alone: its tiles
+    // host bookkeeping
+    long long steps_queued = 0;   // steps launched so far
+    long long drained = 0;        // ring entries already moved to the host
+    long long target = -1;        // batch slots: total steps wanted
+    int parity0 = 0;
+    std::vector<double> pw, qw;   // drained series
+    size_t pw_taken = 0, qw_taken = 0;
+};
+
+size_t instance_bytes(const vfps_params* p, int ring, size_t* offs)
+{
+    size_t es = elem_size(p);
+    int n = p->n;
+    int ld = (int)align_up(n, 16 / es);
+    int M = fft_length(p);
+    size_t o = 0;
+    auto take = [&](int slot, size_t b) {
+        o = align_up(o, kAlign);
+        offs[slot] = o;
+        o += b;
+    };
+    take(0, (size_t)n * ld * es);        // psi0
+    take(1, (size_t)n * ld * es);        // psi1
+    take(2, (size_t)(M / 2 + 1) * 2 * es);  // zhat
+    take(3, (size_t)(M / 2) * 2 * es);   // twiddles
+    take(4, (size_t)n * 8);              // colsum
+    take(5, (size_t)n * 8);              // rho
+    take(6, (size_t)n * es);             // kick
+    take(7, (size_t)ring * 8);           // pring
+    take(8, (size_t)ring * 8);           // qring
+    take(9, sizeof(DevState));           // state
+    take(10, sizeof(Desc<double>));      // descriptor
+    take(11, sizeof(int2) * (size_t)((n + 1) / 2 + 1));  // tiles (W >= 2)
+    return align_up(o, kAlign);
+}
+
+template <typename T>
+void fill_desc(Instance& I)
+{
+    Desc<T> d{};
+    d.psi[0] = (T*)I.psi[0];
+    d.psi[1] = (T*)I.psi[1];
+    d.zhat = (const typename C2<T>::type*)I.zhat;
+    d.tw = (const typename C2<T>::type*)I.tw;
+    d.colsum = I.colsum;
+    d.rho = I.rho;
+    d.kick = (T*)I.kick;
+    d.pring = I.pring;
+    d.qring = I.qring;
+    d.st = I.st;
+    d.n = I.n;
+    d.ld = I.ld;
+    d.M = I.M;
+    d.logM = ilog2(I.M);
+    d.ring_mask = I.ring - 1;
+    d.renorm = I.p.renormalize;
+    d.clamp = I.p.clamp;
+    d.h = halo_for(&I.p);
+    d.ntiles = I.ntiles;
+    double phi = I.phi;
+    double s2 = std::sin(0.5 * phi);
+    d.cm1 = T(-2.0 * s2 * s2);
+    d.sn = T(std::sin(phi));
+    d.c = T(0.5 * (I.n - 1));
+    // FP increment g_k(y) psi_b(y+k), k = -1..2:  h (a_k + b_k p_y), p_y = -L + y Delta
+    double hh = I.p.beta / I.p.steps_per_period, D = I.delta, L = I.p.half_width;
+    double a[4], b[4];
+    a[0] = 1.0 / (D * D); a[1] = 1.0 - 2.0 / (D * D); a[2] = 1.0 / (D * D); a[3] = 0.0;
+    if (I.p.fp_derivative) {  // Eq. cubic diff: (-2 f_{-1} - 3 f_0 + 6 f_1 - f_2) / (6 Delta)
+        b[0] = -2.0 / (6.0 * D); b[1] = -3.0 / (6.0 * D); b[2] = 6.0 / (6.0 * D); b[3] = -1.0 / (6.0 * D);
+    } else {                  // central: (f_1 - f_{-1}) / (2 Delta)
+        b[0] = -1.0 / (2.0 * D); b[1] = 0.0; b[2] = 1.0 / (2.0 * D); b[3] = 0.0;
+    }
+    for (int k = 0; k < 4; ++k) {
+        d.ga[k] = T(hh * (a[k] - b[k] * L));
+        d.gb[k] = T(hh * b[k] * D);
+    }
+    d.delta = I.delta;
+    d.dkappa = 2.0 * kPi / (I.M * I.delta);
+    d.kick_per_v = -I.S * I.phi / I.delta;
+    std::memcpy(I.hdesc, &d, sizeof(d));
+}
+
+int upload_desc(Instance& I, cudaStream_t s)
+{
+    if (I.p.precision) fill_desc<double>(I);
+    else fill_desc<float>(I);
+    CU(cudaMemcpyAsync(I.ddesc, I.hdesc, sizeof(Desc<double>), cudaMemcpyHostToDevice, s));
+    return VFPS_OK;
+}
+
+void destroy_instance(Instance* I)
+{
+    if (!I) return;
+    if (I->dmem) cudaFree(I->dmem);
+    delete I;
+}
+
+// psi (host, n*n doubles) -> normalised device psi[parity]; the pending scale is 1.
+int upload_psi(Instance& I, const double* psi, cudaStream_t s)
+{
+    int n = I.n;
+    double d2 = I.delta * I.delta;
+    std::vector<double> g;
+    const double* src = psi;
+    if (!psi) {
+        g.resize((size_t)n * n);
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                double q = -I.p.half_width + i * I.delta, pp = -I.p.half_width + j * I.delta;
+                g[(size_t)i * n + j] = std::exp(-0.5 * (q * q + pp * pp));
+            }
+        src = g.data();
+    }
+    double sum = 0.0;
+    for (size_t i = 0; i < (size_t)n * n; ++i) {
+        double v = src[i];
+        if (!std::isfinite(v) || v < 0.0) return VFPS_EINVAL;
+        sum += v;
+    }
+    if (!(sum > 0.0)) return VFPS_EINVAL;
+    double inv = 1.0 / (d2 * sum);
+    size_t es = elem_size(&I.p);
+    std::vector<unsigned char> buf((size_t)n * I.ld * es, 0);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            double v = src[(size_t)i * n + j] * inv;
+            if (es == 8) reinterpret_cast<double*>(buf.data())[(size_t)i * I.ld + j] = v;
+            else reinterpret_cast<float*>(buf.data())[(size_t)i * I.ld + j] = (float)v;
+        }
+    DevState st{};
+    CU(cudaMemcpyAsync(&st, I.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    CU(cudaMemcpyAsync(I.psi[st.parity], buf.data(), buf.size(), cudaMemcpyHostToDevice, s));
+    st.scale = 1.0;
+    st.ticket = 0;
+    CU(cudaMemcpyAsync(I.st, &st, sizeof(DevState), cudaMemcpyHostToDevice, s));
+    CU(cudaStreamSynchronize(s));
+    return VFPS_OK;
+}
+
+int upload_impedance(Instance& I, int model, double Pi, double S, const double* table, cudaStream_t s)
+{
+    int K = I.M / 2;
+    std::vector<std::complex<double>> z;
+    if (model == VFPS_IMPEDANCE_TABLE) {
+        if (!table) return VFPS_EINVAL;
+        z.resize(K + 1);
+        for (int k = 0; k <= K; ++k) {
+            z[k] = {table[2 * k], table[2 * k + 1]};
+            if (!std::isfinite(z[k].real()) || !std::isfinite(z[k].imag())) return VFPS_EINVAL;
+        }
+    } else if (model >= 0 && model <= 2) {
+        if (model == 2 && !(Pi > 0.0)) return VFPS_EINVAL;
+        vfps::impedance_table(model, I.M, I.delta, Pi, z);
+    } else {
+        return VFPS_EINVAL;
+    }
+    if (!std::isfinite(S)) return VFPS_EINVAL;
+    size_t es = elem_size(&I.p);
+    std::vector<unsigned char> buf((size_t)(K + 1) * 2 * es);
+    for (int k = 0; k <= K; ++k) {
+        if (es == 8) {
+            reinterpret_cast<double*>(buf.data())[2 * k] = z[k].real();
+            reinterpret_cast<double*>(buf.data())[2 * k + 1] = z[k].imag();
+        } else {
+            reinterpret_cast<float*>(buf.data())[2 * k] = (float)z[k].real();
+            reinterpret_cast<float*>(buf.data())[2 * k + 1] = (float)z[k].imag();
+        }
+    }
+    CU(cudaMemcpyAsync(I.zhat, buf.data(), buf.size(), cudaMemcpyHostToDevice, s));
+    CU(cudaStreamSynchronize(s));
+    I.model = model;
+    I.Pi = Pi;
+    I.S = S;
+    return VFPS_OK;
+}
+
+int create_instance(const vfps_params* p, const double* psi0, int ring, cudaStream_t s, Instance** out)
+{
+    int rc = check_params(p);
+    if (rc) return rc;
+    int W = choose_width(p);
+    if (W == 0) return VFPS_EINVAL;  // grid too large for the staged slab at this step angle
+    std::unique_ptr<Instance, void (*)(Instance*)> I(new (std::nothrow) Instance(), destroy_instance);
+    if (!I) return VFPS_ENOMEM;
+    I->p = *p;
+    I->n = p->n;
+    I->ld = (int)align_up(p->n, 16 / elem_size(p));
+    I->M = fft_length(p);
+    I->W = W;
+    I->ntiles = (p->n + W - 1) / W;
+    I->ring = ring;
+    I->delta = 2.0 * p->half_width / (p->n - 1);
+    I->phi = 2.0 * kPi / p->steps_per_period;
+    size_t offs[12];
+    I->dbytes = instance_bytes(p, ring, offs);
+    if (cudaMalloc(&I->dmem, I->dbytes) != cudaSuccess) {
+        cudaGetLastError();
+        return VFPS_ENOMEM;
+    }
+    unsigned char* b = (unsigned char*)I->dmem;
+    if (cudaMemsetAsync(b, 0, I->dbytes, s) != cudaSuccess) return VFPS_ECUDA;
+    I->psi[0] = b + offs[0];
+    I->psi[1] = b + offs[1];
+    I->zhat = b + offs[2];
+    I->tw = b + offs[3];
+    I->colsum = (double*)(b + offs[4]);
+    I->rho = (double*)(b + offs[5]);
+    I->kick = b + offs[6];
+    I->pring = (double*)(b + offs[7]);
+    I->qring = (double*)(b + offs[8]);
+    I->st = (DevState*)(b + offs[9]);
+    I->ddesc = b + offs[10];
+    I->dtiles = (int2*)(b + offs[11]);
+    // twiddles exp(-2 pi i k/M), FP64 on the host
+    {
+        int K = I->M / 2;
+        size_t es = elem_size(p);
+        std::vector<unsigned char> buf((size_t)K * 2 * es);
+        for (int k = 0; k < K; ++k) {
+            double ang = -2.0 * kPi * k / I->M;
+            double c = std::cos(ang), s = std::sin(ang);
+            if (es == 8) {
+                reinterpret_cast<double*>(buf.data())[2 * k] = c;
+                reinterpret_cast<double*>(buf.data())[2 * k + 1] = s;
+            } else {
+                reinterpret_cast<float*>(buf.data())[2 * k] = (float)c;
+                reinterpret_cast<float*>(buf.data())[2 * k + 1] = (float)s;
+            }
+        }
+        if (cudaMemcpyAsync(I->tw, buf.data(), buf.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return VFPS_ECUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return VFPS_ECUDA;
+    }
+    {
+        std::vector<int2> t(I->ntiles);
+        for (int i = 0; i < I->ntiles; ++i) t[i] = make_int2(0, i * W);
+        if (cudaMemcpyAsync(I->dtiles, t.data(), sizeof(int2) * t.size(), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess)
+            return VFPS_ECUDA;
+        DevState st{};
+        st.scale = 1.0;
+        if (cudaMemcpyAsync(I->st, &st, sizeof(st), cudaMemcpyHostToDevice, s) != cudaSuccess) return VFPS_ECUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return VFPS_ECUDA;
+    }
+    rc = upload_impedance(*I, 0, 0.0, 0.0, nullptr, s);
+    if (rc) return rc;
+    rc = upload_psi(*I, psi0, s);
+    if (rc) return rc;
+    *out = I.release();
+    return VFPS_OK;
+}
+
+// ----------------------------------------------------------------------------
+// Launch groups: instances with equal (precision, N_I, W) advance in one
+// launch per step.  The tile table lists (instance, first column) per CTA.
+struct Group {
+    int prec = 0, ni = 4, W = 8;
+    size_t smem = 0;
+    int ntiles = 0;
+    void* ddescs = nullptr;  // array of Desc<T>
+    int2* dtiles = nullptr;
+    size_t cap_desc = 0, cap_tiles = 0;
+};
+
+template <typename T, int NI, int W>
+int launch_step_t(const Group& g, cudaStream_t s)
+{
+    auto k = step_kernel<T, NI, W>;
+    k<<<g.ntiles, W * 32, g.smem, s>>>((const Desc<T>*)g.ddescs, g.dtiles);
+    CU(cudaGetLastError());
+    return VFPS_OK;
+}
+
+template <typename T, int W>
+int launch_project_t(const Group& g, cudaStream_t s)
+{
+    auto k = project_kernel<T, W>;
+    k<<<g.ntiles, W * 32, g.smem, s>>>((const Desc<T>*)g.ddescs, g.dtiles);
+    CU(cudaGetLastError());
+    return VFPS_OK;
+}
+
+template <typename T, int NI>
+int launch_step_w(const Group& g, cudaStream_t s)
+{
+    switch (g.W) {
+    case 8: return launch_step_t<T, NI, 8>(g, s);
+    case 4: return launch_step_t<T, NI, 4>(g, s);
+    case 2: return launch_step_t<T, NI, 2>(g, s);
+    }
+    return VFPS_EINVAL;
+}
+
+template <typename T>
+int launch_step_ni(const Group& g, cudaStream_t s)
+{
+    switch (g.ni) {
+    case 4: return launch_step_w<T, 4>(g, s);
+    case 3: return launch_step_w<T, 3>(g, s);
+    case 2: return launch_step_w<T, 2>(g, s);
+    }
+    return VFPS_EINVAL;
+}
+
+int launch_step(const Group& g, cudaStream_t s)
+{
+    if (g.ntiles == 0) return VFPS_OK;
+    return g.prec ? launch_step_ni<double>(g, s) : launch_step_ni<float>(g, s);
+}
+
+int launch_project(const Group& g, cudaStream_t s)
+{
+    if (g.ntiles == 0) return VFPS_OK;
+    if (g.prec) {
+        switch (g.W) {
+        case 8: return launch_project_t<double, 8>(g, s);
+        case 4: return launch_project_t<double, 4>(g, s);
+        case 2: return launch_project_t<double, 2>(g, s);
+        }
+    } else {
+        switch (g.W) {
+        case 8: return launch_project_t<float, 8>(g, s);
+        case 4: return launch_project_t<float, 4>(g, s);
+        case 2: return launch_project_t<float, 2>(g, s);
+        }
+    }
+    return VFPS_EINVAL;
+}
+
+// Allow every kernel variant the device's full opt-in shared memory (once,
+// before any launch or stream capture).
+template <typename T, int NI, int W>
+cudaError_t set_smem_attr(int lim)
+{
+    cudaError_t e = cudaFuncSetAttribute(step_kernel<T, NI, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    if (e != cudaSuccess) return e;
+    if (NI == 4) e = cudaFuncSetAttribute(project_kernel<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    return e;
+}
+
+template <typename T>
+cudaError_t set_smem_attr_all(int lim)
+{
+    cudaError_t e = cudaSuccess;
+    cudaError_t r;
+#define VFPS_SET(NI, W) if ((r = set_smem_attr<T, NI, W>(lim)) != cudaSuccess) e = r;
+    VFPS_SET(4, 8) VFPS_SET(4, 4) VFPS_SET(4, 2)
+    VFPS_SET(3, 8) VFPS_SET(3, 4) VFPS_SET(3, 2)
+    VFPS_SET(2, 8) VFPS_SET(2, 4) VFPS_SET(2, 2)
+#undef VFPS_SET
+    return e;
+}
+
+int g_kernels_ready = 0;
+
+int init_kernels()
+{
+    if (g_kernels_ready) return VFPS_OK;
+    int lim = device_smem_limit();
+    if (lim <= 0) return VFPS_ECUDA;
+    if (set_smem_attr_all<float>(lim) != cudaSuccess) return VFPS_ECUDA;
+    if (set_smem_attr_all<double>(lim) != cudaSuccess) return VFPS_ECUDA;
+    g_kernels_ready = 1;
+    return VFPS_OK;
+}
+
+// A group made of one instance, using its own descriptor and tile table.
+Group single_group(const Instance& I)
+{
+    Group g;
+    g.prec = I.p.precision;
+    g.ni = I.p.interp_points;
+    g.W = I.W;
+    g.smem = step_smem(&I.p, I.W);
+    g.ntiles = I.ntiles;
+    g.ddescs = I.ddesc;
+    g.dtiles = I.dtiles;
+    return g;
+}
+
+// Recompute the wake, profile and power of the current state of one instance.
+int prologue(Instance& I, cudaStream_t s)
+{
+    int rc = upload_desc(I, s);
+    if (rc) return rc;
+    Group g = single_group(I);
+    return launch_project(g, s);
+}
+
+int read_status(Instance& I, cudaStream_t s)
+{
+    DevState st;
+    CU(cudaMemcpyAsync(&st, I.st, sizeof(st), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    return st.status;
+}
+
+// Move ring entries [drained, steps_queued) to the host series (synchronises).
+int drain(Instance& I, cudaStream_t s)
+{
+    long long lo = I.drained, hi = I.steps_queued;
+    if (hi <= lo) return VFPS_OK;
+    std::vector<double> pr(I.ring), qr(I.ring);
+    CU(cudaMemcpyAsync(pr.data(), I.pring, sizeof(double) * I.ring, cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(qr.data(), I.qring, sizeof(double) * I.ring, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    for (long long t = lo; t < hi; ++t) {
+        I.pw.push_back(pr[t & (I.ring - 1)]);
+        I.qw.push_back(qr[t & (I.ring - 1)]);
+    }
+    I.drained = hi;
+    return VFPS_OK;
+}
+
+int copy_state(Instance& I, cudaStream_t s, double* psi_out)
+{
+    int n = I.n;
+    DevState st;
+    CU(cudaMemcpyAsync(&st, I.st, sizeof(st), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    size_t es = elem_size(&I.p);
+    std::vector<unsigned char> buf((size_t)n * I.ld * es);
+    CU(cudaMemcpyAsync(buf.data(), I.psi[st.parity], buf.size(), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            double v = es == 8 ? reinterpret_cast<double*>(buf.data())[(size_t)i * I.ld + j]
+                               : (double)reinterpret_cast<float*>(buf.data())[(size_t)i * I.ld + j];
+            psi_out[(size_t)i * n + j] = v * st.scale;
+        }
+    return st.status;
+}
+
+}  // namespace
+
+// ============================================================================
+// Single-simulation handle
+struct vfps_handle {
+    Instance* I = nullptr;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaGraphExec_t graph = nullptr;
+};
+
+extern "C" {
+
+void vfps_params_default(vfps_params* p)
+{
+    if (!p) return;
+    p->n = 256;
+    p->steps_per_period = 1000;
+    p->interp_points = 4;
+    p->clamp = 0;
+    p->fp_derivative = 1;
+    p->pad_factor = 2;
+    p->precision = 0;
+    p->renormalize = 1;
+    p->half_width = 6.0;
+    p->beta = 0.0;
+}
+
+const char* vfps_strerror(int code)
+{
+    switch (code) {
+    case VFPS_OK: return "ok";
+    case VFPS_EINVAL: return "invalid argument";
+    case VFPS_ENOMEM: return "out of memory";
+    case VFPS_ECUDA: return "CUDA runtime error";
+    case VFPS_ETIMEOUT: return "bounded device wait timed out";
+    case VFPS_ENAN: return "non-finite or non-positive charge";
+    case VFPS_EBUSY: return "capacity exhausted";
+    }
+    return "unknown error";
+}
+
+int vfps_create(const vfps_params* params, const double* psi0, void* cuda_stream, vfps_handle** out)
+{
+    if (!out) return VFPS_EINVAL;
+    *out = nullptr;
+    std::unique_ptr<vfps_handle> h(new (std::nothrow) vfps_handle());
+    if (!h) return VFPS_ENOMEM;
+    if (cuda_stream) {
+        h->stream = (cudaStream_t)cuda_stream;
+    } else {
+        CU(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+        h->own_stream = true;
+    }
+    Instance* I = nullptr;
+    int rc = init_kernels();
+    if (rc == VFPS_OK) rc = create_instance(params, psi0, kRingDefault, h->stream, &I);
+    if (rc) {
+        if (h->own_stream) cudaStreamDestroy(h->stream);
+        return rc;
+    }
+    h->I = I;
+    rc = prologue(*I, h->stream);
+    if (rc) {
+        destroy_instance(I);
+        if (h->own_stream) cudaStreamDestroy(h->stream);
+        return rc;
+    }
+    *out = h.release();
+    return VFPS_OK;
+}
+
+int vfps_set_impedance(vfps_handle* h, int model, double Pi, double S_csr, const double* table)
+{
+    if (!h) return VFPS_EINVAL;
+    CU(cudaStreamSynchronize(h->stream));
+    int rc = upload_impedance(*h->I, model, Pi, S_csr, table, h->stream);
+    if (rc) return rc;
+    return prologue(*h->I, h->stream);
+}
+
+static int ensure_graph(vfps_handle* h)
+{
+    if (h->graph) return VFPS_OK;
+    Group g = single_group(*h->I);
+    cudaGraph_t graph;
+    CU(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = VFPS_OK;
+    for (int i = 0; i < kGraphSteps && rc == VFPS_OK; ++i) rc = launch_step(g, h->stream);
+    cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+    if (rc) return rc;
+    if (e != cudaSuccess) return VFPS_ECUDA;
+    e = cudaGraphInstantiate(&h->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        h->graph = nullptr;
+        return VFPS_ECUDA;
+    }
+    return VFPS_OK;
+}
+
+int vfps_step(vfps_handle* h, int64_t nsteps)
+{
+    if (!h || nsteps < 0) return VFPS_EINVAL;
+    Instance& I = *h->I;
+    Group g = single_group(I);
+    int rc;
+    while (nsteps > 0) {
+        // keep the ring from overwriting undrained entries
+        long long room = (long long)I.ring - 1 - (I.steps_queued - I.drained);
+        if (room <= 0) {
+            rc = drain(I, h->stream);
+            if (rc) return rc;
+            continue;
+        }
+        long long chunk = std::min<long long>(nsteps, room);
+        if (chunk >= kGraphSteps) {
+            rc = ensure_graph(h);
+            if (rc) return rc;
+            long long ng = chunk / kGraphSteps;
+            for (long long i = 0; i < ng; ++i) CU(cudaGraphLaunch(h->graph, h->stream));
+            chunk = ng * kGraphSteps;
+        } else {
+            for (long long i = 0; i < chunk; ++i) {
+                rc = launch_step(g, h->stream);
+                if (rc) return rc;
+            }
+        }
+        I.steps_queued += chunk;
+        nsteps -= chunk;
+    }
+    return VFPS_OK;
+}
+
+int vfps_profile(vfps_handle* h, double* rho_out)
+{
+    if (!h || !rho_out) return VFPS_EINVAL;
+    CU(cudaMemcpyAsync(rho_out, h->I->rho, sizeof(double) * h->I->n, cudaMemcpyDeviceToHost, h->stream));
+    return read_status(*h->I, h->stream);
+}
+
+static int drain_series(vfps_handle* h, bool power, double* out, int64_t cap, int64_t* n_written)
+{
+    if (!h || !n_written || cap < 0 || (cap > 0 && !out)) return VFPS_EINVAL;
+    Instance& I = *h->I;
+    int rc = drain(I, h->stream);
+    if (rc) return rc;
+    std::vector<double>& v = power ? I.pw : I.qw;
+    size_t& taken = power ? I.pw_taken : I.qw_taken;
+    int64_t k = std::min<int64_t>(cap, (int64_t)(v.size() - taken));
+    for (int64_t i = 0; i < k; ++i) out[i] = v[taken + i];
+    taken += k;
+    *n_written = k;
+    if (I.pw_taken == I.pw.size() && I.qw_taken == I.qw.size()) {
+        I.pw.clear();
+        I.qw.clear();
+        I.pw_taken = I.qw_taken = 0;
+    }
+    return read_status(I, h->stream);
+}
+
+int vfps_csr_power(vfps_handle* h, double* out, int64_t cap, int64_t* n_written)
+{
+    return drain_series(h, true, out, cap, n_written);
+}
+
+int vfps_charge_series(vfps_handle* h, double* out, int64_t cap, int64_t* n_written)
+{
+    return drain_series(h, false, out, cap, n_written);
+}
+
+int vfps_get_state(vfps_handle* h, double* psi_out)
+{
+    if (!h || !psi_out) return VFPS_EINVAL;
+    return copy_state(*h->I, h->stream, psi_out);
+}
+
+int vfps_set_state(vfps_handle* h, const double* psi)
+{
+    if (!h || !psi) return VFPS_EINVAL;
+    CU(cudaStreamSynchronize(h->stream));
+    int rc = upload_psi(*h->I, psi, h->stream);
+    if (rc) return rc;
+    return prologue(*h->I, h->stream);
+}
+
+int vfps_steps_done(vfps_handle* h, int64_t* steps)
+{
+    if (!h || !steps) return VFPS_EINVAL;
+    *steps = h->I->steps_queued;
+    return VFPS_OK;
+}
+
+int vfps_destroy(vfps_handle* h)
+{
+    if (!h) return VFPS_OK;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    destroy_instance(h->I);
+    if (h->own_stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return VFPS_OK;
+}
+
+// Host-only helper (no device needed): the library's own impedance table for
+// a grid, as interleaved (re, im) pairs, M/2+1 of them.
+int vfps_impedance_table(int model, int32_t n, double half_width, int32_t pad_factor, double Pi,
+                         double* out_re_im)
+{
+    if (!out_re_im || n < 8 || n > 2048 || pad_factor < 2 || pad_factor > 64 || !(half_width > 0.0))
+        return VFPS_EINVAL;
+    if ((long long)pad_factor * n > 16384) return VFPS_EINVAL;
+    if (model < 0 || model > 2 || (model == 2 && !(Pi > 0.0))) return VFPS_EINVAL;
+    vfps_params tmp{};
+    tmp.n = n;
+    tmp.pad_factor = pad_factor;
+    int M = fft_length(&tmp);
+    std::vector<std::complex<double>> z;
+    vfps::impedance_table(model, M, 2.0 * half_width / (n - 1), Pi, z);
+    for (size_t k = 0; k < z.size(); ++k) {
+        out_re_im[2 * k] = z[k].real();
+        out_re_im[2 * k + 1] = z[k].imag();
+    }
+    return VFPS_OK;
+}
+
+}  // extern "C"
+
+// ============================================================================
+// Batch of slots (vfps_batch_*)
+struct vfps_batch {
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int max_slots = 0;
+    long long budget = 0;
+    long long used = 0;
+    std::vector<Instance*> slots;  // nullptr = free
+    std::vector<Group> groups;
+    bool dirty = true;             // active set changed: rebuild groups
+    void* gmem = nullptr;          // descriptor and tile arrays of the groups
+    size_t gbytes = 0;
+};
+
+namespace {
+
+long long remaining(const Instance* I) { return I->target - I->steps_queued; }
+
+void free_groups(vfps_batch* b)
+{
+    if (b->gmem) cudaFree(b->gmem);
+    b->gmem = nullptr;
+    b->gbytes = 0;
+    b->groups.clear();
+}
+
+// Group the slots that still have steps to run by (precision, N_I, W).
+int rebuild_groups(vfps_batch* b)
+{
+    CU(cudaStreamSynchronize(b->stream));
+    free_groups(b);
+    std::map<std::tuple<int, int, int>, std::vector<Instance*>> cls;
+    for (Instance* I : b->slots)
+        if (I && remaining(I) > 0) cls[{I->p.precision, I->p.interp_points, I->W}].push_back(I);
+    if (cls.empty()) {
+        b->dirty = false;
+        return VFPS_OK;
+    }
+    size_t total = 0;
+    std::vector<std::pair<size_t, size_t>> offs;
+    for (auto& kv : cls) {
+        size_t nt = 0;
+        for (Instance* I : kv.second) nt += I->ntiles;
+        size_t od = align_up(total, kAlign);
+        size_t ot = align_up(od + kv.second.size() * sizeof(Desc<double>), kAlign);
+        total = ot + nt * sizeof(int2);
+        offs.push_back({od, ot});
+    }
+    if (cudaMalloc(&b->gmem, total) != cudaSuccess) {
+        cudaGetLastError();
+        return VFPS_ENOMEM;
+    }
+    b->gbytes = total;
+    std::vector<unsigned char> host(total, 0);
+    size_t gi = 0;
+    for (auto& kv : cls) {
+        Group g;
+        std::tie(g.prec, g.ni, g.W) = kv.first;
+        g.ddescs = (unsigned char*)b->gmem + offs[gi].first;
+        g.dtiles = (int2*)((unsigned char*)b->gmem + offs[gi].second);
+        int2* ht = (int2*)(host.data() + offs[gi].second);
+        int nt = 0;
+        for (size_t k = 0; k < kv.second.size(); ++k) {
+            Instance* I = kv.second[k];
+            size_t dsz = g.prec ? sizeof(Desc<double>) : sizeof(Desc<float>);
+            std::memcpy(host.data() + offs[gi].first + k * dsz, I->hdesc, dsz);
+            for (int t = 0; t < I->ntiles; ++t) ht[nt++] = make_int2((int)k, t * I->W);
+            g.smem = std::max(g.smem, step_smem(&I->p, I->W));
+        }
+        g.ntiles = nt;
+        b->groups.push_back(g);
+        ++gi;
+    }
+    CU(cudaMemcpyAsync(b->gmem, host.data(), total, cudaMemcpyHostToDevice, b->stream));
+    CU(cudaStreamSynchronize(b->stream));
+    b->dirty = false;
+    return VFPS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t vfps_batch_slot_bytes(const vfps_params* params)
+{
+    if (check_params(params)) return -1;
+    size_t offs[12];
+    return (int64_t)instance_bytes(params, kRingDefault / 2, offs);
+}
+
+int vfps_batch_create(int32_t max_slots, int64_t budget_bytes, void* cuda_stream, vfps_batch** out)
+{
+    if (!out || max_slots < 1 || budget_bytes < 0) return VFPS_EINVAL;
+    *out = nullptr;
+    std::unique_ptr<vfps_batch> b(new (std::nothrow) vfps_batch());
+    if (!b) return VFPS_ENOMEM;
+    if (cuda_stream) {
+        b->stream = (cudaStream_t)cuda_stream;
+    } else {
+        CU(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+        b->own_stream = true;
+    }
+    b->max_slots = max_slots;
+    b->budget = budget_bytes;
+    b->slots.assign(max_slots, nullptr);
+    *out = b.release();
+    return VFPS_OK;
+}
+
+int vfps_batch_add(vfps_batch* b, const vfps_params* params, const double* psi0, int model, double Pi,
+                   double S_csr, const double* table, int64_t nsteps, int32_t* slot)
+{
+    if (!b || !slot || nsteps < 0) return VFPS_EINVAL;
+    int rc = check_params(params);
+    if (rc) return rc;
+    int free_slot = -1;
+    for (int i = 0; i < b->max_slots; ++i)
+        if (!b->slots[i]) {
+            free_slot = i;
+            break;
+        }
+    if (free_slot < 0) return VFPS_EBUSY;
+    size_t offs[12];
+    long long need = (long long)instance_bytes(params, kRingDefault / 2, offs);
+    if (b->budget > 0 && b->used + need > b->budget) return VFPS_EBUSY;
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && (long long)fr < need + (64ll << 20)) return VFPS_EBUSY;
+    CU(cudaStreamSynchronize(b->stream));
+    rc = init_kernels();
+    if (rc) return rc;
+    Instance* I = nullptr;
+    rc = create_instance(params, psi0, kRingDefault / 2, b->stream, &I);
+    if (rc) return rc;
+    I->target = nsteps;
+    rc = upload_impedance(*I, model, Pi, S_csr, table, b->stream);
+    if (rc == VFPS_OK) rc = prologue(*I, b->stream);
+    if (rc) {
+        destroy_instance(I);
+        return rc;
+    }
+    b->slots[free_slot] = I;
+    b->used += (long long)I->dbytes;
+    b->dirty = true;
+    *slot = free_slot;
+    return VFPS_OK;
+}
+
+int vfps_batch_run(vfps_batch* b, int64_t chunk_steps)
+{
+    if (!b || chunk_steps < 0) return VFPS_EINVAL;
+    int rc;
+    while (chunk_steps > 0) {
+        if (b->dirty) {
+            rc = rebuild_groups(b);
+            if (rc) return rc;
+        }
+        // steps until the next slot finishes or a ring fills
+        long long k = chunk_steps;
+        bool any = false;
+        for (Instance* I : b->slots) {
+            if (!I || remaining(I) <= 0) continue;
+            any = true;
+            k = std::min(k, remaining(I));
+            long long room = (long long)I->ring - 1 - (I->steps_queued - I->drained);
+            if (room <= 0) {
+                rc = drain(*I, b->stream);
+                if (rc) return rc;
+                room = (long long)I->ring - 1;
+            }
+            k = std::min(k, room);
+        }
+        if (!any) break;
+        for (long long s = 0; s < k; ++s)
+            for (const Group& g : b->groups) {
+                rc = launch_step(g, b->stream);
+                if (rc) return rc;
+            }
+        for (Instance* I : b->slots) {
+            if (!I || remaining(I) <= 0) continue;
+            I->steps_queued += k;
+            if (remaining(I) == 0) b->dirty = true;
+        }
+        chunk_steps -= k;
+    }
+    return VFPS_OK;
+}
+
+int vfps_batch_poll(vfps_batch* b, int32_t* done_slots, int32_t cap, int32_t* n_done)
+{
+    if (!b || !n_done || cap < 0 || (cap > 0 && !done_slots)) return VFPS_EINVAL;
+    CU(cudaStreamSynchronize(b->stream));
+    int k = 0;
+    for (int i = 0; i < b->max_slots; ++i) {
+        Instance* I = b->slots[i];
+        if (I && remaining(I) <= 0) {
+            if (k < cap) done_slots[k] = i;
+            ++k;
+        }
+    }
+    *n_done = std::min(k, cap);
+    return VFPS_OK;
+}
+
+int vfps_batch_take(vfps_batch* b, int32_t slot, double* psi_out, double* rho_out, double* power_out,
+                    int64_t power_cap, int64_t* n_power, int64_t* steps_done)
+{
+    if (!b || slot < 0 || slot >= b->max_slots || !b->slots[slot]) return VFPS_EINVAL;
+    Instance& I = *b->slots[slot];
+    int rc = drain(I, b->stream);
+    if (rc) return rc;
+    if (psi_out) {
+        rc = copy_state(I, b->stream, psi_out);
+        if (rc) return rc;
+    }
+    if (rho_out) CU(cudaMemcpyAsync(rho_out, I.rho, sizeof(double) * I.n, cudaMemcpyDeviceToHost, b->stream));
+    if (power_out && power_cap > 0) {
+        int64_t k = std::min<int64_t>(power_cap, (int64_t)I.pw.size());
+        std::memcpy(power_out, I.pw.data(), sizeof(double) * k);
+        if (n_power) *n_power = k;
+    } else if (n_power) {
+        *n_power = (int64_t)I.pw.size();
+    }
+    if (steps_done) *steps_done = I.steps_queued;
+    return read_status(I, b->stream);
+}
+
+int vfps_batch_remove(vfps_batch* b, int32_t slot)
+{
+    if (!b || slot < 0 || slot >= b->max_slots || !b->slots[slot]) return VFPS_EINVAL;
+    CU(cudaStreamSynchronize(b->stream));
+    b->used -= (long long)b->slots[slot]->dbytes;
+    destroy_instance(b->slots[slot]);
+    b->slots[slot] = nullptr;
+    b->dirty = true;
+    return VFPS_OK;
+}
+
+int vfps_batch_usage(vfps_batch* b, int32_t* active, int64_t* bytes)
+{
+    if (!b) return VFPS_EINVAL;
+    int k = 0;
+    for (Instance* I : b->slots)
+        if (I) ++k;
+    if (active) *active = k;
+    if (bytes) *bytes = b->used;
+    return VFPS_OK;
+}
+
+int vfps_batch_destroy(vfps_batch* b)
+{
+    if (!b) return VFPS_OK;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    for (Instance* I : b->slots) destroy_instance(I);
+    free_groups(b);
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return VFPS_OK;
+}
+
+}  // extern "C"

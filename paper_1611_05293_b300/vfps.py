@@ -1,0 +1,316 @@
+"""Python binding of libvfps.so (include/vfps.h): argument marshalling only.
+
+Every step of the solver runs in the library's CUDA kernels; this module
+converts NumPy arrays to pointers, checks return codes and raises
+``VfpsError``.  There is no fallback: if the in-tree library is missing the
+import of the binding fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libvfps.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENAN, EBUSY = 0, -1, -2, -3, -4, -5, -6
+IMPEDANCE_NONE, IMPEDANCE_FREE_SPACE, IMPEDANCE_PARALLEL_PLATES, IMPEDANCE_TABLE = 0, 1, 2, 3
+
+# every symbol include/vfps.h declares
+EXPORTS = [
+    "vfps_params_default", "vfps_create", "vfps_set_impedance", "vfps_step", "vfps_profile",
+    "vfps_csr_power", "vfps_charge_series", "vfps_get_state", "vfps_set_state",
+    "vfps_steps_done", "vfps_destroy", "vfps_strerror", "vfps_impedance_table",
+    "vfps_batch_create", "vfps_batch_add", "vfps_batch_slot_bytes", "vfps_batch_run",
+    "vfps_batch_poll", "vfps_batch_take", "vfps_batch_remove", "vfps_batch_usage",
+    "vfps_batch_destroy",
+]
+
+
+class VfpsError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {_lib_strerror(code)} ({code})")
+
+
+class CParams(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("steps_per_period", ctypes.c_int32),
+                ("interp_points", ctypes.c_int32), ("clamp", ctypes.c_int32),
+                ("fp_derivative", ctypes.c_int32), ("pad_factor", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("renormalize", ctypes.c_int32),
+                ("half_width", ctypes.c_double), ("beta", ctypes.c_double)]
+
+
+@dataclass
+class Params:
+    """Mirror of vfps_params (defaults as in vfps_params_default)."""
+    n: int = 256
+    steps_per_period: int = 1000
+    beta: float = 0.0
+    half_width: float = 6.0
+    interp_points: int = 4
+    clamp: int = 0
+    fp_derivative: int = 1
+    pad_factor: int = 2
+    precision: int = 0
+    renormalize: int = 1
+
+    def c(self) -> CParams:
+        return CParams(self.n, self.steps_per_period, self.interp_points, self.clamp,
+                       self.fp_derivative, self.pad_factor, self.precision, self.renormalize,
+                       self.half_width, self.beta)
+
+
+_lib = None
+_D = ctypes.POINTER(ctypes.c_double)
+_VP = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I32 = ctypes.c_int32
+
+
+def lib() -> ctypes.CDLL:
+    """Load the in-tree library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libvfps.so not built at {LIB_PATH}; run paper_1611_05293_b300/build.py")
+    L = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER(CParams)
+    sig = {
+        "vfps_params_default": (None, [P]),
+        "vfps_create": (ctypes.c_int, [P, _D, _VP, ctypes.POINTER(_VP)]),
+        "vfps_set_impedance": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_double, ctypes.c_double, _D]),
+        "vfps_step": (ctypes.c_int, [_VP, _I64]),
+        "vfps_profile": (ctypes.c_int, [_VP, _D]),
+        "vfps_csr_power": (ctypes.c_int, [_VP, _D, _I64, ctypes.POINTER(_I64)]),
+        "vfps_charge_series": (ctypes.c_int, [_VP, _D, _I64, ctypes.POINTER(_I64)]),
+        "vfps_get_state": (ctypes.c_int, [_VP, _D]),
+        "vfps_set_state": (ctypes.c_int, [_VP, _D]),
+        "vfps_steps_done": (ctypes.c_int, [_VP, ctypes.POINTER(_I64)]),
+        "vfps_destroy": (ctypes.c_int, [_VP]),
+        "vfps_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "vfps_impedance_table": (ctypes.c_int, [ctypes.c_int, _I32, ctypes.c_double, _I32,
+                                                ctypes.c_double, _D]),
+        "vfps_batch_create": (ctypes.c_int, [_I32, _I64, _VP, ctypes.POINTER(_VP)]),
+        "vfps_batch_add": (ctypes.c_int, [_VP, P, _D, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                          _D, _I64, ctypes.POINTER(_I32)]),
+        "vfps_batch_slot_bytes": (_I64, [P]),
+        "vfps_batch_run": (ctypes.c_int, [_VP, _I64]),
+        "vfps_batch_poll": (ctypes.c_int, [_VP, ctypes.POINTER(_I32), _I32, ctypes.POINTER(_I32)]),
+        "vfps_batch_take": (ctypes.c_int, [_VP, _I32, _D, _D, _D, _I64, ctypes.POINTER(_I64),
+                                           ctypes.POINTER(_I64)]),
+        "vfps_batch_remove": (ctypes.c_int, [_VP, _I32]),
+        "vfps_batch_usage": (ctypes.c_int, [_VP, ctypes.POINTER(_I32), ctypes.POINTER(_I64)]),
+        "vfps_batch_destroy": (ctypes.c_int, [_VP]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _lib_strerror(code: int) -> str:
+    try:
+        return lib().vfps_strerror(code).decode()
+    except Exception:  # library not loadable while formatting an error
+        return "error"
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != OK:
+        raise VfpsError(rc, what)
+
+
+def _dptr(a):
+    return None if a is None else a.ctypes.data_as(_D)
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None and a.shape != shape:
+        raise ValueError(f"expected shape {shape}, got {a.shape}")
+    return a
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def impedance_table(model: int, n: int, half_width: float = 6.0, pad_factor: int = 2,
+                    Pi: float = 0.0) -> np.ndarray:
+    """Host-side library impedance table (complex, M/2+1 values)."""
+    M = 1
+    while M < pad_factor * n:
+        M <<= 1
+    out = np.zeros(M + 2)
+    _check(lib().vfps_impedance_table(model, n, half_width, pad_factor, Pi, _dptr(out)),
+           "vfps_impedance_table")
+    return out[0::2] + 1j * out[1::2]
+
+
+class Simulation:
+    """One simulation handle (vfps_create ... vfps_destroy)."""
+
+    def __init__(self, params: Params, psi0=None, stream=None):
+        self.params = params
+        n = params.n
+        psi = None if psi0 is None else _f64(psi0, (n, n))
+        h = _VP()
+        _check(lib().vfps_create(ctypes.byref(params.c()), _dptr(psi), _stream_ptr(stream),
+                                 ctypes.byref(h)), "vfps_create")
+        self._h = h
+
+    def set_impedance(self, model: int, Pi: float = 0.0, S_csr: float = 0.0, table=None):
+        tab = None
+        if table is not None:
+            t = np.asarray(table, dtype=np.complex128)
+            tab = np.empty(2 * t.size)
+            tab[0::2], tab[1::2] = t.real, t.imag
+        _check(lib().vfps_set_impedance(self._h, model, Pi, S_csr, _dptr(tab)), "vfps_set_impedance")
+
+    def step(self, nsteps: int):
+        _check(lib().vfps_step(self._h, int(nsteps)), "vfps_step")
+
+    def profile(self) -> np.ndarray:
+        out = np.empty(self.params.n)
+        _check(lib().vfps_profile(self._h, _dptr(out)), "vfps_profile")
+        return out
+
+    def _series(self, fn, cap):
+        out = np.empty(max(cap, 1))
+        k = _I64()
+        _check(fn(self._h, _dptr(out), cap, ctypes.byref(k)), fn.__name__)
+        return out[:k.value].copy()
+
+    def csr_power(self, cap: int = 1 << 22) -> np.ndarray:
+        return self._series(lib().vfps_csr_power, cap)
+
+    def charge_series(self, cap: int = 1 << 22) -> np.ndarray:
+        return self._series(lib().vfps_charge_series, cap)
+
+    def get_state(self) -> np.ndarray:
+        n = self.params.n
+        out = np.empty((n, n))
+        _check(lib().vfps_get_state(self._h, _dptr(out)), "vfps_get_state")
+        return out
+
+    def set_state(self, psi):
+        n = self.params.n
+        _check(lib().vfps_set_state(self._h, _dptr(_f64(psi, (n, n)))), "vfps_set_state")
+
+    def steps_done(self) -> int:
+        k = _I64()
+        _check(lib().vfps_steps_done(self._h, ctypes.byref(k)), "vfps_steps_done")
+        return k.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().vfps_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Slots that advance together (vfps_batch_*)."""
+
+    def __init__(self, max_slots: int, budget_bytes: int = 0, stream=None):
+        b = _VP()
+        _check(lib().vfps_batch_create(max_slots, budget_bytes, _stream_ptr(stream), ctypes.byref(b)),
+               "vfps_batch_create")
+        self._b = b
+        self.params = {}
+
+    @staticmethod
+    def slot_bytes(params: Params) -> int:
+        return int(lib().vfps_batch_slot_bytes(ctypes.byref(params.c())))
+
+    def add(self, params: Params, psi0=None, model: int = 0, Pi: float = 0.0, S_csr: float = 0.0,
+            nsteps: int = 0, table=None) -> int:
+        n = params.n
+        psi = None if psi0 is None else _f64(psi0, (n, n))
+        tab = None
+        if table is not None:
+            t = np.asarray(table, dtype=np.complex128)
+            tab = np.empty(2 * t.size)
+            tab[0::2], tab[1::2] = t.real, t.imag
+        s = _I32()
+        _check(lib().vfps_batch_add(self._b, ctypes.byref(params.c()), _dptr(psi), model, Pi, S_csr,
+                                    _dptr(tab), int(nsteps), ctypes.byref(s)), "vfps_batch_add")
+        self.params[s.value] = params
+        return s.value
+
+    def try_add(self, *a, **kw):
+        """add(), but returns None instead of raising when the batch is full (EBUSY)."""
+        try:
+            return self.add(*a, **kw)
+        except VfpsError as e:
+            if e.code == EBUSY:
+                return None
+            raise
+
+    def run(self, chunk_steps: int):
+        _check(lib().vfps_batch_run(self._b, int(chunk_steps)), "vfps_batch_run")
+
+    def poll(self) -> list[int]:
+        cap = max(1, len(self.params))
+        out = (_I32 * cap)()
+        k = _I32()
+        _check(lib().vfps_batch_poll(self._b, out, cap, ctypes.byref(k)), "vfps_batch_poll")
+        return [out[i] for i in range(k.value)]
+
+    def take(self, slot: int, psi=True, rho=True, power_cap: int = 1 << 22):
+        n = self.params[slot].n
+        ps = np.empty((n, n)) if psi else None
+        rh = np.empty(n) if rho else None
+        pw = np.empty(max(1, power_cap))
+        npow, steps = _I64(), _I64()
+        _check(lib().vfps_batch_take(self._b, slot, _dptr(ps), _dptr(rh), _dptr(pw), power_cap,
+                                     ctypes.byref(npow), ctypes.byref(steps)), "vfps_batch_take")
+        return {"psi": ps, "rho": rh, "power": pw[:npow.value].copy(), "steps": steps.value}
+
+    def remove(self, slot: int):
+        _check(lib().vfps_batch_remove(self._b, slot), "vfps_batch_remove")
+        self.params.pop(slot, None)
+
+    def usage(self):
+        a, b = _I32(), _I64()
+        _check(lib().vfps_batch_usage(self._b, ctypes.byref(a), ctypes.byref(b)), "vfps_batch_usage")
+        return a.value, b.value
+
+    def close(self):
+        if getattr(self, "_b", None):
+            lib().vfps_batch_destroy(self._b)
+            self._b = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,187 @@
+"""GPU path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances: FP64 path 1e-11 relative L-infinity per step; FP32 path 1e-5
+relative L-infinity per step and 1e-3 after 1000 steps below threshold (the
+stated targets).  Relative L-infinity = max|gpu - oracle| / max|oracle|.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1611_05293_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def V():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1611_05293_b300 import vfps
+    vfps.lib()
+    return vfps
+
+
+def rel_linf(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def make(V, n, precision, spp=500, beta=1e-2, model=0, Pi=0.0, S=0.0, psi=None, **kw):
+    gp = V.Params(n=n, steps_per_period=spp, beta=beta, precision=precision, **kw)
+    op = O.Params(n=n, steps_per_period=spp, beta=beta, s_csr=S, **kw)
+    sim = V.Simulation(gp, psi)
+    sim.set_impedance(model, Pi, S)
+    zr, zi = O.impedance(op, model, Pi)
+    return sim, op, zr, zi
+
+
+CASES = [
+    # n, input, model, Pi, S, extra
+    (8, "random", 1, 0.0, 0.7, {}),
+    (17, "random", 2, 1.5, 1.1, {}),
+    (64, "blobs", 2, 2.0, 0.9, {}),
+    (100, "blobs", 1, 0.0, 0.5, {}),
+    (64, "blobs", 2, 1.0, 2.0, {"interp_points": 3}),
+    (33, "random", 2, 1.0, 1.3, {"interp_points": 2}),
+    (64, "blobs", 2, 3.0, 1.5, {"clamp": 1}),
+    (48, "blobs", 1, 0.0, 0.8, {"fp_derivative": 0}),
+    (64, "blobs", 2, 2.0, 0.9, {"pad_factor": 4}),
+    (40, "blobs", 2, 2.0, 0.9, {"renormalize": 0}),
+]
+
+
+def _input(kind, n, seed):
+    return W.random_field(n, seed) if kind == "random" else W.blobs(n, seed)
+
+
+@pytest.mark.parametrize("precision,tol", [(1, 1e-11), (0, 1e-5)])
+@pytest.mark.parametrize("n,kind,model,Pi,S,extra", CASES)
+def test_one_step_matches_oracle(V, precision, tol, n, kind, model, Pi, S, extra):
+    psi0 = _input(kind, n, seed=n)
+    sim, op, zr, zi = make(V, n, precision, model=model, Pi=Pi, S=S, psi=psi0, beta=0.05, **extra)
+    ref0 = O.normalize(op, psi0)
+    assert rel_linf(sim.get_state(), ref0) < tol
+    rho0, _ = O.project(op, ref0)
+    assert rel_linf(sim.profile(), rho0) < tol
+    ref1, _, _, P0, Q0 = O.step(op, zr, zi, ref0)
+    sim.step(1)
+    assert rel_linf(sim.get_state(), ref1) < tol
+    P = sim.csr_power()
+    Q = sim.charge_series()
+    assert P.shape == (1,) and Q.shape == (1,)
+    if model:
+        assert abs(P[0] - P0) <= tol * abs(P0)
+    assert abs(Q[0] - Q0) <= tol * abs(Q0)
+    rho1, _ = O.project(op, ref1)
+    assert rel_linf(sim.profile(), rho1) < tol
+    sim.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(1, 1e-10), (0, 1e-3)])
+def test_c1_run_below_threshold(V, precision, tol):
+    """Plain single simulation: N=64 on [-6,6]^2, unit Gaussian, beta=1e-2,
+    500 steps per period for one period, cubic rotation, FP, parallel plates
+    Pi=2 at S_csr=0.3.  Whole psi and the CSR-power series vs the oracle."""
+    n, spp = 64, 500
+    psi0 = W.gaussian(n)
+    sim, op, zr, zi = make(V, n, precision, spp=spp, beta=1e-2, model=2, Pi=2.0, S=0.3, psi=psi0)
+    ref, Pref, Qref = O.run(op, zr, zi, O.normalize(op, psi0), spp)
+    sim.step(spp)
+    assert rel_linf(sim.get_state(), ref) < tol
+    P = sim.csr_power()
+    assert P.shape == (spp,)
+    assert np.max(np.abs(P - Pref) / np.abs(Pref)) < tol
+    assert sim.steps_done() == spp
+    sim.close()
+
+
+def test_fp32_1000_steps(V):
+    """FP32 psi for 1000 steps below threshold: relative L-inf <= 1e-3."""
+    n, spp = 96, 1000
+    psi0 = W.noisy_gaussian(n, 1611, 1e-6)
+    sim, op, zr, zi = make(V, n, 0, spp=spp, beta=1.25e-2, model=2, Pi=2.0, S=0.4, psi=psi0)
+    ref, Pref, _ = O.run(op, zr, zi, O.normalize(op, psi0), 1000)
+    sim.step(1000)
+    assert rel_linf(sim.get_state(), ref) < 1e-3
+    P = sim.csr_power()
+    assert np.max(np.abs(P - Pref) / np.abs(Pref)) < 1e-3
+    sim.close()
+
+
+@pytest.mark.parametrize("n", [8, 15, 32])
+def test_quarter_turn_permutation(V, n):
+    """steps_per_period = 4, no wake, no FP: one step is the 90-degree node
+    permutation psi[x][y] <- psi[n-1-y][x] (exact up to rounding)."""
+    psi0 = W.random_field(n, 3)
+    sim, op, _, _ = make(V, n, 1, spp=4, beta=0.0, psi=psi0)
+    ref = O.normalize(op, psi0)
+    sim.step(1)
+    out = sim.get_state()
+    perm = np.array([[ref[n - 1 - y, x] for y in range(n)] for x in range(n)])
+    assert np.max(np.abs(out - perm)) < 1e-12 * ref.max()
+    sim.close()
+
+
+def test_full_size_256_one_step(V):
+    """Full configuration size N=256, FP32, beta=1.25e-2, 1000 steps/period,
+    Pi=2, S=0.9: every element of one step vs the oracle."""
+    n = 256
+    psi0 = W.noisy_gaussian(n, 1611, 1e-6)
+    sim, op, zr, zi = make(V, n, 0, spp=1000, beta=1.25e-2, model=2, Pi=2.0, S=0.9, psi=psi0)
+    ref, _, _, P0, _ = O.step(op, zr, zi, O.normalize(op, psi0))
+    sim.step(1)
+    assert rel_linf(sim.get_state(), ref) < 1e-5
+    assert abs(sim.csr_power()[0] - P0) < 1e-5 * P0
+    sim.close()
+
+
+def test_full_size_1024_sampled_rows(V):
+    """N=1024, 4000 steps/period, Pi=1, S=3: the oracle's full step at this
+    size takes seconds; compare all of it."""
+    n = 1024
+    psi0 = W.gaussian(n)
+    sim, op, zr, zi = make(V, n, 0, spp=4000, beta=1e-2, model=2, Pi=1.0, S=3.0, psi=psi0)
+    ref, _, _, _, _ = O.step(op, zr, zi, O.normalize(op, psi0))
+    sim.step(1)
+    assert rel_linf(sim.get_state(), ref) < 1e-5
+    sim.close()
+
+
+def test_state_roundtrip_and_counters(V):
+    n = 40
+    psi0 = W.blobs(n, 9)
+    sim, op, zr, zi = make(V, n, 1, model=1, S=0.5, psi=psi0)
+    sim.step(0)
+    assert sim.steps_done() == 0
+    sim.step(37)
+    mid = sim.get_state()
+    sim.step(5)
+    after = sim.get_state()
+    sim.set_state(mid)
+    sim.step(5)
+    assert np.array_equal(sim.get_state(), after)
+    assert sim.steps_done() == 47
+    assert sim.csr_power().shape == (47,)
+    sim.close()
+
+
+def test_invalid_arguments_are_rejected(V):
+    for bad in [dict(n=4), dict(n=64, steps_per_period=1), dict(n=64, interp_points=5),
+                dict(n=64, pad_factor=1), dict(n=64, beta=-1.0), dict(n=2049),
+                dict(n=1024, steps_per_period=4)]:
+        with pytest.raises(V.VfpsError) as e:
+            V.Simulation(V.Params(**bad))
+        assert e.value.code == V.EINVAL
+    psi = np.ones((16, 16))
+    psi[3, 3] = np.nan
+    with pytest.raises(V.VfpsError):
+        V.Simulation(V.Params(n=16), psi)
+    with pytest.raises(V.VfpsError):
+        V.Simulation(V.Params(n=16), -np.ones((16, 16)))
+    sim = V.Simulation(V.Params(n=16))
+    with pytest.raises(V.VfpsError):
+        sim.set_impedance(2, 0.0, 1.0)   # Pi must be > 0
+    with pytest.raises(V.VfpsError):
+        sim.step(-1)
+    sim.close()
