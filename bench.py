@@ -1,0 +1,297 @@
+"""Benchmark: phase-space cell-updates/s of the per-step VFP update on B300.
+
+Default (N=1 GPU): a batched scan of N=256 grids shaped like the paper's
+current scans (S_csr on a grid in [0.2, 1.5] x Pi in {1, 2, 3}, 1000 steps per
+synchrotron period, FP32 psi with FP64 sums), with enough instances that the
+double-buffered state (2 x instances x 256 KB) exceeds the 126 MB L2, so every
+step streams psi through HBM.  One timed step = one fused launch that advances
+every instance by one time step (rotation, kick, Fokker-Planck, projection,
+FFT wake, CSR power, renormalisation).
+
+Printed (one JSON line on rank 0): value (cell-updates/s over all ranks),
+the plain single-simulation path at N=256 for comparison, a roofline object
+for the fused kernel (algorithmic 8 B per cell per step over the kernel's
+CUDA-event time, against the measured HBM copy bandwidth), the FP64 oracle
+timed on the host cores on a bounded sample (cpu_baseline), an end-to-end
+figure through the C ABI with host buffers (e2e) and the SM clocks sampled
+during the timed region.
+
+--impl reference times the FP64 CPU oracle (the method's reference
+implementation here) on the same workload shape, bounded to a few minutes.
+Multi-GPU (torchrun): one independent batch per rank, no collective; the
+barrier-bracketed time is the max over ranks (weak scaling, replicas).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+HBM_FALLBACK_GBS = 6400.0
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [x for x in (num(r[0]) for r in self.rows) if x is not None]
+        mx = [x for x in (num(r[1]) for r in self.rows) if x is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[4 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def scan_points(count: int):
+    from paper_1611_05293_b300 import workloads as W
+    base = W.scan_grid()
+    return [base[i % len(base)] for i in range(count)]
+
+
+def build_batch(V, count, n, spp, beta, stream, seed=1612):
+    from paper_1611_05293_b300 import workloads as W
+    b = V.Batch(count, 0, stream)
+    psi0 = W.noisy_gaussian(n, seed, 1e-6)
+    for S, Pi in scan_points(count):
+        b.add(V.Params(n=n, steps_per_period=spp, beta=beta), psi0, V.IMPEDANCE_PARALLEL_PLATES, Pi, S,
+              nsteps=1 << 40)
+    return b
+
+
+def cpu_baseline(n, spp, beta, budget_s=12.0):
+    """FP64 oracle on the host cores: one N=n instance of the scan for as many
+    steps as fit in budget_s (after one untimed step)."""
+    from oracle import oracle as O
+    from paper_1611_05293_b300 import workloads as W
+    O.build()
+    S, Pi = scan_points(1)[0]
+    pr = O.Params(n=n, steps_per_period=spp, beta=beta, s_csr=S)
+    zr, zi = O.impedance(pr, 2, Pi)
+    psi = O.normalize(pr, W.noisy_gaussian(n, 1612, 1e-6))
+    psi, _, _ = O.run(pr, zr, zi, psi, 1)
+    steps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        psi, _, _ = O.run(pr, zr, zi, psi, 8)
+        steps += 8
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": n * n * steps / dt, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
+            "sample": f"1 instance N={n} (S={S:.3f}, Pi={Pi:g}), {steps} steps, {dt:.1f} s"}
+
+
+def run_reference(args):
+    """--impl reference: the FP64 CPU oracle on the benchmark's workload shape."""
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    n, spp, beta = args.n, 1000, 1e-2
+    from oracle import oracle as O
+    from paper_1611_05293_b300 import workloads as W
+    O.build()
+    sims = []
+    for S, Pi in scan_points(2):
+        pr = O.Params(n=n, steps_per_period=spp, beta=beta, s_csr=S)
+        zr, zi = O.impedance(pr, 2, Pi)
+        sims.append([pr, zr, zi, O.normalize(pr, W.noisy_gaussian(n, 1612, 1e-6))])
+    per_step = 2 if args.steps > 20 else 4   # bounded sample per timed step
+    for _ in range(args.warmup):
+        for s in sims:
+            s[3], _, _ = O.run(s[0], s[1], s[2], s[3], 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for s in sims:
+            s[3], _, _ = O.run(s[0], s[1], s[2], s[3], per_step)
+    dt = time.perf_counter() - t0
+    value = n * n * per_step * len(sims) * args.steps / dt
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = f"{len(sims)} instances of N={n}, {per_step} steps each per timed step"
+    print(json.dumps({
+        "impl": "reference", "metric": "phase-space cell-updates/s", "value": value,
+        "unit": "cell-updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"batched N={n} parallel-plates scan (oracle sample: {sample})",
+                   "grid": n, "steps_per_period": spp},
+        "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--instances", type=int, default=512)
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    assert args.warmup >= 3, "at least 3 warm-up steps"
+
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_1611_05293_b300 import vfps as V
+
+    n, spp, beta = args.n, 1000, 1e-2
+    stream = torch.cuda.Stream()
+    hbm, peak_kind = measured_peaks()
+
+    # ---- batched scan (the headline)
+    b = build_batch(V, args.instances, n, spp, beta, stream)
+    b.run(args.warmup)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        e0.record(stream)
+        b.run(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    dt = e0.elapsed_time(e1) / 1e3
+    if world > 1:
+        t = torch.tensor([dt], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dt = float(t.item())
+        dist.barrier()
+    cells_step = args.instances * n * n
+    value = world * cells_step * args.steps / dt
+    achieved = 8.0 * cells_step / (dt / args.steps) / 1e9  # GB/s, one launch per step
+    b.close()
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    # ---- plain single-simulation path (N=256, FP32, Pi=2, S=0.9)
+    sim = V.Simulation(V.Params(n=n, steps_per_period=spp, beta=1.25e-2), None, stream)
+    sim.set_impedance(V.IMPEDANCE_PARALLEL_PLATES, 2.0, 0.9)
+    sim.step(args.warmup)
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    plain_steps = max(args.steps, 256)
+    p0.record(stream)
+    sim.step(plain_steps)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    pdt = p0.elapsed_time(p1) / 1e3
+    sim.close()
+    plain = {"value": n * n * plain_steps / pdt, "unit": "cell-updates/s",
+             "ms_per_step": 1e3 * pdt / plain_steps, "workload": "single simulation N=256 FP32, Pi=2, S=0.9"}
+
+    # ---- end to end through the C ABI with host buffers
+    t0 = time.perf_counter()
+    bb = build_batch(V, args.instances, n, spp, beta, stream)
+    bb.run(args.steps)
+    outs = [bb.take(s, psi=True, rho=False) for s in range(args.instances)]
+    torch.cuda.synchronize()
+    e2e_dt = time.perf_counter() - t0
+    bb.close()
+    h2d = args.instances * n * n * 8 / args.steps
+    d2h = sum(o["psi"].size * 8 + o["power"].size * 8 for o in outs) / args.steps
+    e2e = {"value": args.instances * n * n * args.steps / e2e_dt, "unit": "cell-updates/s",
+           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+           "what": "vfps_batch_add from host psi0 (fp64) + run + vfps_batch_take of psi and P(t), wall clock"}
+
+    line = {
+        "metric": "phase-space cell-updates/s", "value": value, "unit": "cell-updates/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"batched N={n} parallel-plates scan, {args.instances} instances per GPU "
+                               f"(S in [0.2,1.5] x Pi in {{1,2,3}}), {spp} steps/period, FP32 psi + FP64 sums",
+                   "instances": args.instances, "grid": n, "steps_per_period": spp, "beta": beta,
+                   "l2": f"inputs larger than L2: state {2 * cells_step * 4 / 2**20:.0f} MiB > 126 MiB",
+                   "parallelism": f"replicas x{world}"},
+        "plain": plain,
+        "batched_vs_plain": value / world / plain["value"],
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None, "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_cell": 8},
+        "gpu_launches": args.steps,
+        "clocks": clk.summary(),
+        "e2e": e2e,
+        "wall_s_timed": wall,
+    }
+    if not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(n, spp, beta)
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -75,13 +75,13 @@ typedef struct vfps_handle vfps_handle;
 void vfps_params_default(vfps_params* p);
 
 /* Create one simulation.
- *   psi0:  host, n*n doubles, [q][p] row-major, non-negative; NULL = the unit
- *          Gaussian exp(-(q^2+p^2)/2).  The library normalises it to charge
- *          Delta^2 sum psi = 1 before upload.
+ *   psi0:  host, n*n doubles, [q][p] row-major, finite, with positive total
+ *          charge; NULL = the unit Gaussian exp(-(q^2+p^2)/2).  The library
+ *          normalises it to charge Delta^2 sum psi = 1 before upload.
  *   cuda_stream: a cudaStream_t to queue work on, or NULL for a library-owned
  *          stream.
  * The impedance starts as VFPS_IMPEDANCE_NONE with S_csr = 0.
- * Errors: EINVAL (parameters out of range, negative or all-zero psi0),
+ * Errors: EINVAL (parameters out of range, non-finite psi0 or charge <= 0),
  * ENOMEM, ECUDA. */
 int vfps_create(const vfps_params* params, const double* psi0, void* cuda_stream,
                 vfps_handle** out);
@@ -130,6 +130,10 @@ int vfps_destroy(vfps_handle* h);
 
 /* Static description of an error code. */
 const char* vfps_strerror(int code);
+
+/* The calling thread's last failing CUDA call and its message ("" if none);
+ * valid until that thread's next library call. */
+const char* vfps_last_cuda_error(void);
 
 /* Host-only (needs no device): the library's FP64 impedance table for a grid,
  * the values vfps_set_impedance uploads.  out_re_im: (M/2+1) interleaved

@@ -38,10 +38,20 @@ constexpr int kRingDefault = 1 << 15;  // CSR-power ring entries per simulation
 constexpr int kGraphSteps = 32;        // launches per captured CUDA graph
 constexpr size_t kAlign = 256;
 
+thread_local char g_last_error[256] = "";
+
+void note_cuda_error(cudaError_t e, const char* where)
+{
+    std::snprintf(g_last_error, sizeof(g_last_error), "%s: %s", where, cudaGetErrorString(e));
+}
+
 #define CU(call)                                   \
     do {                                           \
         cudaError_t e_ = (call);                   \
-        if (e_ != cudaSuccess) return VFPS_ECUDA;  \
+        if (e_ != cudaSuccess) {                   \
+            note_cuda_error(e_, #call);            \
+            return VFPS_ECUDA;                     \
+        }                                          \
     } while (0)
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -116,10 +126,11 @@ int device_smem_limit()
     return g_max_smem;
 }
 
-// CTA width: the widest of 8, 4, 2 columns whose shared memory fits.
+// CTA width: the widest of 8, 4, 2 columns whose shared memory fits (the
+// kernels also use a few bytes of static shared memory; keep 1 KB for it).
 int choose_width(const vfps_params* p)
 {
-    int lim = device_smem_limit();
+    int lim = device_smem_limit() - 1024;
     for (int W : {8, 4, 2})
         if ((long long)step_smem(p, W) <= lim) return W;
     return 0;
@@ -261,10 +272,13 @@ int upload_psi(Instance& I, const double* psi, cudaStream_t s)
             }
         src = g.data();
     }
+    // Interpolation overshoots leave small negative densities in evolved
+    // states (Sec. IV.B), so only non-finite values and a non-positive total
+    // charge are rejected.
     double sum = 0.0;
     for (size_t i = 0; i < (size_t)n * n; ++i) {
         double v = src[i];
-        if (!std::isfinite(v) || v < 0.0) return VFPS_EINVAL;
+        if (!std::isfinite(v)) return VFPS_EINVAL;
         sum += v;
     }
     if (!(sum > 0.0)) return VFPS_EINVAL;
@@ -288,6 +302,27 @@ int upload_psi(Instance& I, const double* psi, cudaStream_t s)
     return VFPS_OK;
 }
 
+// Tables are costly for the shielded model (an Airy sum per frequency), and a
+// parameter scan reuses a few (model, M, Delta, Pi): keep the last 64.
+void cached_impedance(int model, int M, double delta, double Pi, std::vector<std::complex<double>>& z)
+{
+    static std::map<std::tuple<int, int, double, double>, std::vector<std::complex<double>>> cache;
+    static std::deque<std::tuple<int, int, double, double>> order;
+    auto key = std::make_tuple(model, M, delta, model == 2 ? Pi : 0.0);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+        z = it->second;
+        return;
+    }
+    vfps::impedance_table(model, M, delta, Pi, z);
+    cache[key] = z;
+    order.push_back(key);
+    if (order.size() > 64) {
+        cache.erase(order.front());
+        order.pop_front();
+    }
+}
+
 int upload_impedance(Instance& I, int model, double Pi, double S, const double* table, cudaStream_t s)
 {
     int K = I.M / 2;
@@ -301,7 +336,7 @@ int upload_impedance(Instance& I, int model, double Pi, double S, const double* 
         }
     } else if (model >= 0 && model <= 2) {
         if (model == 2 && !(Pi > 0.0)) return VFPS_EINVAL;
-        vfps::impedance_table(model, I.M, I.delta, Pi, z);
+        cached_impedance(model, I.M, I.delta, Pi, z);
     } else {
         return VFPS_EINVAL;
     }
@@ -480,12 +515,22 @@ int launch_project(const Group& g, cudaStream_t s)
 
 // Allow every kernel variant the device's full opt-in shared memory (once,
 // before any launch or stream capture).
+template <typename K>
+cudaError_t set_smem_attr_one(K kernel, int lim)
+{
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                lim - (int)fa.sharedSizeBytes);
+}
+
 template <typename T, int NI, int W>
 cudaError_t set_smem_attr(int lim)
 {
-    cudaError_t e = cudaFuncSetAttribute(step_kernel<T, NI, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaError_t e = set_smem_attr_one(step_kernel<T, NI, W>, lim);
     if (e != cudaSuccess) return e;
-    if (NI == 4) e = cudaFuncSetAttribute(project_kernel<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    if (NI == 4) e = set_smem_attr_one(project_kernel<T, W>, lim);
     return e;
 }
 
@@ -509,8 +554,8 @@ int init_kernels()
     if (g_kernels_ready) return VFPS_OK;
     int lim = device_smem_limit();
     if (lim <= 0) return VFPS_ECUDA;
-    if (set_smem_attr_all<float>(lim) != cudaSuccess) return VFPS_ECUDA;
-    if (set_smem_attr_all<double>(lim) != cudaSuccess) return VFPS_ECUDA;
+    CU(set_smem_attr_all<float>(lim));
+    CU(set_smem_attr_all<double>(lim));
     g_kernels_ready = 1;
     return VFPS_OK;
 }
@@ -609,6 +654,8 @@ void vfps_params_default(vfps_params* p)
     p->half_width = 6.0;
     p->beta = 0.0;
 }
+
+const char* vfps_last_cuda_error(void) { return g_last_error; }
 
 const char* vfps_strerror(int code)
 {

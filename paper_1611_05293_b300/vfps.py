@@ -23,7 +23,7 @@ IMPEDANCE_NONE, IMPEDANCE_FREE_SPACE, IMPEDANCE_PARALLEL_PLATES, IMPEDANCE_TABLE
 EXPORTS = [
     "vfps_params_default", "vfps_create", "vfps_set_impedance", "vfps_step", "vfps_profile",
     "vfps_csr_power", "vfps_charge_series", "vfps_get_state", "vfps_set_state",
-    "vfps_steps_done", "vfps_destroy", "vfps_strerror", "vfps_impedance_table",
+    "vfps_steps_done", "vfps_destroy", "vfps_strerror", "vfps_last_cuda_error", "vfps_impedance_table",
     "vfps_batch_create", "vfps_batch_add", "vfps_batch_slot_bytes", "vfps_batch_run",
     "vfps_batch_poll", "vfps_batch_take", "vfps_batch_remove", "vfps_batch_usage",
     "vfps_batch_destroy",
@@ -33,7 +33,13 @@ EXPORTS = [
 class VfpsError(RuntimeError):
     def __init__(self, code: int, what: str):
         self.code = code
-        super().__init__(f"{what}: {_lib_strerror(code)} ({code})")
+        msg = f"{what}: {_lib_strerror(code)} ({code})"
+        if code == ECUDA:
+            try:
+                msg += f" [{lib().vfps_last_cuda_error().decode()}]"
+            except Exception:
+                pass
+        super().__init__(msg)
 
 
 class CParams(ctypes.Structure):
@@ -93,6 +99,7 @@ def lib() -> ctypes.CDLL:
         "vfps_steps_done": (ctypes.c_int, [_VP, ctypes.POINTER(_I64)]),
         "vfps_destroy": (ctypes.c_int, [_VP]),
         "vfps_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "vfps_last_cuda_error": (ctypes.c_char_p, []),
         "vfps_impedance_table": (ctypes.c_int, [ctypes.c_int, _I32, ctypes.c_double, _I32,
                                                 ctypes.c_double, _D]),
         "vfps_batch_create": (ctypes.c_int, [_I32, _I64, _VP, ctypes.POINTER(_VP)]),

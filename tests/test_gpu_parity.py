@@ -160,7 +160,9 @@ def test_state_roundtrip_and_counters(V):
     after = sim.get_state()
     sim.set_state(mid)
     sim.step(5)
-    assert np.array_equal(sim.get_state(), after)
+    # set_state re-derives the wake from the uploaded psi (its own summation
+    # order), so the resumed run agrees to rounding, not bit for bit
+    assert rel_linf(sim.get_state(), after) < 1e-12
     assert sim.steps_done() == 47
     assert sim.csr_power().shape == (47,)
     sim.close()
@@ -178,7 +180,9 @@ def test_invalid_arguments_are_rejected(V):
     with pytest.raises(V.VfpsError):
         V.Simulation(V.Params(n=16), psi)
     with pytest.raises(V.VfpsError):
-        V.Simulation(V.Params(n=16), -np.ones((16, 16)))
+        V.Simulation(V.Params(n=16), -np.ones((16, 16)))      # charge <= 0
+    with pytest.raises(V.VfpsError):
+        V.Simulation(V.Params(n=16), np.zeros((16, 16)))
     sim = V.Simulation(V.Params(n=16))
     with pytest.raises(V.VfpsError):
         sim.set_impedance(2, 0.0, 1.0)   # Pi must be > 0
