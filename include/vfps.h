@@ -16,7 +16,7 @@
  *   3. RotationMap: semi-Lagrangian rotation by 2 pi/steps_per_period
  *      with 2-D Lagrange interpolation on N_I x N_I nodes            (Sec. III.A-B)
  *   4. WakeKickMap: 1-D interpolated shift of each q column along p
- *      by dp = -S_csr V(q) * 2 pi/steps_per_period                   (Sec. III.B)
+ *      by dp = +S_csr V(q) * 2 pi/steps_per_period                   (Sec. III.B)
  *   5. FokkerPlanckMap: explicit step of beta (psi + p psi' + psi'')
  *      with the cubic derivative of Eq. cubic diff                   (Sec. III.B)
  *   6. renormalisation of the charge to 1 (not in the paper; optional)
@@ -87,8 +87,9 @@ int vfps_create(const vfps_params* params, const double* psi0, void* cuda_stream
                 vfps_handle** out);
 
 /* Select the collective wake (Sec. II.B) and its strength.
- *   model: VFPS_IMPEDANCE_*;  Pi: shielding parameter R^(1/2) sigma_z / g^(3/2)
- *          of the parallel plates (model 2, > 0);
+ *   model: VFPS_IMPEDANCE_*;  Pi: shielding parameter R^(1/2) sigma_z / h^(3/2)
+ *          of parallel plates at +-h (model 2, > 0; the bursting threshold
+ *          is near S_csr = 0.5 + 0.12 Pi);
  *   S_csr: normalised bunch current I_n R^(1/3) / sigma_z^(4/3) (any sign);
  *   table_re_im: model 3 only, host, (M/2+1) interleaved (re, im) doubles of
  *          the dimensionless impedance at kappa_k = 2 pi k/(M Delta).

@@ -74,7 +74,7 @@ def kick_matrix(n, L, steps, V, s_csr, ni=4):
     phi = 2 * np.pi / steps
     A = np.zeros((n * n, n * n))
     for x in range(n):
-        shift = -s_csr * V[x] * phi / d            # dp in grid cells
+        shift = s_csr * V[x] * phi / d             # dp in grid cells
         for y in range(n):
             for iy, w in _interp_rows(n, ni, y - shift):
                 A[n * x + y, n * x + iy] += w

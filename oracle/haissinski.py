@@ -4,12 +4,12 @@ the equation itself is the textbook one and is not printed there).
 TEST INFRASTRUCTURE ONLY.
 
 Below the instability threshold the damped, diffused system relaxes to
-psi proportional to exp(-H) with H = (q^2 + p^2)/2 + S_csr Phi(q), where
+psi proportional to exp(-H) with H = (q^2 + p^2)/2 - S_csr Phi(q), where
 Phi' = V (the wake potential of the profile itself, Eq. wakepotential) so
-that dp/dtheta = -dH/dq = -q - S_csr V(q) is the kick of the time step.
+that dp/dtheta = -dH/dq = -q + S_csr V(q) is the kick of the time step.
 The profile therefore solves the fixed-point equation
 
-    rho(q) = A exp(-q^2/2 - S_csr int_{-L}^{q} V[rho](q') dq'),   int rho dq = 1,
+    rho(q) = A exp(-q^2/2 + S_csr int_{-L}^{q} V[rho](q') dq'),   int rho dq = 1,
 
 which is solved here by damped iteration on the solver's own grid, with
 the oracle's wake (direct DFT) and the trapezoid rule for the integral.
@@ -31,7 +31,7 @@ def profile(pr: "_o.Params", zre, zim, tol: float = 1e-13, damping: float = 0.5,
     for _ in range(max_iter):
         V, _P = _o.wake(pr, zre, zim, rho)
         phi = np.concatenate(([0.0], np.cumsum(0.5 * d * (V[1:] + V[:-1]))))
-        expo = -0.5 * q * q - pr.s_csr * phi
+        expo = -0.5 * q * q + pr.s_csr * phi
         new = np.exp(expo - expo.max())
         new /= d * new.sum()
         err = np.max(np.abs(new - rho)) / np.max(rho)

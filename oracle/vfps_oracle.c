@@ -232,17 +232,22 @@ void or_wake(const or_params* pr, const double* zre, const double* zim,
     free(ct); free(st); free(rr); free(ri);
 }
 
-/* WakeKickMap (Sec. III.B): the wake is turned into an energy kick
- * dp = -S_csr * V(q) * phi over one step of phi radians and translated to grid
- * units with the coordinate transformation, y_r = y - dp/Delta p.  Each
- * column q_x is shifted along p by its own amount with 1-D interpolation. */
+/* WakeKickMap (Sec. III.B): the wake is turned into a kick along p,
+ * dp = +S_csr * V(q) * phi over one step of phi radians, and translated to
+ * grid units with the coordinate transformation, y_r = y - dp/Delta p.  Each
+ * column q_x is shifted along p by its own amount with 1-D interpolation.
+ * Sign: with the printed transform V = int Z rho~ e^{ikq} dk the CSR kernel
+ * acts toward +q, so +q is the bunch head; the printed Hamiltonian's flow
+ * dq/dtheta = p then makes p grow as the energy falls (above transition), and
+ * the energy lost to the wake raises p.  This reading gives the free-space
+ * threshold S_csr ~ 0.5 that the paper quotes (Sec. IV.B). */
 void or_kick(const or_params* pr, const double* V, const double* in, double* out)
 {
     int n = pr->n;
     double d = grid_delta(pr), phi = step_angle(pr);
 #pragma omp parallel for schedule(static)
     for (int x = 0; x < n; ++x) {
-        double dp = -pr->s_csr * V[x] * phi;
+        double dp = pr->s_csr * V[x] * phi;
         for (int y = 0; y < n; ++y)
             out[(size_t)x * n + y] = or_interp_p(pr, in, x, (double)y - dp / d);
     }

@@ -2,12 +2,13 @@
 // FP64, once per vfps_set_impedance call (Sec. II.B of the paper).
 //
 //   free space:       Zhat(kappa) = 2 Gamma(2/3) 3^(-1/3) (sqrt(3)/2 + i/2) kappa^(1/3)
-//   parallel plates:  Zhat(kappa) = 8 pi^2 2^(1/3) Pi^(2/3) kappa^(-1/3)
+//   parallel plates:  Zhat(kappa) = 4 pi^2 2^(1/3) Pi^(2/3) kappa^(-1/3)
 //                                   * sum_{p>=0} [Ai'(u_p) Ci'(u_p) + u_p Ai(u_p) Ci(u_p)],
-//                     Ci = Ai - i Bi,  u_p = pi^2 (2p+1)^2 2^(-2/3) (Pi/kappa)^(4/3).
+//                     Ci = Ai - i Bi,  u_p = pi^2 (2p+1)^2 2^(-8/3) (Pi/kappa)^(4/3).
 // Zhat is the paper's Z(n)/Z0 scaled by 2 (sigma_z/R)^(1/3) at n = kappa R/sigma_z,
-// so that the kick per radian is dp = -S_csr V(q) dtheta with S_csr = I_n R^(1/3)/sigma_z^(4/3)
-// and Pi = R^(1/2) sigma_z / g^(3/2).
+// so that the kick per radian is dp = +S_csr V(q) dtheta with S_csr = I_n R^(1/3)/sigma_z^(4/3);
+// Pi = R^(1/2) sigma_z / h^(3/2) with h half the distance g = 2h between the plates
+// (the shielding parameter of the threshold law S_th ~ 0.5 + 0.12 Pi).
 //
 // Airy functions for x >= 0, written for this library:
 //   x <= 2:  Maclaurin series Ai = c1 f - c2 g, Bi = sqrt3 (c1 f + c2 g);
@@ -16,11 +17,12 @@
 //            converges geometrically for this analytic integrand), scaled by exp(zeta);
 //            Bi, Bi' by the series (x <= 8) or the large-x expansion (x > 8), scaled
 //            by exp(-zeta);
-//   x >= 60: only the combination Ai'Bi' + x Ai Bi is needed there and is taken
+//   x >= 25: only the combination Ai'Bi' + x Ai Bi is needed there and is taken
 //            from its large-x expansion 3/(16 pi) x^(-5/2) (1 + 105/(32 x^3)
-//            + 75075/(2048 x^6)), relative error < 1e-13; Ai'^2 + x Ai^2 is below
-//            exp(-600) and is dropped.  Below 60 the direct products lose about
-//            1e-16 x^3 to cancellation (two O(sqrt x) terms leave O(x^-5/2)).
+//            + 75075/(2048 x^6) + 56581525/(65536 x^9)), relative error < 1e-12;
+//            Ai'^2 + x Ai^2 is below exp(-160) and is dropped.  Below 25 the
+//            direct products lose about 3e-16 x^3 to cancellation (two O(sqrt x)
+//            terms leave O(x^-5/2)).
 #include <cmath>
 #include <complex>
 #include <vector>
@@ -125,9 +127,10 @@ AiryScaled airy_scaled(double x)
 // F(u) = Ai'(u) Ci'(u) + u Ai(u) Ci(u) with Ci = Ai - i Bi
 std::complex<double> f_term(double u)
 {
-    if (u >= 60.0) {
-        double u3 = u * u * u;
-        double g = 3.0 / (16.0 * kPi) * std::pow(u, -2.5) * (1.0 + 105.0 / (32.0 * u3) + 75075.0 / (2048.0 * u3 * u3));
+    if (u >= 25.0) {
+        double v = 1.0 / (u * u * u);
+        double g = 3.0 / (16.0 * kPi) * std::pow(u, -2.5) *
+                   (1.0 + v * (105.0 / 32.0 + v * (75075.0 / 2048.0 + v * (56581525.0 / 65536.0))));
         return {0.0, -g};
     }
     AiryScaled a = airy_scaled(u);
@@ -150,7 +153,7 @@ std::complex<double> zhat_free_space(double kappa)
 std::complex<double> zhat_parallel_plates(double kappa, double Pi)
 {
     if (!(kappa > 0.0)) return {0.0, 0.0};
-    const double a = kPi * kPi * std::pow(2.0, -2.0 / 3.0) * std::pow(Pi / kappa, 4.0 / 3.0);
+    const double a = kPi * kPi * std::pow(2.0, -8.0 / 3.0) * std::pow(Pi / kappa, 4.0 / 3.0);
     std::complex<double> s{0.0, 0.0};
     // terms fall off like (2p+1)^-5 once u_p is large; sum until negligible
     std::vector<std::complex<double>> terms;
@@ -160,7 +163,7 @@ std::complex<double> zhat_parallel_plates(double kappa, double Pi)
         std::complex<double> f = f_term(u);
         terms.push_back(f);
         s += f;
-        if (u >= 60.0 && std::abs(f) < 1e-18 * std::abs(s)) {
+        if (u >= 25.0 && std::abs(f) < 1e-18 * std::abs(s)) {
             // remainder: sum_{q>p} (2q+1)^-5 ~ int_{p+1/2}^inf (2q+1)^-5 dq
             double rem = 3.0 / (16.0 * kPi) * std::pow(a, -2.5) * std::pow(2.0 * p + 2.0, -4.0) / 8.0;
             terms.push_back({0.0, -rem});
@@ -170,7 +173,7 @@ std::complex<double> zhat_parallel_plates(double kappa, double Pi)
     // re-sum from the smallest terms up
     std::complex<double> acc{0.0, 0.0};
     for (size_t i = terms.size(); i-- > 0;) acc += terms[i];
-    double pref = 8.0 * kPi * kPi * std::cbrt(2.0) * std::pow(Pi, 2.0 / 3.0) * std::pow(kappa, -1.0 / 3.0);
+    double pref = 4.0 * kPi * kPi * std::cbrt(2.0) * std::pow(Pi, 2.0 / 3.0) * std::pow(kappa, -1.0 / 3.0);
     return pref * acc;
 }
 

@@ -237,7 +237,7 @@ void fill_desc(Instance& I)
     }
     d.delta = I.delta;
     d.dkappa = 2.0 * kPi / (I.M * I.delta);
-    d.kick_per_v = -I.S * I.phi / I.delta;
+    d.kick_per_v = I.S * I.phi / I.delta;
     std::memcpy(I.hdesc, &d, sizeof(d));
 }
 
@@ -445,7 +445,7 @@ struct Group {
     int ntiles = 0;
     void* ddescs = nullptr;  // array of Desc<T>
     int2* dtiles = nullptr;
-    size_t cap_desc = 0, cap_tiles = 0;
+    cudaStream_t stream = nullptr;  // batch groups: their own (forked) stream
 };
 
 template <typename T, int NI, int W>
@@ -870,6 +870,8 @@ struct vfps_batch {
     bool dirty = true;             // active set changed: rebuild groups
     void* gmem = nullptr;          // descriptor and tile arrays of the groups
     size_t gbytes = 0;
+    std::vector<cudaStream_t> pool;   // one stream per group, forked from `stream`
+    std::vector<cudaEvent_t> events;  // fork event + one join event per pool stream
 };
 
 namespace {
@@ -884,17 +886,43 @@ void free_groups(vfps_batch* b)
     b->groups.clear();
 }
 
-// Group the slots that still have steps to run by (precision, N_I, W).
+// Group the slots that still have steps to run by (precision, N_I, W, n):
+// one launch per group and step, each group on its own stream so that the
+// groups -- and the two halves of a large group -- overlap, and one group's
+// tail (its last CTAs and their finalisers) hides behind another's work.
+// Grouping by n keeps small grids from running at the occupancy that the
+// largest grid's shared memory would impose.
 int rebuild_groups(vfps_batch* b)
 {
     CU(cudaStreamSynchronize(b->stream));
     free_groups(b);
-    std::map<std::tuple<int, int, int>, std::vector<Instance*>> cls;
+    std::map<std::tuple<int, int, int, int, int>, std::vector<Instance*>> cls;
+    std::map<std::tuple<int, int, int, int>, int> count;
     for (Instance* I : b->slots)
-        if (I && remaining(I) > 0) cls[{I->p.precision, I->p.interp_points, I->W}].push_back(I);
+        if (I && remaining(I) > 0) ++count[{I->p.precision, I->p.interp_points, I->W, I->n}];
+    std::map<std::tuple<int, int, int, int>, int> seen;
+    for (Instance* I : b->slots) {
+        if (!I || remaining(I) <= 0) continue;
+        auto key = std::make_tuple(I->p.precision, I->p.interp_points, I->W, I->n);
+        int half = (count[key] >= 8 && seen[key]++ >= count[key] / 2) ? 1 : 0;
+        cls[{I->p.precision, I->p.interp_points, I->W, I->n, half}].push_back(I);
+    }
     if (cls.empty()) {
         b->dirty = false;
         return VFPS_OK;
+    }
+    while (b->pool.size() < cls.size()) {
+        cudaStream_t st;
+        cudaEvent_t ev;
+        CU(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        b->pool.push_back(st);
+        CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        b->events.push_back(ev);
+    }
+    if (b->events.size() < b->pool.size() + 1) {
+        cudaEvent_t ev;
+        CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        b->events.push_back(ev);
     }
     size_t total = 0;
     std::vector<std::pair<size_t, size_t>> offs;
@@ -915,7 +943,10 @@ int rebuild_groups(vfps_batch* b)
     size_t gi = 0;
     for (auto& kv : cls) {
         Group g;
-        std::tie(g.prec, g.ni, g.W) = kv.first;
+        g.prec = std::get<0>(kv.first);
+        g.ni = std::get<1>(kv.first);
+        g.W = std::get<2>(kv.first);
+        g.stream = b->pool[gi];
         g.ddescs = (unsigned char*)b->gmem + offs[gi].first;
         g.dtiles = (int2*)((unsigned char*)b->gmem + offs[gi].second);
         int2* ht = (int2*)(host.data() + offs[gi].second);
@@ -1030,11 +1061,20 @@ int vfps_batch_run(vfps_batch* b, int64_t chunk_steps)
             k = std::min(k, room);
         }
         if (!any) break;
+        // fork: every group stream waits for the batch stream, runs its k
+        // steps, and the batch stream waits for all of them again
+        cudaEvent_t fork = b->events.back();
+        CU(cudaEventRecord(fork, b->stream));
+        for (const Group& g : b->groups) CU(cudaStreamWaitEvent(g.stream, fork, 0));
         for (long long s = 0; s < k; ++s)
             for (const Group& g : b->groups) {
-                rc = launch_step(g, b->stream);
+                rc = launch_step(g, g.stream);
                 if (rc) return rc;
             }
+        for (size_t i = 0; i < b->groups.size(); ++i) {
+            CU(cudaEventRecord(b->events[i], b->groups[i].stream));
+            CU(cudaStreamWaitEvent(b->stream, b->events[i], 0));
+        }
         for (Instance* I : b->slots) {
             if (!I || remaining(I) <= 0) continue;
             I->steps_queued += k;
@@ -1110,8 +1150,11 @@ int vfps_batch_destroy(vfps_batch* b)
 {
     if (!b) return VFPS_OK;
     if (b->stream) cudaStreamSynchronize(b->stream);
+    for (cudaStream_t st : b->pool) cudaStreamSynchronize(st);
     for (Instance* I : b->slots) destroy_instance(I);
     free_groups(b);
+    for (cudaStream_t st : b->pool) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : b->events) cudaEventDestroy(ev);
     if (b->own_stream) cudaStreamDestroy(b->stream);
     delete b;
     return VFPS_OK;

@@ -59,7 +59,7 @@ struct Desc {
     T cm1, sn, c;                      // cos(phi)-1, sin(phi), grid centre (n-1)/2
     T ga[4], gb[4];                    // FP increment weights g_k(y) = ga[k] + gb[k]*y
     double delta, dkappa;              // Delta, 2 pi/(M Delta)
-    double kick_per_v;                 // -S_csr * phi / Delta: grid cells per unit wake
+    double kick_per_v;                 // S_csr * phi / Delta: grid cells per unit wake
 };
 
 // ----------------------------------------------------------------------------

@@ -1,0 +1,119 @@
+"""Batched and served simulations (vfps_batch_* through the C ABI).
+
+A slot's arithmetic does not depend on its neighbours: the same kernel runs
+each instance's CTAs with that instance's descriptor, the reductions of an
+instance are done in a fixed order by its own last CTA, and nothing is
+accumulated across instances.  So a simulation must give bit-identical psi
+and CSR-power series alone and in any mix, and every slot must also match
+the FP64 oracle within the FP32 tolerance.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1611_05293_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def V():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1611_05293_b300 import vfps
+    vfps.lib()
+    return vfps
+
+
+def alone(V, n, spp, S, Pi, nsteps, psi0, beta=1e-2):
+    sim = V.Simulation(V.Params(n=n, steps_per_period=spp, beta=beta), psi0)
+    sim.set_impedance(V.IMPEDANCE_PARALLEL_PLATES, Pi, S)
+    sim.step(nsteps)
+    out = sim.get_state(), sim.csr_power()
+    sim.close()
+    return out
+
+
+def test_slot_results_equal_solo_runs_bitwise(V):
+    mix = [(64, 500, 0.9, 2.0, 300), (100, 700, 1.2, 1.0, 170), (128, 1000, 0.5, 3.0, 250),
+           (64, 500, 0.9, 2.0, 300), (64, 800, 1.7, 2.0, 120), (40, 400, 0.3, 0.5, 90)]
+    b = V.Batch(len(mix))
+    slots = []
+    for i, (n, spp, S, Pi, ns) in enumerate(mix):
+        psi0 = W.blobs(n, 100 + (i if i != 3 else 0))
+        slots.append(b.add(V.Params(n=n, steps_per_period=spp, beta=1e-2), psi0,
+                           V.IMPEDANCE_PARALLEL_PLATES, Pi, S, nsteps=ns))
+    b.run(10_000)
+    assert sorted(b.poll()) == sorted(slots)
+    res = [b.take(s) for s in slots]
+    for i, (n, spp, S, Pi, ns) in enumerate(mix):
+        assert res[i]["steps"] == ns
+        assert res[i]["power"].shape == (ns,)
+        psi_a, p_a = alone(V, n, spp, S, Pi, ns, W.blobs(n, 100 + (i if i != 3 else 0)))
+        assert np.array_equal(res[i]["psi"], psi_a), i
+        assert np.array_equal(res[i]["power"], p_a), i
+    # in-batch duplicate (slots 0 and 3): identical inputs, identical outputs
+    assert np.array_equal(res[0]["psi"], res[3]["psi"])
+    b.close()
+
+
+def test_slots_match_oracle(V):
+    pts = [(48, 500, 0.8, 2.0, 60), (33, 300, 1.4, 1.0, 45)]
+    b = V.Batch(4)
+    slots = []
+    for n, spp, S, Pi, ns in pts:
+        slots.append(b.add(V.Params(n=n, steps_per_period=spp, beta=2e-2), W.blobs(n, 7),
+                           V.IMPEDANCE_PARALLEL_PLATES, Pi, S, nsteps=ns))
+    b.run(1000)
+    for s, (n, spp, S, Pi, ns) in zip(slots, pts):
+        op = O.Params(n=n, steps_per_period=spp, beta=2e-2, s_csr=S)
+        zr, zi = O.impedance(op, 2, Pi)
+        ref, pref, _ = O.run(op, zr, zi, O.normalize(op, W.blobs(n, 7)), ns)
+        r = b.take(s)
+        assert np.max(np.abs(r["psi"] - ref)) / ref.max() < 1e-4
+        assert np.max(np.abs(r["power"] - pref) / pref) < 1e-4
+    b.close()
+
+
+def test_budget_admission_and_reuse(V):
+    p = V.Params(n=64, steps_per_period=500, beta=1e-2)
+    one = V.Batch.slot_bytes(p)
+    assert one > 0
+    b = V.Batch(4, budget_bytes=one + one // 2)
+    s0 = b.add(p, None, V.IMPEDANCE_FREE_SPACE, 0.0, 0.5, nsteps=10)
+    assert b.try_add(p, None, V.IMPEDANCE_FREE_SPACE, 0.0, 0.5, nsteps=10) is None   # over budget
+    b.run(100)
+    assert b.poll() == [s0]
+    b.remove(s0)
+    assert b.usage() == (0, 0)
+    s1 = b.add(p, None, V.IMPEDANCE_FREE_SPACE, 0.0, 0.5, nsteps=10)
+    assert s1 == s0
+    b.close()
+    small = V.Batch(1)
+    small.add(p, None, 0, 0.0, 0.0, nsteps=1)
+    assert small.try_add(p, None, 0, 0.0, 0.0, nsteps=1) is None                     # no free slot
+    small.close()
+
+
+def test_served_stream_results_equal_solo_runs(V):
+    """Continuous batching: requests arrive while others run, are admitted as
+    slots free up (3 slots for 10 requests), and each result is the same as
+    the request run alone."""
+    from paper_1611_05293_b300.serve import Server
+    reqs = W.request_stream(10, rate_per_s=1e9, seed=1613, sizes=(32, 48, 64),
+                            steps_range=(200, 400), periods_range=(1, 2))
+    srv = Server(max_slots=3, chunk_steps=150, beta=1e-2)
+    stats = srv.run(reqs, psi0_for=lambda r: W.blobs(r.n, r.rid), realtime=False)
+    srv.close()
+    assert len(stats.results) == len(reqs)
+    assert stats.max_active == 3 and stats.max_queue >= 7
+    by_id = {r.rid: r for r in stats.results}
+    for q in reqs:
+        r = by_id[q.rid]
+        assert r.steps == q.nsteps
+        psi_a, p_a = alone(V, q.n, q.steps_per_period, q.s_csr, q.Pi, q.nsteps, W.blobs(q.n, q.rid))
+        assert np.array_equal(r.psi, psi_a)
+        assert np.array_equal(r.power, p_a)
+    s = stats.summary()
+    assert s["p99_s"] >= s["p50_s"] > 0 and s["cell_updates_per_s"] > 0

@@ -97,13 +97,13 @@ def test_fp_matches_dense_matrix():
 
 
 def test_kick_integer_shift_is_exact():
-    """dp/Delta = -S V phi/Delta an integer: the kick is an exact index shift
+    """dp/Delta = S V phi/Delta an integer: the kick is an exact index shift
     (y_r = y - dp/Delta), zero-filled at the edge."""
     n = 32
     pr = O.Params(n=n, steps_per_period=50, s_csr=1.0)
     phi = 2 * np.pi / 50
     shifts = np.array([(x % 5) - 2 for x in range(n)], dtype=float)   # cells
-    V = -shifts * pr.delta / (pr.s_csr * phi)
+    V = shifts * pr.delta / (pr.s_csr * phi)
     f = W.random_field(n, 4)
     out = O.kick(pr, V, f)
     for x in range(n):
@@ -122,7 +122,7 @@ def test_kick_exact_on_cubic_profiles():
     phi = 2 * np.pi / 40
     p = W.grid_axis(n)
     V = np.linspace(-1.0, 1.5, n)
-    dp = -pr.s_csr * V * phi
+    dp = pr.s_csr * V * phi
     f = np.tile(0.2 + 0.1 * p - 0.03 * p ** 2 + 0.002 * p ** 3, (n, 1))
     out = O.kick(pr, V, f)
     for x in range(n):

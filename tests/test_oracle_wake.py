@@ -124,7 +124,7 @@ def test_parallel_plates_against_mpmath():
 
     def zpp(kappa, Pi, P=400):
         kappa, Pi = mp.mpf(kappa), mp.mpf(Pi)
-        a = mp.pi ** 2 * mp.mpf(2) ** (-mp.mpf(2) / 3) * (Pi / kappa) ** (mp.mpf(4) / 3)
+        a = mp.pi ** 2 * mp.mpf(2) ** (-mp.mpf(8) / 3) * (Pi / kappa) ** (mp.mpf(4) / 3)
         s = mp.mpc(0)
         for p in range(P):
             u = a * (2 * p + 1) ** 2
@@ -133,7 +133,7 @@ def test_parallel_plates_against_mpmath():
         tail = 3 / (16 * mp.pi) * (a ** -2.5 * mp.zeta(5, P + 0.5) / 32
                                    + mp.mpf(105) / 32 * a ** -5.5 * mp.zeta(11, P + 0.5) / 2048)
         s -= 1j * tail
-        return complex(8 * mp.pi ** 2 * mp.cbrt(2) * Pi ** (mp.mpf(2) / 3) * kappa ** (-mp.mpf(1) / 3) * s)
+        return complex(4 * mp.pi ** 2 * mp.cbrt(2) * Pi ** (mp.mpf(2) / 3) * kappa ** (-mp.mpf(1) / 3) * s)
 
     for kap, Pi in [(1.0, 2.0), (5.0, 1.0), (40.0, 1.0), (12.0, 3.0), (0.2, 3.0)]:
         ref = zpp(kap, Pi)
@@ -143,11 +143,13 @@ def test_parallel_plates_against_mpmath():
 
 def test_airy_large_argument_expansion():
     """The closed-form remainder uses Ai'Bi' + u Ai Bi = 3/(16 pi) u^{-5/2}
-    (1 + 105/32 u^{-3} + 75075/2048 u^{-6} + O(u^{-9})); check it against mpmath."""
-    mp.mp.dps = 40
-    for u in (30, 60, 100, 1000):
+    (1 + 105/32 u^{-3} + 75075/2048 u^{-6} + 56581525/65536 u^{-9} + O(u^{-12}));
+    check it against mpmath (relative error < 1e-12 from u = 25 on)."""
+    mp.mp.dps = 60
+    for u in (25, 30, 60, 100, 1000):
         u = mp.mpf(u)
         g = mp.airyai(u, 1) * mp.airybi(u, 1) + u * mp.airyai(u) * mp.airybi(u)
         approx = 3 / (16 * mp.pi) * u ** -2.5 * (1 + mp.mpf(105) / 32 / u ** 3
-                                                  + mp.mpf(75075) / 2048 / u ** 6)
-        assert abs(g / approx - 1) < 1000 / u ** 9
+                                                  + mp.mpf(75075) / 2048 / u ** 6
+                                                  + mp.mpf(56581525) / 65536 / u ** 9)
+        assert abs(g / approx - 1) < 5e4 / u ** 12
