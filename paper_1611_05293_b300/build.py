@@ -15,7 +15,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libvfps.so")
 SOURCES = [os.path.join(CSRC, f) for f in ("vfps.cu", "impedance_host.cpp")]
-DEPS = SOURCES + [os.path.join(CSRC, "vfps_kernels.cuh"), os.path.join(ROOT, "include", "vfps.h")]
+DEPS = SOURCES + [os.path.join(CSRC, "vfps_kernels.cuh"), os.path.join(CSRC, "vfps_fast.cuh"),
+                  os.path.join(ROOT, "include", "vfps.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

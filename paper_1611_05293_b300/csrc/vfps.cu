@@ -24,6 +24,7 @@
 
 #include "../../include/vfps.h"
 #include "vfps_kernels.cuh"
+#include "vfps_fast.cuh"
 
 namespace vfps {
 void impedance_table(int model, int M, double delta, double Pi, std::vector<std::complex<double>>& z);
@@ -126,11 +127,33 @@ int device_smem_limit()
     return g_max_smem;
 }
 
+// The FP32 register-blocked kernel (vfps_fast.cuh) covers cubic
+// interpolation without clamping on grids with n a multiple of 4.
+bool fast_eligible(const vfps_params* p)
+{
+    return p->precision == 0 && p->interp_points == 4 && p->clamp == 0 && (p->n % 4) == 0;
+}
+
+size_t fast_smem(const vfps_params* p, int W)
+{
+    int M = fft_length(p);
+    size_t fin = (size_t)(M + M / 2) * 8 + (size_t)W * 32 * 8;
+    return align_up(std::max(vfps::fast_smem_bytes(p->n, halo_for(p), W), fin), 16);
+}
+
 // CTA width: the widest of 8, 4, 2 columns whose shared memory fits (the
 // kernels also use a few bytes of static shared memory; keep 1 KB for it).
-int choose_width(const vfps_params* p)
+// *fast is set when the FP32 register-blocked kernel applies and fits.
+int choose_width(const vfps_params* p, int* fast = nullptr)
 {
     int lim = device_smem_limit() - 1024;
+    if (fast) *fast = 0;
+    if (fast_eligible(p))
+        for (int W : {8, 4, 2})
+            if ((long long)fast_smem(p, W) <= lim) {
+                if (fast) *fast = 1;
+                return W;
+            }
     for (int W : {8, 4, 2})
         if ((long long)step_smem(p, W) <= lim) return W;
     return 0;
@@ -141,6 +164,7 @@ int choose_width(const vfps_params* p)
 struct Instance {
     vfps_params p{};
     int n = 0, ld = 0, M = 0, W = 0, ntiles = 0, ring = kRingDefault;
+    int fast = 0;  // 1: FP32 register-blocked step kernel
     double delta = 0, phi = 0;
     int model = 0;
     double Pi = 0, S = 0;
@@ -364,7 +388,8 @@ int create_instance(const vfps_params* p, const double* psi0, int ring, cudaStre
 {
     int rc = check_params(p);
     if (rc) return rc;
-    int W = choose_width(p);
+    int fast = 0;
+    int W = choose_width(p, &fast);
     if (W == 0) return VFPS_EINVAL;  // grid too large for the staged slab at this step angle
     std::unique_ptr<Instance, void (*)(Instance*)> I(new (std::nothrow) Instance(), destroy_instance);
     if (!I) return VFPS_ENOMEM;
@@ -373,6 +398,7 @@ int create_instance(const vfps_params* p, const double* psi0, int ring, cudaStre
     I->ld = (int)align_up(p->n, 16 / elem_size(p));
     I->M = fft_length(p);
     I->W = W;
+    I->fast = fast;
     I->ntiles = (p->n + W - 1) / W;
     I->ring = ring;
     I->delta = 2.0 * p->half_width / (p->n - 1);
@@ -440,7 +466,7 @@ int create_instance(const vfps_params* p, const double* psi0, int ring, cudaStre
 // Launch groups: instances with equal (precision, N_I, W) advance in one
 // launch per step.  The tile table lists (instance, first column) per CTA.
 struct Group {
-    int prec = 0, ni = 4, W = 8;
+    int prec = 0, ni = 4, W = 8, fast = 0;
     size_t smem = 0;
     int ntiles = 0;
     void* ddescs = nullptr;  // array of Desc<T>
@@ -488,9 +514,25 @@ int launch_step_ni(const Group& g, cudaStream_t s)
     return VFPS_EINVAL;
 }
 
+template <int W>
+int launch_fast_t(const Group& g, cudaStream_t s)
+{
+    step_kernel_f32<W><<<g.ntiles, W * 32, g.smem, s>>>((const Desc<float>*)g.ddescs, g.dtiles);
+    CU(cudaGetLastError());
+    return VFPS_OK;
+}
+
 int launch_step(const Group& g, cudaStream_t s)
 {
     if (g.ntiles == 0) return VFPS_OK;
+    if (g.fast) {
+        switch (g.W) {
+        case 8: return launch_fast_t<8>(g, s);
+        case 4: return launch_fast_t<4>(g, s);
+        case 2: return launch_fast_t<2>(g, s);
+        }
+        return VFPS_EINVAL;
+    }
     return g.prec ? launch_step_ni<double>(g, s) : launch_step_ni<float>(g, s);
 }
 
@@ -556,6 +598,9 @@ int init_kernels()
     if (lim <= 0) return VFPS_ECUDA;
     CU(set_smem_attr_all<float>(lim));
     CU(set_smem_attr_all<double>(lim));
+    CU(set_smem_attr_one(step_kernel_f32<8>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<4>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<2>, lim));
     g_kernels_ready = 1;
     return VFPS_OK;
 }
@@ -567,7 +612,8 @@ Group single_group(const Instance& I)
     g.prec = I.p.precision;
     g.ni = I.p.interp_points;
     g.W = I.W;
-    g.smem = step_smem(&I.p, I.W);
+    g.fast = I.fast;
+    g.smem = I.fast ? std::max(fast_smem(&I.p, I.W), step_smem(&I.p, I.W)) : step_smem(&I.p, I.W);
     g.ntiles = I.ntiles;
     g.ddescs = I.ddesc;
     g.dtiles = I.dtiles;
@@ -899,13 +945,13 @@ int rebuild_groups(vfps_batch* b)
     std::map<std::tuple<int, int, int, int, int>, std::vector<Instance*>> cls;
     std::map<std::tuple<int, int, int, int>, int> count;
     for (Instance* I : b->slots)
-        if (I && remaining(I) > 0) ++count[{I->p.precision, I->p.interp_points, I->W, I->n}];
+        if (I && remaining(I) > 0) ++count[{I->p.precision, I->p.interp_points * 2 + I->fast, I->W, I->n}];
     std::map<std::tuple<int, int, int, int>, int> seen;
     for (Instance* I : b->slots) {
         if (!I || remaining(I) <= 0) continue;
-        auto key = std::make_tuple(I->p.precision, I->p.interp_points, I->W, I->n);
+        auto key = std::make_tuple(I->p.precision, I->p.interp_points * 2 + I->fast, I->W, I->n);
         int half = (count[key] >= 8 && seen[key]++ >= count[key] / 2) ? 1 : 0;
-        cls[{I->p.precision, I->p.interp_points, I->W, I->n, half}].push_back(I);
+        cls[{I->p.precision, I->p.interp_points * 2 + I->fast, I->W, I->n, half}].push_back(I);
     }
     if (cls.empty()) {
         b->dirty = false;
@@ -944,7 +990,8 @@ int rebuild_groups(vfps_batch* b)
     for (auto& kv : cls) {
         Group g;
         g.prec = std::get<0>(kv.first);
-        g.ni = std::get<1>(kv.first);
+        g.ni = std::get<1>(kv.first) / 2;
+        g.fast = std::get<1>(kv.first) & 1;
         g.W = std::get<2>(kv.first);
         g.stream = b->pool[gi];
         g.ddescs = (unsigned char*)b->gmem + offs[gi].first;
@@ -957,6 +1004,7 @@ int rebuild_groups(vfps_batch* b)
             std::memcpy(host.data() + offs[gi].first + k * dsz, I->hdesc, dsz);
             for (int t = 0; t < I->ntiles; ++t) ht[nt++] = make_int2((int)k, t * I->W);
             g.smem = std::max(g.smem, step_smem(&I->p, I->W));
+            if (g.fast) g.smem = std::max(g.smem, fast_smem(&I->p, I->W));
         }
         g.ntiles = nt;
         b->groups.push_back(g);

@@ -1,0 +1,337 @@
+// vfps_fast.cuh -- FP32 step kernel for the hot configuration (cubic
+// interpolation, no clamp, n a multiple of 4), written to issue few
+// instructions per cell.  Same arithmetic as step_kernel<float, 4, W>:
+// rotation (2-D cubic Lagrange, Sec. III.A-B), kick along p, Fokker-Planck
+// step (Eq. cubic diff), column sums, and the same last-CTA finaliser.
+//
+// Work of one lane: four consecutive rows y0..y0+3 of its warp's column x.
+//  * Rotation.  Along a column the source point moves by (-sin phi, ~1)
+//    cells per row, so the four outputs share one window of 5 source
+//    columns x 12 rows, read with 15 LDS.128.  The y-node offset
+//    floor(dy) is the same for all four rows and, almost always, for the
+//    whole warp (dy changes by cos phi - 1 ~ 1e-5 per row): the window's
+//    row alignment is then warp-uniform and selects a compile-time
+//    register layout.  The x-node may step back by one inside the block
+//    (dx changes by -sin phi per row); a 5-column weight vector with a zero
+//    at one end covers both cases.  A warp whose rows do not meet these
+//    conditions computes its block cell by cell (rotate_cell).
+//  * Kick and Fokker-Planck.  The column's kick shift s + t is uniform, so
+//    psi_b(y0-1..y0+5) comes from one 16-row window of the psi_a column
+//    (zero-padded rows), and psi_c(y0..y0+3) from psi_b and the per-row FP
+//    weights g(y) held in shared memory.  One STG.128 writes the block.
+//  * Pairs of rows go through packed FP32x2 FMAs (__ffma2_rn, sm_100+).
+#pragma once
+#include "vfps_kernels.cuh"
+
+namespace vfps {
+
+constexpr int kColPad = 16;  // zero rows above and below each psi_a column
+
+// Row padding of the staged slab: covers the largest y-node offset plus the
+// 12-row window, rounded to a multiple of 4 for 16-byte rows.
+__host__ __device__ inline int fast_row_pad(int h) { return ((h + 4 + 3) / 4) * 4; }
+
+__host__ inline size_t fast_smem_bytes(int n, int h, int W)
+{
+    int RP = fast_row_pad(h);
+    size_t slab = (size_t)(W + 2 * h) * (n + 2 * RP) * 4;
+    size_t cols = (size_t)W * (n + 2 * kColPad) * 4;
+    size_t gtab = (size_t)n * 16;
+    return slab + cols + gtab;
+}
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+// Cubic Lagrange weights (nodes -1, 0, 1, 2) for two fractions at once.
+__device__ __forceinline__ void lagrange2(float2 t, float2 w[4])
+{
+    const float2 one = f2(1.f, 1.f), two = f2(2.f, 2.f);
+    float2 tm1 = __fadd2_rn(t, f2(-1.f, -1.f));
+    float2 tm2 = __fadd2_rn(t, f2(-2.f, -2.f));
+    float2 tp1 = __fadd2_rn(t, one);
+    float2 a = __fmul2_rn(t, tm1);
+    float2 b = __fmul2_rn(tp1, t);
+    w[0] = __fmul2_rn(__fmul2_rn(a, tm2), f2(-1.f / 6.f, -1.f / 6.f));
+    w[1] = __fmul2_rn(__fmul2_rn(__fmul2_rn(tp1, tm1), tm2), f2(0.5f, 0.5f));
+    w[2] = __fmul2_rn(__fmul2_rn(b, tm2), f2(-0.5f, -0.5f));
+    w[3] = __fmul2_rn(__fmul2_rn(b, tm1), f2(1.f / 6.f, 1.f / 6.f));
+    (void)two;
+}
+
+// Rotation of four rows from a 5 x 12 register window whose first row is
+// O rows above the first stencil row of output 0.  tx, ty hold the node
+// fractions of rows (0,1) and (2,3) as pairs (packed weight arithmetic).
+template <int O>
+__device__ __forceinline__ void rotate_block(const float* __restrict__ colbase, int P, float2 tx01, float2 tx23,
+                                             float2 ty01, float2 ty23, bool e1, bool e2, bool e3, float out[4])
+{
+    float2 wy01[4], wy23[4], wx01[4], wx23[4];
+    lagrange2(ty01, wy01);
+    lagrange2(ty23, wy23);
+    lagrange2(tx01, wx01);
+    lagrange2(tx23, wx23);
+    const float wy[4][4] = {{wy01[0].x, wy01[1].x, wy01[2].x, wy01[3].x},
+                            {wy01[0].y, wy01[1].y, wy01[2].y, wy01[3].y},
+                            {wy23[0].x, wy23[1].x, wy23[2].x, wy23[3].x},
+                            {wy23[0].y, wy23[1].y, wy23[2].y, wy23[3].y}};
+    // x-weights over the 5 window columns: output k uses columns 1..4 when its
+    // x-node equals row 0's, columns 0..3 when it stepped back by one
+    const float wx[4][4] = {{wx01[0].x, wx01[1].x, wx01[2].x, wx01[3].x},
+                            {wx01[0].y, wx01[1].y, wx01[2].y, wx01[3].y},
+                            {wx23[0].x, wx23[1].x, wx23[2].x, wx23[3].x},
+                            {wx23[0].y, wx23[1].y, wx23[2].y, wx23[3].y}};
+    const bool e[4] = {false, e1, e2, e3};
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int a = 0; a < 5; ++a) {
+        const float4* cp = reinterpret_cast<const float4*>(colbase + a * P);
+        const float4 q0 = cp[0], q1 = cp[1], q2 = cp[2];
+        const float win[12] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, q2.x, q2.y, q2.z, q2.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float r = wy[k][0] * win[O + k];
+            r = fmaf(wy[k][1], win[O + k + 1], r);
+            r = fmaf(wy[k][2], win[O + k + 2], r);
+            r = fmaf(wy[k][3], win[O + k + 3], r);
+            const float wa = e[k] ? ((a <= 3) ? wx[k][a] : 0.f) : ((a >= 1) ? wx[k][a - 1] : 0.f);
+            acc[k] = fmaf(wa, r, acc[k]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) out[k] = acc[k];
+}
+
+// Kick + Fokker-Planck for the lane's row blocks of one column; the psi_a
+// window starts O2 rows above the first row the kick of row y0-1 needs.
+template <int O2>
+__device__ __forceinline__ float kick_fp_column(const float* __restrict__ colA_col, const float4* __restrict__ gtab,
+                                                float* __restrict__ dst, int n, int s, int A2,
+                                                const float w[4], int lane)
+{
+    float lsum = 0.f;
+    for (int y0 = 4 * lane; y0 < n; y0 += 128) {
+        const float4* wp = reinterpret_cast<const float4*>(colA_col + y0 + A2 - O2);
+        float4 q0 = wp[0], q1 = wp[1], q2 = wp[2], q3 = wp[3];
+        const float win[16] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w,
+                               q2.x, q2.y, q2.z, q2.w, q3.x, q3.y, q3.z, q3.w};
+        // psi_b(y0 + j - 1), j = 0..6: nodes y0+j+s-2 .. y0+j+s+1
+        float b[7];
+#pragma unroll
+        for (int j = 0; j < 7; ++j) {
+            float v = w[0] * win[O2 + j];
+            v = fmaf(w[1], win[O2 + j + 1], v);
+            v = fmaf(w[2], win[O2 + j + 2], v);
+            b[j] = fmaf(w[3], win[O2 + j + 3], v);
+        }
+        // zero psi_b off the grid and where the kick source is > 1 cell outside
+#pragma unroll
+        for (int j = 0; j < 7; ++j) {
+            int y = y0 + j - 1;
+            int m = y + s;
+            bool ok = (y >= 0) && (y < n) && (m >= -1) && (m <= n - 1);
+            b[j] = ok ? b[j] : 0.f;
+        }
+        float c[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float4 g = gtab[y0 + k];
+            float inc = g.x * b[k] + g.y * b[k + 1] + g.z * b[k + 2] + g.w * b[k + 3];
+            c[k] = b[k + 1] + inc;
+        }
+        *reinterpret_cast<float4*>(dst + y0) = make_float4(c[0], c[1], c[2], c[3]);
+        lsum += (c[0] + c[1]) + (c[2] + c[3]);
+    }
+    return lsum;
+}
+
+// ----------------------------------------------------------------------------
+// Asynchronous 16-byte global -> shared copy (Ampere-style cp.async); with
+// src_bytes = 0 nothing is read and the 16 bytes are zero-filled.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc, int src_bytes)
+{
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gsrc), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// One CTA per tile (W columns of one instance).  The slab is staged with
+// cp.async, so all of a CTA's loads are in flight at once; the pending scale
+// multiplies psi_a after the rotation instead of the staged psi.
+template <int W>
+__global__ void __launch_bounds__(W * 32, 32 / W)
+step_kernel_f32(const Desc<float>* __restrict__ descs, const int2* __restrict__ tiles)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_last;
+    const int2 tile = tiles[blockIdx.x];
+    const Desc<float>& D = descs[tile.x];
+    const int x0 = tile.y;
+    const int n = D.n, ld = D.ld, h = D.h;
+    const int RP = fast_row_pad(h);
+    const int P = n + 2 * RP;         // slab rows -RP .. n+RP-1
+    const int SW = W + 2 * h;         // slab columns x0-h .. x0+W+h-1
+    const int PA = n + 2 * kColPad;   // psi_a column rows -kColPad .. n+kColPad-1
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    float* slab = reinterpret_cast<float*>(smem);
+    float* colA = slab + SW * P;
+    float4* gtab = reinterpret_cast<float4*>(colA + W * PA);
+
+    const int par = D.st->parity;
+    const float* __restrict__ in = D.psi[par];
+    float* __restrict__ out = D.psi[par ^ 1];
+
+    // stage psi_t: 16-byte asynchronous copies, zero-filled outside the grid
+    const int P4 = P >> 2;
+    for (int cx = warp; cx < SW; cx += W) {
+        const int gx = x0 - h + cx;
+        const bool colok = (gx >= 0 && gx < n);
+        const float* src = in + (size_t)(colok ? gx : 0) * ld;
+        float* dst = slab + cx * P;
+        for (int r4 = lane; r4 < P4; r4 += 32) {
+            const int y = 4 * r4 - RP;
+            const bool ok = colok && y >= 0 && y < n;
+            cp_async16(dst + 4 * r4, src + (ok ? y : 0), ok ? 16 : 0);
+        }
+    }
+    cp_async_commit();
+    for (int i = threadIdx.x; i < W * 2 * kColPad; i += blockDim.x) {
+        const int w = i / (2 * kColPad), r = i % (2 * kColPad);
+        colA[w * PA + (r < kColPad ? r : n + r)] = 0.f;
+    }
+    for (int y = threadIdx.x; y < n; y += blockDim.x) {
+        const float yf = float(y);
+        gtab[y] = make_float4(D.ga[0] + D.gb[0] * yf, D.ga[1] + D.gb[1] * yf, D.ga[2] + D.gb[2] * yf,
+                              D.ga[3] + D.gb[3] * yf);
+    }
+    const float scale = float(D.st->scale);
+    const float cm1 = D.cm1, sn = D.sn, c = D.c;
+    cp_async_wait_0();
+    __syncthreads();
+
+    const int x = x0 + warp;
+    const bool active = x < n;
+    float* ca = colA + warp * PA + kColPad;  // row 0 of this warp's psi_a column
+    if (active) {
+        const float xc = float(x) - c;
+        const float2 sn2 = f2(sn, sn), cm12 = f2(cm1, cm1);
+        const float2 snxc = f2(sn * xc, sn * xc), cmxc = f2(cm1 * xc, cm1 * xc);
+        const int cx0 = x0 - h;
+        for (int y0 = 4 * lane; y0 < n; y0 += 128) {
+            const float yc0 = float(y0) - c;
+            const float2 yc01 = f2(yc0, yc0 + 1.f), yc23 = f2(yc0 + 2.f, yc0 + 3.f);
+            // dx = (cos phi - 1) xc - sin phi yc,  dy = sin phi xc + (cos phi - 1) yc
+            const float2 dx01 = __ffma2_rn(f2(-sn, -sn), yc01, cmxc);
+            const float2 dx23 = __ffma2_rn(f2(-sn, -sn), yc23, cmxc);
+            const float2 dy01 = __ffma2_rn(cm12, yc01, snxc);
+            const float2 dy23 = __ffma2_rn(cm12, yc23, snxc);
+            const float2 fx01 = f2(floorf(dx01.x), floorf(dx01.y)), fx23 = f2(floorf(dx23.x), floorf(dx23.y));
+            const float2 fy01 = f2(floorf(dy01.x), floorf(dy01.y)), fy23 = f2(floorf(dy23.x), floorf(dy23.y));
+            const unsigned mask = __activemask();
+            const int leader = __ffs(mask) - 1;
+            const int FY = int(fy01.x);
+            const int FY0 = __shfl_sync(mask, FY, leader);
+            const bool ok = (fy01.y == fy01.x) && (fy23.x == fy01.x) && (fy23.y == fy01.x) && (FY == FY0) &&
+                            (fx23.y >= fx01.x - 1.f) && (fx01.y <= fx01.x);
+            float r[4];
+            if (__all_sync(mask, ok)) {
+                const int A = FY0 - 1 + RP;
+                const int o = A & 3;
+                const float* colbase = slab + (x + int(fx01.x) - 2 - cx0) * P + y0 + A - o;
+                const float2 tx01 = __fadd2_rn(dx01, f2(-fx01.x, -fx01.y));
+                const float2 tx23 = __fadd2_rn(dx23, f2(-fx23.x, -fx23.y));
+                const float2 ty01 = __fadd2_rn(dy01, f2(-fy01.x, -fy01.x));
+                const float2 ty23 = __fadd2_rn(dy23, f2(-fy01.x, -fy01.x));
+                const bool e1 = fx01.y < fx01.x, e2 = fx23.x < fx01.x, e3 = fx23.y < fx01.x;
+                switch (o) {
+                case 0: rotate_block<0>(colbase, P, tx01, tx23, ty01, ty23, e1, e2, e3, r); break;
+                case 1: rotate_block<1>(colbase, P, tx01, tx23, ty01, ty23, e1, e2, e3, r); break;
+                case 2: rotate_block<2>(colbase, P, tx01, tx23, ty01, ty23, e1, e2, e3, r); break;
+                default: rotate_block<3>(colbase, P, tx01, tx23, ty01, ty23, e1, e2, e3, r); break;
+                }
+                // sources more than one cell outside the grid give 0
+                const int mx0 = x + int(fx01.x);
+                const bool inner = (mx0 >= 0) && (mx0 <= n - 1) && (y0 + FY >= -1) && (y0 + 3 + FY <= n - 1);
+                if (!inner) {
+                    const float fxk[4] = {fx01.x, fx01.y, fx23.x, fx23.y};
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int mx = x + int(fxk[k]), my = y0 + k + FY;
+                        if (mx <= -2 || mx >= n || my <= -2 || my >= n) r[k] = 0.f;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    r[k] = rotate_cell<float, 4>(slab + (RP - 2), P, cx0, x, y0 + k, n, cm1, sn, c, 0);
+            }
+            *reinterpret_cast<float4*>(ca + y0) = make_float4(scale * r[0], scale * r[1], scale * r[2], scale * r[3]);
+        }
+    }
+    __syncwarp();
+
+    double csum = 0.0;
+    if (active) {
+        const float ks = -D.kick[x];
+        const float fk = floorf(ks);
+        const int s = int(fk);
+        float w[4];
+        lagrange_w<float, 4>(ks - fk, w);
+        float* dst = out + (size_t)x * ld;
+        float lsum = 0.f;
+        if (s >= -4 && s <= 4) {
+            const int A2 = s - 2 + kColPad;  // column index of row y0+s-2, minus y0
+            const float* colcol = colA + warp * PA;
+            switch (A2 & 3) {
+            case 0: lsum = kick_fp_column<0>(colcol, gtab, dst, n, s, A2, w, lane); break;
+            case 1: lsum = kick_fp_column<1>(colcol, gtab, dst, n, s, A2, w, lane); break;
+            case 2: lsum = kick_fp_column<2>(colcol, gtab, dst, n, s, A2, w, lane); break;
+            default: lsum = kick_fp_column<3>(colcol, gtab, dst, n, s, A2, w, lane); break;
+            }
+        } else {
+            // large kick: plain per-row evaluation with bounds
+            for (int y = lane; y < n; y += 32) {
+                float b[4];
+#pragma unroll
+                for (int d = 0; d < 4; ++d) {
+                    const int yy = y - 1 + d;
+                    const int mm = yy + s;
+                    float v = 0.f;
+                    if (yy >= 0 && yy < n && mm > -2 && mm < n) {
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const int rr = mm - 1 + k;
+                            if (rr >= 0 && rr < n) v += w[k] * ca[rr];
+                        }
+                    }
+                    b[d] = v;
+                }
+                const float4 g = gtab[y];
+                const float v = b[1] + (g.x * b[0] + g.y * b[1] + g.z * b[2] + g.w * b[3]);
+                dst[y] = v;
+                lsum += v;
+            }
+        }
+        csum = double(lsum);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) csum += __shfl_down_sync(0xffffffffu, csum, o);
+        if (lane == 0) {
+            D.colsum[x] = csum;
+            __threadfence();
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned prev = atomicAdd(&D.st->ticket, 1u);
+        s_last = (prev == (unsigned)(D.ntiles - 1));
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        finalise<float>(D, smem, 1);
+    }
+}
+
+}  // namespace vfps
