@@ -132,8 +132,9 @@ int vfps_destroy(vfps_handle* h);
 /* Static description of an error code. */
 const char* vfps_strerror(int code);
 
-/* The calling thread's last failing CUDA call and its message ("" if none);
- * valid until that thread's next library call. */
+/* The calling thread's last failing CUDA call and its message, or the reason
+ * vfps_step_static refused a request ("" if none); valid until that thread's
+ * next library call. */
 const char* vfps_last_cuda_error(void);
 
 /* Host-only (needs no device): the library's FP64 impedance table for a grid,
@@ -143,6 +144,30 @@ const char* vfps_last_cuda_error(void);
  * Errors: EINVAL. */
 int vfps_impedance_table(int model, int32_t n, double half_width, int32_t pad_factor,
                          double Pi, double* out_re_im);
+
+/* One step without allocating device memory.  The paper has no counterpart:
+ * this exists for callers that may not call cudaMalloc -- a plug-in inside an
+ * application whose memory pool owns the device (allocating behind the pool
+ * can fail or fragment it), or a latency-critical loop that cannot take
+ * cudaMalloc's implicit synchronisation and failure path.
+ *   psi_in:  device, n*n FP32 [q][p] row-major (any positive charge);
+ *   psi_out: device, n*n FP32, distinct from psi_in; receives the next state
+ *            normalised to charge 1 (as vfps_step with renormalize = 1);
+ *            both 16-byte aligned when n is a multiple of 4;
+ *   model, Pi, S_csr: as in vfps_set_impedance (models 0-2);
+ *   power_out: host, NULL or one double: P(psi_in); when given, the call
+ *            synchronises the stream and also reports VFPS_ENAN;
+ *   cuda_stream: the stream to queue on (NULL = legacy default stream).
+ * Only precision = 0.  Limits: n <= 1024 and FFT length <= 4096; larger
+ * requests return VFPS_EINVAL with the reason in vfps_last_cuda_error().
+ * Scratch lives in a fixed device array of about 80 KB inside the library
+ * image (held by every GPU that loads the library until exit).  It is looked
+ * up on the first call on each device: make that first call before any
+ * stream capture.  All calls share that array; calls whose work overlaps on
+ * the GPU (other streams or host threads) race on it.  Host-side tables
+ * (impedance, twiddles) use ordinary host memory. */
+int vfps_step_static(const vfps_params* params, int model, double Pi, double S_csr,
+                     const float* psi_in, float* psi_out, double* power_out, void* cuda_stream);
 
 /* ---------------------------------------------------------------------------
  * Batch: many independent simulations of possibly different grid sizes that

@@ -20,6 +20,7 @@
 #include <memory>
 #include <new>
 #include <tuple>
+#include <mutex>
 #include <vector>
 
 #include "../../include/vfps.h"
@@ -1209,3 +1210,190 @@ int vfps_batch_destroy(vfps_batch* b)
 }
 
 }  // extern "C"
+
+// ============================================================================
+// Allocation-free single step (vfps_step_static).
+//
+// Some callers may not allocate device memory at all: plug-ins living inside
+// a host application whose memory pool owns the whole device (an allocation
+// behind the pool's back can fail or fragment it), and latency-critical loops
+// that cannot afford cudaMalloc's implicit synchronisation or its failure
+// path.  This entry point advances one caller-owned FP32 state by one step
+// using only the caller's buffers and a fixed scratch area that lives in the
+// library image itself, so it never calls cudaMalloc or cudaFree.
+//
+// Scratch: g_vfps_static_scratch below (STATIC_SCRATCH_BYTES, about 80 KB),
+// sized for n <= 1024 and an FFT length M <= 4096.  Every GPU that loads the
+// library holds it until the process exits.  All calls share it and it keeps
+// the last call's contents; each call rewrites the parts that must start
+// fresh (descriptor, tile list, state word with its zero ticket, impedance,
+// twiddles), and the column sums, profile and kick are fully overwritten by
+// the kernels before they are read.  Calls whose kernels overlap on the GPU
+// (different streams, or different host threads) race on this scratch.
+namespace {
+
+constexpr int kStaticMaxN = 1024;
+constexpr int kStaticMaxFFT = 4096;
+constexpr size_t kSA = 256;
+constexpr size_t sa(size_t v) { return (v + kSA - 1) / kSA * kSA; }
+constexpr size_t kOffDesc = 0;
+constexpr size_t kOffTiles = kOffDesc + sa(sizeof(Desc<float>));
+constexpr size_t kOffState = kOffTiles + sa(sizeof(int2) * (kStaticMaxN / 2 + 1));
+constexpr size_t kOffColsum = kOffState + sa(sizeof(DevState));
+constexpr size_t kOffRho = kOffColsum + sa(sizeof(double) * kStaticMaxN);
+constexpr size_t kOffKick = kOffRho + sa(sizeof(double) * kStaticMaxN);
+constexpr size_t kOffZhat = kOffKick + sa(sizeof(float) * kStaticMaxN);
+constexpr size_t kOffTw = kOffZhat + sa(sizeof(float2) * (kStaticMaxFFT / 2 + 1));
+constexpr size_t kOffRings = kOffTw + sa(sizeof(float2) * (kStaticMaxFFT / 2));
+constexpr size_t STATIC_SCRATCH_BYTES = kOffRings + sa(sizeof(double) * 4);
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_vfps_static_scratch[STATIC_SCRATCH_BYTES];
+
+namespace {
+
+std::mutex g_static_mu;
+void* g_static_dev_ptr[64] = {};
+// host-side staging of what each call uploads (guarded by g_static_mu)
+unsigned char g_static_host[kOffRings];
+
+// Device address of the scratch on the current device.  In host code the
+// array's name only stands in for it, so it is looked up once per device
+// (with that device current) and cached.
+int static_scratch(void** out)
+{
+    int dev = 0;
+    CU(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return VFPS_EINVAL;
+    if (!g_static_dev_ptr[dev]) {
+        void* p = nullptr;
+        CU(cudaGetSymbolAddress(&p, g_vfps_static_scratch));
+        g_static_dev_ptr[dev] = p;
+    }
+    *out = g_static_dev_ptr[dev];
+    return VFPS_OK;
+}
+
+__global__ void static_scale_kernel(float* psi, int n, const DevState* st)
+{
+    const float s = float(st->scale);
+    const size_t nn = (size_t)n * n;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += (size_t)gridDim.x * blockDim.x)
+        psi[i] *= s;
+}
+
+int static_fail(const char* msg)
+{
+    std::snprintf(g_last_error, sizeof(g_last_error), "%s", msg);
+    return VFPS_EINVAL;
+}
+
+}  // namespace
+
+extern "C" int vfps_step_static(const vfps_params* params, int model, double Pi, double S_csr,
+                                const float* psi_in, float* psi_out, double* power_out, void* cuda_stream)
+{
+    int rc = check_params(params);
+    if (rc) return static_fail("vfps_step_static: invalid parameters");
+    if (params->precision != 0) return static_fail("vfps_step_static: FP32 states only (precision = 0)");
+    if (params->n > kStaticMaxN) {
+        char m[160];
+        std::snprintf(m, sizeof(m), "vfps_step_static: n = %d exceeds the static scratch limit of %d points per axis",
+                      params->n, kStaticMaxN);
+        return static_fail(m);
+    }
+    const int M = fft_length(params);
+    if (M > kStaticMaxFFT) {
+        char m[160];
+        std::snprintf(m, sizeof(m), "vfps_step_static: FFT length %d exceeds the static scratch limit of %d", M,
+                      kStaticMaxFFT);
+        return static_fail(m);
+    }
+    if (!psi_in || !psi_out || psi_in == (const float*)psi_out)
+        return static_fail("vfps_step_static: psi_in and psi_out must be two distinct device buffers");
+    if (model < 0 || model > 2 || (model == 2 && !(Pi > 0.0)) || !std::isfinite(S_csr))
+        return static_fail("vfps_step_static: impedance model 0, 1 or 2 (Pi > 0) and a finite S_csr");
+    int fast = 0;
+    const int W = choose_width(params, &fast);
+    if (W == 0) return static_fail("vfps_step_static: grid too large for the staged slab at this step angle");
+    if (fast && (((uintptr_t)psi_in | (uintptr_t)psi_out) & 15))
+        return static_fail("vfps_step_static: psi buffers must be 16-byte aligned");
+    rc = init_kernels();
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    void* base = nullptr;
+    rc = static_scratch(&base);
+    if (rc) return rc;
+    unsigned char* d = (unsigned char*)base;
+
+    // the simulation's buffers: caller's psi, scratch for everything else
+    Instance I;
+    I.p = *params;
+    I.n = params->n;
+    I.ld = params->n;
+    I.M = M;
+    I.W = W;
+    I.fast = fast;
+    I.ntiles = (params->n + W - 1) / W;
+    I.ring = 2;
+    I.delta = 2.0 * params->half_width / (params->n - 1);
+    I.phi = 2.0 * kPi / params->steps_per_period;
+    I.S = S_csr;
+    I.psi[0] = (void*)psi_in;
+    I.psi[1] = psi_out;
+    I.zhat = d + kOffZhat;
+    I.tw = d + kOffTw;
+    I.colsum = (double*)(d + kOffColsum);
+    I.rho = (double*)(d + kOffRho);
+    I.kick = d + kOffKick;
+    I.pring = (double*)(d + kOffRings);
+    I.qring = (double*)(d + kOffRings) + 2;
+    I.st = (DevState*)(d + kOffState);
+    fill_desc<float>(I);
+
+    // stage the per-call inputs on the host, then upload them
+    unsigned char* h = g_static_host;
+    std::memcpy(h + kOffDesc, I.hdesc, sizeof(Desc<float>));
+    int2* tiles = (int2*)(h + kOffTiles);
+    for (int i = 0; i < I.ntiles; ++i) tiles[i] = make_int2(0, i * W);
+    DevState st{};
+    st.scale = 1.0;
+    std::memcpy(h + kOffState, &st, sizeof(st));
+    std::vector<std::complex<double>> z;
+    cached_impedance(model, M, I.delta, Pi, z);
+    float2* zh = (float2*)(h + kOffZhat);
+    for (int k = 0; k <= M / 2; ++k) zh[k] = make_float2((float)z[k].real(), (float)z[k].imag());
+    float2* tw = (float2*)(h + kOffTw);
+    for (int k = 0; k < M / 2; ++k) {
+        const double ang = -2.0 * kPi * k / M;
+        tw[k] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+    }
+    CU(cudaMemcpyAsync(d, h, kOffRings, cudaMemcpyHostToDevice, s));
+
+    Group g;
+    g.prec = 0;
+    g.ni = params->interp_points;
+    g.W = W;
+    g.fast = fast;
+    g.ntiles = I.ntiles;
+    g.smem = fast ? std::max(fast_smem(params, W), step_smem(params, W)) : step_smem(params, W);
+    g.ddescs = d + kOffDesc;
+    g.dtiles = (int2*)(d + kOffTiles);
+    rc = launch_project(g, s);   // profile, wake and P of psi_in
+    if (rc) return rc;
+    rc = launch_step(g, s);      // psi_out = one un-normalised step
+    if (rc) return rc;
+    static_scale_kernel<<<std::min(1024, (I.n * I.n + 255) / 256), 256, 0, s>>>(psi_out, I.n, I.st);
+    CU(cudaGetLastError());
+    if (power_out) {
+        DevState out{};
+        CU(cudaMemcpyAsync(power_out, I.pring, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CU(cudaMemcpyAsync(&out, I.st, sizeof(out), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        if (out.status) return out.status;
+    }
+    return VFPS_OK;
+}

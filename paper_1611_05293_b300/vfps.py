@@ -26,7 +26,7 @@ EXPORTS = [
     "vfps_steps_done", "vfps_destroy", "vfps_strerror", "vfps_last_cuda_error", "vfps_impedance_table",
     "vfps_batch_create", "vfps_batch_add", "vfps_batch_slot_bytes", "vfps_batch_run",
     "vfps_batch_poll", "vfps_batch_take", "vfps_batch_remove", "vfps_batch_usage",
-    "vfps_batch_destroy",
+    "vfps_batch_destroy", "vfps_step_static",
 ]
 
 
@@ -113,6 +113,8 @@ def lib() -> ctypes.CDLL:
         "vfps_batch_remove": (ctypes.c_int, [_VP, _I32]),
         "vfps_batch_usage": (ctypes.c_int, [_VP, ctypes.POINTER(_I32), ctypes.POINTER(_I64)]),
         "vfps_batch_destroy": (ctypes.c_int, [_VP]),
+        "vfps_step_static": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_double, ctypes.c_double, _VP, _VP,
+                                            _D, _VP]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -321,3 +323,17 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def step_static(params: Params, model: int, Pi: float, S_csr: float, psi_in_ptr: int, psi_out_ptr: int,
+                stream=None, want_power: bool = True):
+    """vfps_step_static on caller-owned device buffers (raw device pointers).
+    Returns P(psi_in) when want_power (the call then synchronises)."""
+    p = ctypes.c_double()
+    rc = lib().vfps_step_static(ctypes.byref(params.c()), model, Pi, S_csr, ctypes.c_void_p(psi_in_ptr),
+                                ctypes.c_void_p(psi_out_ptr), ctypes.byref(p) if want_power else None,
+                                _stream_ptr(stream))
+    if rc != OK:
+        msg = lib().vfps_last_cuda_error().decode()
+        raise VfpsError(rc, f"vfps_step_static [{msg}]")
+    return p.value if want_power else None
