@@ -139,7 +139,20 @@ size_t fast_smem(const vfps_params* p, int W)
 {
     int M = fft_length(p);
     size_t fin = (size_t)(M + M / 2) * 8 + (size_t)W * 32 * 8;
-    return align_up(std::max(vfps::fast_smem_bytes(p->n, halo_for(p), W), fin), 16);
+    return align_up(std::max(vfps::fast_ring_smem(p->n, halo_for(p), W), fin), 16);
+}
+
+int g_num_sms = 0;
+
+int num_sms()
+{
+    if (g_num_sms <= 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            g_num_sms = 1;
+    }
+    return g_num_sms;
 }
 
 // CTA width: the widest of 8, 4, 2 columns whose shared memory fits (the
@@ -468,6 +481,7 @@ int create_instance(const vfps_params* p, const double* psi0, int ring, cudaStre
 // launch per step.  The tile table lists (instance, first column) per CTA.
 struct Group {
     int prec = 0, ni = 4, W = 8, fast = 0;
+    int tps = 1;  // FP32 streaming kernel: consecutive tiles per CTA
     size_t smem = 0;
     int ntiles = 0;
     void* ddescs = nullptr;  // array of Desc<T>
@@ -518,7 +532,7 @@ int launch_step_ni(const Group& g, cudaStream_t s)
 template <int W>
 int launch_fast_t(const Group& g, cudaStream_t s)
 {
-    step_kernel_f32<W><<<g.ntiles, W * 32, g.smem, s>>>((const Desc<float>*)g.ddescs, g.dtiles);
+    step_kernel_f32<W><<<g.ntiles / g.tps, W * 32, g.smem, s>>>((const Desc<float>*)g.ddescs, g.dtiles, g.tps);
     CU(cudaGetLastError());
     return VFPS_OK;
 }
@@ -1008,6 +1022,21 @@ int rebuild_groups(vfps_batch* b)
             if (g.fast) g.smem = std::max(g.smem, fast_smem(&I->p, I->W));
         }
         g.ntiles = nt;
+        if (g.fast) {
+            // a strip of tps consecutive tiles per CTA: the largest divisor of
+            // the tiles per instance that still leaves ~3 CTAs per resident slot
+            const int per_inst = kv.second[0]->ntiles;
+            const int target = 3 * 4 * num_sms();
+            for (int t = per_inst; t >= 1; --t)
+                if (per_inst % t == 0 && (t == 1 || nt / t >= target)) {
+                    g.tps = t;
+                    break;
+                }
+            for (size_t k = 0; k < kv.second.size(); ++k) {
+                Desc<float>* dd = (Desc<float>*)(host.data() + offs[gi].first + k * sizeof(Desc<float>));
+                dd->ntiles = per_inst / g.tps;
+            }
+        }
         b->groups.push_back(g);
         ++gi;
     }

@@ -58,12 +58,14 @@ __device__ __forceinline__ void lagrange2(float2 t, float2 w[4])
     (void)two;
 }
 
-// Rotation of four rows from a 5 x 12 register window whose first row is
-// O rows above the first stencil row of output 0.  tx, ty hold the node
-// fractions of rows (0,1) and (2,3) as pairs (packed weight arithmetic).
+// Rotation of four rows from a 5 x 12 register window: 5 consecutive slab
+// columns (ring slots slot0.., row offset rowoff) whose first row is O rows
+// above the first stencil row of output 0.  tx, ty hold the node fractions
+// of rows (0,1) and (2,3) as pairs (packed weight arithmetic).
 template <int O>
-__device__ __forceinline__ void rotate_block(const float* __restrict__ colbase, int P, float2 tx01, float2 tx23,
-                                             float2 ty01, float2 ty23, bool e1, bool e2, bool e3, float out[4])
+__device__ __forceinline__ void rotate_block(const float* __restrict__ ring, int slot0, int R, int P, int rowoff,
+                                             float2 tx01, float2 tx23, float2 ty01, float2 ty23, bool e1,
+                                             bool e2, bool e3, float out[4])
 {
     float2 wy01[4], wy23[4], wx01[4], wx23[4];
     lagrange2(ty01, wy01);
@@ -84,7 +86,7 @@ __device__ __forceinline__ void rotate_block(const float* __restrict__ colbase, 
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int a = 0; a < 5; ++a) {
-        const float4* cp = reinterpret_cast<const float4*>(colbase + a * P);
+        const float4* cp = reinterpret_cast<const float4*>(ring + ((slot0 + a) & (R - 1)) * P + rowoff);
         const float4 q0 = cp[0], q1 = cp[1], q2 = cp[2];
         const float win[12] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, q2.x, q2.y, q2.z, q2.w};
 #pragma unroll
@@ -156,46 +158,149 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-// One CTA per tile (W columns of one instance).  The slab is staged with
-// cp.async, so all of a CTA's loads are in flight at once; the pending scale
-// multiplies psi_a after the rotation instead of the staged psi.
+// Rotation of one cell from the column ring (general path; same arithmetic
+// as rotate_cell, with slab column col stored in ring slot col & (R-1)).
+__device__ __forceinline__ float rotate_cell_ring(const float* __restrict__ ring, int R, int P, int RP, int x, int y,
+                                                  int n, float cm1, float sn, float c)
+{
+    const float xc = float(x) - c, yc = float(y) - c;
+    const float dx = cm1 * xc - sn * yc;
+    const float dy = sn * xc + cm1 * yc;
+    const float fx = floorf(dx), fy = floorf(dy);
+    const int mx = x + int(fx), my = y + int(fy);
+    if (mx <= -2 || mx >= n || my <= -2 || my >= n) return 0.f;
+    float wx[4], wy[4];
+    lagrange_w<float, 4>(dx - fx, wx);
+    lagrange_w<float, 4>(dy - fy, wy);
+    float acc = 0.f;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const float* col = ring + ((mx - 1 + a) & (R - 1)) * P + (my - 1 + RP);
+        float r = 0.f;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) r += wy[b] * col[b];
+        acc += wx[a] * r;
+    }
+    return acc;
+}
+
+// Issue cp.async copies of slab columns col0 .. col0+ncols-1 into their ring
+// slots: rows 0 .. n-1 only (the RP padding rows above and below stay zero
+// from the CTA's start); columns outside the grid are zero-filled.  Warp w
+// takes columns col0+w, col0+w+W, ...
+template <int W>
+__device__ __forceinline__ void load_columns(float* ring, int R, int P, int RP, const float* __restrict__ in,
+                                             int ld, int n, int col0, int ncols)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n4 = n >> 2;
+    for (int k = warp; k < ncols; k += W) {
+        const int gx = col0 + k;
+        float* dst = ring + (size_t)(gx & (R - 1)) * P + RP + 4 * lane;
+        if (gx >= 0 && gx < n) {
+            const float* src = in + (size_t)gx * ld + 4 * lane;
+            for (int r4 = lane; r4 < n4; r4 += 32, dst += 128, src += 128) cp_async16(dst, src, 16);
+        } else {
+            for (int r4 = lane; r4 < n4; r4 += 32, dst += 128)
+                *reinterpret_cast<float4*>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+}
+
+__host__ __device__ inline int ring_slots(int W, int h)
+{
+    int r = 1;
+    while (r < 2 * W + 2 * h) r <<= 1;
+    return r;
+}
+
+__host__ inline size_t fast_ring_smem(int n, int h, int W)
+{
+    const int RP = fast_row_pad(h);
+    return (size_t)ring_slots(W, h) * (n + 2 * RP) * 4 + (size_t)W * (n + 2 * kColPad) * 4 + (size_t)n * 16;
+}
+
+// Rotation of one column x (rows 0..n-1, four per lane and pass) when the
+// y-node offset FY is the same on every row (window alignment O = A & 3,
+// A = FY - 1 + RP) and the x-node steps back by at most one inside a block
+// of four rows (sin phi < 1/3).
+template <int O>
+__device__ __forceinline__ void rotate_column(const float* __restrict__ ring, int R, int P, int RP, int A,
+                                              float* __restrict__ ca, int x, int n, int lane, float xc, float c,
+                                              float sn, float cm1, int FY, float scale)
+{
+    const float2 msn2 = f2(-sn, -sn), cm12 = f2(cm1, cm1);
+    const float2 snxc = f2(sn * xc, sn * xc), cmxc = f2(cm1 * xc, cm1 * xc);
+    const float fyf = float(FY);
+    const float2 mfy = f2(-fyf, -fyf);
+    for (int y0 = 4 * lane; y0 < n; y0 += 128) {
+        const float yc0 = float(y0) - c;
+        const float2 yc01 = f2(yc0, yc0 + 1.f), yc23 = f2(yc0 + 2.f, yc0 + 3.f);
+        // dx = (cos phi - 1) xc - sin phi yc,  dy = sin phi xc + (cos phi - 1) yc
+        const float2 dx01 = __ffma2_rn(msn2, yc01, cmxc);
+        const float2 dx23 = __ffma2_rn(msn2, yc23, cmxc);
+        const float2 ty01 = __fadd2_rn(__ffma2_rn(cm12, yc01, snxc), mfy);
+        const float2 ty23 = __fadd2_rn(__ffma2_rn(cm12, yc23, snxc), mfy);
+        const float fx0 = floorf(dx01.x), fx1 = floorf(dx01.y), fx2 = floorf(dx23.x), fx3 = floorf(dx23.y);
+        const float2 tx01 = f2(dx01.x - fx0, dx01.y - fx1), tx23 = f2(dx23.x - fx2, dx23.y - fx3);
+        const int mx0 = x + int(fx0);
+        float r[4];
+        rotate_block<O>(ring, (mx0 - 2) & (R - 1), R, P, y0 + A - O, tx01, tx23, ty01, ty23, fx1 < fx0, fx2 < fx0,
+                        fx3 < fx0, r);
+        // sources more than one cell outside the grid give 0
+        if (!((mx0 >= 0) && (mx0 <= n - 1) && (y0 + FY >= -1) && (y0 + 3 + FY <= n - 1))) {
+            const float fxk[4] = {fx0, fx1, fx2, fx3};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int mx = x + int(fxk[k]), my = y0 + k + FY;
+                if (mx <= -2 || mx >= n || my <= -2 || my >= n) r[k] = 0.f;
+            }
+        }
+        *reinterpret_cast<float4*>(ca + y0) = make_float4(scale * r[0], scale * r[1], scale * r[2], scale * r[3]);
+    }
+}
+
+// Streaming FP32 step.  CTA b takes the strip of tps consecutive W-column
+// tiles tiles[b*tps .. b*tps+tps-1] (one instance, consecutive columns) and
+// walks it tile by tile.  The slab columns live in a ring of R shared-memory
+// slots (R >= 2W + 2h): while tile j is computed, the W new columns of tile
+// j+1 are resident or landing and those of tile j+2 are requested, so each
+// column of psi is read from HBM once per strip and the copies overlap the
+// arithmetic.  The pending scale multiplies psi_a after the rotation.
 template <int W>
 __global__ void __launch_bounds__(W * 32, 32 / W)
-step_kernel_f32(const Desc<float>* __restrict__ descs, const int2* __restrict__ tiles)
+step_kernel_f32(const Desc<float>* __restrict__ descs, const int2* __restrict__ tiles, int tps)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_last;
-    const int2 tile = tiles[blockIdx.x];
-    const Desc<float>& D = descs[tile.x];
-    const int x0 = tile.y;
+    const int2 first = tiles[blockIdx.x * tps];
+    const Desc<float>& D = descs[first.x];
+    const int xs = first.y;
     const int n = D.n, ld = D.ld, h = D.h;
     const int RP = fast_row_pad(h);
-    const int P = n + 2 * RP;         // slab rows -RP .. n+RP-1
-    const int SW = W + 2 * h;         // slab columns x0-h .. x0+W+h-1
-    const int PA = n + 2 * kColPad;   // psi_a column rows -kColPad .. n+kColPad-1
+    const int P = n + 2 * RP;
+    const int R = ring_slots(W, h);
+    const int PA = n + 2 * kColPad;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int T = min(tps, (n - xs + W - 1) / W);
 
-    float* slab = reinterpret_cast<float*>(smem);
-    float* colA = slab + SW * P;
+    float* ring = reinterpret_cast<float*>(smem);
+    float* colA = ring + R * P;
     float4* gtab = reinterpret_cast<float4*>(colA + W * PA);
 
     const int par = D.st->parity;
     const float* __restrict__ in = D.psi[par];
     float* __restrict__ out = D.psi[par ^ 1];
 
-    // stage psi_t: 16-byte asynchronous copies, zero-filled outside the grid
-    const int P4 = P >> 2;
-    for (int cx = warp; cx < SW; cx += W) {
-        const int gx = x0 - h + cx;
-        const bool colok = (gx >= 0 && gx < n);
-        const float* src = in + (size_t)(colok ? gx : 0) * ld;
-        float* dst = slab + cx * P;
-        for (int r4 = lane; r4 < P4; r4 += 32) {
-            const int y = 4 * r4 - RP;
-            const bool ok = colok && y >= 0 && y < n;
-            cp_async16(dst + 4 * r4, src + (ok ? y : 0), ok ? 16 : 0);
-        }
+    // padding rows of every ring slot: zero for the whole strip
+    for (int i = threadIdx.x; i < R * 2 * RP; i += blockDim.x) {
+        const int slot = i / (2 * RP), r = i % (2 * RP);
+        ring[slot * P + (r < RP ? r : n + r)] = 0.f;
     }
+    // window of tile 0, then the new columns of tile 1
+    load_columns<W>(ring, R, P, RP, in, ld, n, xs - h, W + 2 * h);
+    cp_async_commit();
+    if (T > 1) load_columns<W>(ring, R, P, RP, in, ld, n, xs + W + h, W);
     cp_async_commit();
     for (int i = threadIdx.x; i < W * 2 * kColPad; i += blockDim.x) {
         const int w = i / (2 * kColPad), r = i % (2 * kColPad);
@@ -208,120 +313,88 @@ step_kernel_f32(const Desc<float>* __restrict__ descs, const int2* __restrict__ 
     }
     const float scale = float(D.st->scale);
     const float cm1 = D.cm1, sn = D.sn, c = D.c;
-    cp_async_wait_0();
-    __syncthreads();
 
-    const int x = x0 + warp;
-    const bool active = x < n;
-    float* ca = colA + warp * PA + kColPad;  // row 0 of this warp's psi_a column
-    if (active) {
-        const float xc = float(x) - c;
-        const float2 sn2 = f2(sn, sn), cm12 = f2(cm1, cm1);
-        const float2 snxc = f2(sn * xc, sn * xc), cmxc = f2(cm1 * xc, cm1 * xc);
-        const int cx0 = x0 - h;
-        for (int y0 = 4 * lane; y0 < n; y0 += 128) {
-            const float yc0 = float(y0) - c;
-            const float2 yc01 = f2(yc0, yc0 + 1.f), yc23 = f2(yc0 + 2.f, yc0 + 3.f);
-            // dx = (cos phi - 1) xc - sin phi yc,  dy = sin phi xc + (cos phi - 1) yc
-            const float2 dx01 = __ffma2_rn(f2(-sn, -sn), yc01, cmxc);
-            const float2 dx23 = __ffma2_rn(f2(-sn, -sn), yc23, cmxc);
-            const float2 dy01 = __ffma2_rn(cm12, yc01, snxc);
-            const float2 dy23 = __ffma2_rn(cm12, yc23, snxc);
-            const float2 fx01 = f2(floorf(dx01.x), floorf(dx01.y)), fx23 = f2(floorf(dx23.x), floorf(dx23.y));
-            const float2 fy01 = f2(floorf(dy01.x), floorf(dy01.y)), fy23 = f2(floorf(dy23.x), floorf(dy23.y));
-            const unsigned mask = __activemask();
-            const int leader = __ffs(mask) - 1;
-            const int FY = int(fy01.x);
-            const int FY0 = __shfl_sync(mask, FY, leader);
-            const bool ok = (fy01.y == fy01.x) && (fy23.x == fy01.x) && (fy23.y == fy01.x) && (FY == FY0) &&
-                            (fx23.y >= fx01.x - 1.f) && (fx01.y <= fx01.x);
-            float r[4];
-            if (__all_sync(mask, ok)) {
-                const int A = FY0 - 1 + RP;
-                const int o = A & 3;
-                const float* colbase = slab + (x + int(fx01.x) - 2 - cx0) * P + y0 + A - o;
-                const float2 tx01 = __fadd2_rn(dx01, f2(-fx01.x, -fx01.y));
-                const float2 tx23 = __fadd2_rn(dx23, f2(-fx23.x, -fx23.y));
-                const float2 ty01 = __fadd2_rn(dy01, f2(-fy01.x, -fy01.x));
-                const float2 ty23 = __fadd2_rn(dy23, f2(-fy01.x, -fy01.x));
-                const bool e1 = fx01.y < fx01.x, e2 = fx23.x < fx01.x, e3 = fx23.y < fx01.x;
-                switch (o) {
-                case 0: rotate_block<0>(colbase, P, tx01, tx23, ty01, ty23, e1, e2, e3, r); break;
-                case 1: rotate_block<1>(colbase, P, tx01, tx23, ty01, ty23, e1, e2, e3, r); break;
-                case 2: rotate_block<2>(colbase, P, tx01, tx23, ty01, ty23, e1, e2, e3, r); break;
-                default: rotate_block<3>(colbase, P, tx01, tx23, ty01, ty23, e1, e2, e3, r); break;
-                }
-                // sources more than one cell outside the grid give 0
-                const int mx0 = x + int(fx01.x);
-                const bool inner = (mx0 >= 0) && (mx0 <= n - 1) && (y0 + FY >= -1) && (y0 + 3 + FY <= n - 1);
-                if (!inner) {
-                    const float fxk[4] = {fx01.x, fx01.y, fx23.x, fx23.y};
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const int mx = x + int(fxk[k]), my = y0 + k + FY;
-                        if (mx <= -2 || mx >= n || my <= -2 || my >= n) r[k] = 0.f;
-                    }
+    for (int j = 0; j < T; ++j) {
+        cp_async_wait_1();
+        __syncthreads();
+        const int x = xs + j * W + warp;
+        const bool active = x < n;
+        float* ca = colA + warp * PA + kColPad;
+        if (active) {
+            const float xc = float(x) - c;
+            // dy is linear along the column: floor(dy) is the same on every row
+            // iff it is at the first and the last row
+            const float fy_top = floorf(sn * xc + cm1 * (0.f - c));
+            const float fy_bot = floorf(sn * xc + cm1 * (float(n - 1) - c));
+            if (fy_top == fy_bot && sn < 0.3f) {
+                const int FY = int(fy_top);
+                const int A = FY - 1 + RP;
+                switch (A & 3) {
+                case 0: rotate_column<0>(ring, R, P, RP, A, ca, x, n, lane, xc, c, sn, cm1, FY, scale); break;
+                case 1: rotate_column<1>(ring, R, P, RP, A, ca, x, n, lane, xc, c, sn, cm1, FY, scale); break;
+                case 2: rotate_column<2>(ring, R, P, RP, A, ca, x, n, lane, xc, c, sn, cm1, FY, scale); break;
+                default: rotate_column<3>(ring, R, P, RP, A, ca, x, n, lane, xc, c, sn, cm1, FY, scale); break;
                 }
             } else {
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    r[k] = rotate_cell<float, 4>(slab + (RP - 2), P, cx0, x, y0 + k, n, cm1, sn, c, 0);
+                for (int y = lane; y < n; y += 32)
+                    ca[y] = scale * rotate_cell_ring(ring, R, P, RP, x, y, n, cm1, sn, c);
             }
-            *reinterpret_cast<float4*>(ca + y0) = make_float4(scale * r[0], scale * r[1], scale * r[2], scale * r[3]);
         }
-    }
-    __syncwarp();
-
-    double csum = 0.0;
-    if (active) {
-        const float ks = -D.kick[x];
-        const float fk = floorf(ks);
-        const int s = int(fk);
-        float w[4];
-        lagrange_w<float, 4>(ks - fk, w);
-        float* dst = out + (size_t)x * ld;
-        float lsum = 0.f;
-        if (s >= -4 && s <= 4) {
-            const int A2 = s - 2 + kColPad;  // column index of row y0+s-2, minus y0
-            const float* colcol = colA + warp * PA;
-            switch (A2 & 3) {
-            case 0: lsum = kick_fp_column<0>(colcol, gtab, dst, n, s, A2, w, lane); break;
-            case 1: lsum = kick_fp_column<1>(colcol, gtab, dst, n, s, A2, w, lane); break;
-            case 2: lsum = kick_fp_column<2>(colcol, gtab, dst, n, s, A2, w, lane); break;
-            default: lsum = kick_fp_column<3>(colcol, gtab, dst, n, s, A2, w, lane); break;
-            }
-        } else {
-            // large kick: plain per-row evaluation with bounds
-            for (int y = lane; y < n; y += 32) {
-                float b[4];
-#pragma unroll
-                for (int d = 0; d < 4; ++d) {
-                    const int yy = y - 1 + d;
-                    const int mm = yy + s;
-                    float v = 0.f;
-                    if (yy >= 0 && yy < n && mm > -2 && mm < n) {
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            const int rr = mm - 1 + k;
-                            if (rr >= 0 && rr < n) v += w[k] * ca[rr];
-                        }
-                    }
-                    b[d] = v;
+        __syncwarp();
+        if (active) {
+            const float ks = -D.kick[x];
+            const float fk = floorf(ks);
+            const int s = int(fk);
+            float w[4];
+            lagrange_w<float, 4>(ks - fk, w);
+            float* dst = out + (size_t)x * ld;
+            float lsum = 0.f;
+            if (s >= -4 && s <= 4) {
+                const int A2 = s - 2 + kColPad;  // column index of row y0+s-2, minus y0
+                const float* colcol = colA + warp * PA;
+                switch (A2 & 3) {
+                case 0: lsum = kick_fp_column<0>(colcol, gtab, dst, n, s, A2, w, lane); break;
+                case 1: lsum = kick_fp_column<1>(colcol, gtab, dst, n, s, A2, w, lane); break;
+                case 2: lsum = kick_fp_column<2>(colcol, gtab, dst, n, s, A2, w, lane); break;
+                default: lsum = kick_fp_column<3>(colcol, gtab, dst, n, s, A2, w, lane); break;
                 }
-                const float4 g = gtab[y];
-                const float v = b[1] + (g.x * b[0] + g.y * b[1] + g.z * b[2] + g.w * b[3]);
-                dst[y] = v;
-                lsum += v;
+            } else {
+                // large kick: plain per-row evaluation with bounds
+                for (int y = lane; y < n; y += 32) {
+                    float b[4];
+#pragma unroll
+                    for (int d = 0; d < 4; ++d) {
+                        const int yy = y - 1 + d;
+                        const int mm = yy + s;
+                        float v = 0.f;
+                        if (yy >= 0 && yy < n && mm > -2 && mm < n) {
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) {
+                                const int rr = mm - 1 + k;
+                                if (rr >= 0 && rr < n) v += w[k] * ca[rr];
+                            }
+                        }
+                        b[d] = v;
+                    }
+                    const float4 g = gtab[y];
+                    const float v = b[1] + (g.x * b[0] + g.y * b[1] + g.z * b[2] + g.w * b[3]);
+                    dst[y] = v;
+                    lsum += v;
+                }
+            }
+            double csum = double(lsum);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) csum += __shfl_down_sync(0xffffffffu, csum, o);
+            if (lane == 0) {
+                D.colsum[x] = csum;
+                __threadfence();
             }
         }
-        csum = double(lsum);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) csum += __shfl_down_sync(0xffffffffu, csum, o);
-        if (lane == 0) {
-            D.colsum[x] = csum;
-            __threadfence();
-        }
+        __syncthreads();  // the ring slots of columns xs+jW-h .. xs+jW+W-h-1 are free
+        if (j + 2 < T) load_columns<W>(ring, R, P, RP, in, ld, n, xs + (j + 2) * W + h, W);
+        cp_async_commit();
     }
+    cp_async_wait_0();
     __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned prev = atomicAdd(&D.st->ticket, 1u);

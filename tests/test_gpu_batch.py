@@ -117,3 +117,26 @@ def test_served_stream_results_equal_solo_runs(V):
         assert np.array_equal(r.power, p_a)
     s = stats.summary()
     assert s["p99_s"] >= s["p50_s"] > 0 and s["cell_updates_per_s"] > 0
+
+
+def test_large_batch_uses_strips_and_matches_solo_runs(V):
+    """256 instances of N=256 (two launch groups of 128): the FP32 streaming
+    kernel then walks strips of
+    several tiles per CTA (column ring in shared memory); each slot must still
+    equal its solo run bit for bit."""
+    n, spp, steps = 256, 1000, 3
+    pts = W.scan_grid()
+    b = V.Batch(256)
+    slots = []
+    for i in range(256):
+        S, Pi = pts[i % len(pts)]
+        slots.append(b.add(V.Params(n=n, steps_per_period=spp, beta=1e-2), W.noisy_gaussian(n, 1612 + i % 3),
+                           V.IMPEDANCE_PARALLEL_PLATES, Pi, S, nsteps=steps))
+    b.run(steps)
+    for i in (0, 37, 255):
+        S, Pi = pts[i % len(pts)]
+        r = b.take(slots[i])
+        psi_a, p_a = alone(V, n, spp, S, Pi, steps, W.noisy_gaussian(n, 1612 + i % 3))
+        assert np.array_equal(r["psi"], psi_a), i
+        assert np.array_equal(r["power"], p_a), i
+    b.close()
