@@ -38,6 +38,13 @@ sys.path.insert(0, ROOT)
 
 HBM_FALLBACK_GBS = 6400.0
 
+# DRAM bytes (read + write) of one launch of step_kernel_f32 on a 256-instance
+# N=256 group, from the ncu capture summarised in
+# profiles/step_kernel_f32_batched_n256.md; a step of the 512-instance
+# benchmark is two such launches.  Set to None whenever the kernel changes
+# until a new capture is taken.
+MEASURED_TRAFFIC_PER_LAUNCH = 98.0e6
+
 
 def measured_peaks():
     try:
@@ -118,6 +125,64 @@ def build_batch(V, count, n, spp, beta, stream, seed=1612):
     return b
 
 
+def serving(V, stream, count=48, seed=1613):
+    """Continuous batching of a Poisson stream shaped like the paper's scans:
+    N in {128, 256, 512, 1024}, S in U[0.2, 2], Pi in U[0.5, 4], 1000-4000
+    steps per period, 5-50 periods; arrival rate ~0.9x the batched capacity."""
+    from paper_1611_05293_b300 import workloads as W
+    from paper_1611_05293_b300.serve import Server
+    probe = W.request_stream(count, 1.0, seed)
+    mean_cells = float(np.mean([r.cell_updates for r in probe]))
+    rate = 0.9 * 1.4e11 / mean_cells
+    reqs = W.request_stream(count, rate, seed)
+    srv = Server(max_slots=64, chunk_steps=1000, beta=1e-2, stream=stream, keep_psi=False)
+    stats = srv.run(reqs, realtime=True)
+    srv.close()
+    out = stats.summary()
+    out.update({"arrival_rate_per_s": rate, "unit": "s (time to result)",
+                "workload": f"{count} Poisson requests, N in {{128,256,512,1024}}, 1000-4000 steps/period, "
+                            "5-50 periods, 64 slots"})
+    return out
+
+
+def c3_scan_64(V, torch, stream, warmup, steps=100):
+    """The 64-instance N=256 scan itself: its state (32 MiB) fits in L2, so L2 is
+    flushed (a 256 MiB write) before every timed step and only the steps are timed."""
+    b = build_batch(V, 64, 256, 1000, 1e-2, stream)
+    b.run(warmup)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
+    total = 0.0
+    for _ in range(steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.run(1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total += e0.elapsed_time(e1) / 1e3
+    b.close()
+    return {"value": 64 * 65536 * steps / total, "unit": "cell-updates/s", "ms_per_step": 1e3 * total / steps,
+            "l2": "flushed before every timed step"}
+
+
+def c5_single(V, torch, stream, warmup, steps=400):
+    """Large-grid single simulation: N=1024, 4000 steps/period, Pi=1, S=3."""
+    sim = V.Simulation(V.Params(n=1024, steps_per_period=4000, beta=1e-2), None, stream)
+    sim.set_impedance(V.IMPEDANCE_PARALLEL_PLATES, 1.0, 3.0)
+    sim.step(warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dt = e0.elapsed_time(e1) / 1e3
+    sim.close()
+    return {"value": 1024 * 1024 * steps / dt, "unit": "cell-updates/s", "ms_per_step": 1e3 * dt / steps,
+            "roofline_frac": 8.0 * 1024 * 1024 / (dt / steps) / 1e9 / measured_peaks()[0]}
+
+
 def cpu_baseline(n, spp, beta, budget_s=12.0):
     """FP64 oracle on the host cores: one N=n instance of the scan for as many
     steps as fit in budget_s (after one untimed step)."""
@@ -179,12 +244,13 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--instances", type=int, default=512)
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the serving / C3 / C5 side measurements")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -208,6 +274,7 @@ def main():
     # ---- batched scan (the headline)
     b = build_batch(V, args.instances, n, spp, beta, stream)
     b.run(args.warmup)
+    launches = b.launches_per_step()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -228,7 +295,9 @@ def main():
         dist.barrier()
     cells_step = args.instances * n * n
     value = world * cells_step * args.steps / dt
-    achieved = 8.0 * cells_step / (dt / args.steps) / 1e9  # GB/s, one launch per step
+    # every launch of a step runs concurrently with the others of that step (one
+    # stream each): the algorithmic bytes of all of them over the step time
+    achieved = 8.0 * cells_step / (dt / args.steps) / 1e9  # GB/s
     b.close()
 
     if rank != 0:
@@ -279,13 +348,22 @@ def main():
         "plain": plain,
         "batched_vs_plain": value / world / plain["value"],
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None, "peak_kind": peak_kind,
-                     "algorithmic_bytes_per_cell": 8},
-        "gpu_launches": args.steps,
+                     "frac": achieved / hbm,
+                     "traffic": (MEASURED_TRAFFIC_PER_LAUNCH * launches
+                                 if MEASURED_TRAFFIC_PER_LAUNCH and args.instances == 512 and n == 256 else None),
+                     "traffic_unit": "DRAM bytes per step (all launches of the step, ncu)",
+                     "algorithmic_bytes_per_step": 8 * cells_step,
+                     "peak_kind": peak_kind, "algorithmic_bytes_per_cell": 8},
+        "gpu_launches": args.steps * launches,
+        "launches_per_step": launches,
         "clocks": clk.summary(),
         "e2e": e2e,
         "wall_s_timed": wall,
     }
+    if not args.no_extra:
+        line["serving"] = serving(V, stream)
+        line["c3_scan_64"] = c3_scan_64(V, torch, stream, args.warmup)
+        line["c5_n1024"] = c5_single(V, torch, stream, args.warmup)
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(n, spp, beta)
     print(json.dumps(line))

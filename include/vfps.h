@@ -211,6 +211,11 @@ int vfps_batch_take(vfps_batch* b, int32_t slot, double* psi_out, double* rho_ou
 /* Free a slot (its memory returns to the budget). */
 int vfps_batch_remove(vfps_batch* b, int32_t slot);
 
+/* Kernel launches one batch step takes for the current set of unfinished
+ * slots (one per launch group: precision, interpolation order, CTA width,
+ * grid size; large groups are split in two to overlap their tails). */
+int vfps_batch_launches_per_step(vfps_batch* b, int32_t* launches);
+
 /* Number of active slots and device bytes they hold. */
 int vfps_batch_usage(vfps_batch* b, int32_t* active, int64_t* bytes);
 

@@ -1213,6 +1213,17 @@ int vfps_batch_remove(vfps_batch* b, int32_t slot)
     return VFPS_OK;
 }
 
+int vfps_batch_launches_per_step(vfps_batch* b, int32_t* launches)
+{
+    if (!b || !launches) return VFPS_EINVAL;
+    if (b->dirty) {
+        int rc = rebuild_groups(b);
+        if (rc) return rc;
+    }
+    *launches = (int32_t)b->groups.size();
+    return VFPS_OK;
+}
+
 int vfps_batch_usage(vfps_batch* b, int32_t* active, int64_t* bytes)
 {
     if (!b) return VFPS_EINVAL;

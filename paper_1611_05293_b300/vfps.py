@@ -26,7 +26,7 @@ EXPORTS = [
     "vfps_steps_done", "vfps_destroy", "vfps_strerror", "vfps_last_cuda_error", "vfps_impedance_table",
     "vfps_batch_create", "vfps_batch_add", "vfps_batch_slot_bytes", "vfps_batch_run",
     "vfps_batch_poll", "vfps_batch_take", "vfps_batch_remove", "vfps_batch_usage",
-    "vfps_batch_destroy", "vfps_step_static",
+    "vfps_batch_destroy", "vfps_step_static", "vfps_batch_launches_per_step",
 ]
 
 
@@ -112,6 +112,7 @@ def lib() -> ctypes.CDLL:
                                            ctypes.POINTER(_I64)]),
         "vfps_batch_remove": (ctypes.c_int, [_VP, _I32]),
         "vfps_batch_usage": (ctypes.c_int, [_VP, ctypes.POINTER(_I32), ctypes.POINTER(_I64)]),
+        "vfps_batch_launches_per_step": (ctypes.c_int, [_VP, ctypes.POINTER(_I32)]),
         "vfps_batch_destroy": (ctypes.c_int, [_VP]),
         "vfps_step_static": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_double, ctypes.c_double, _VP, _VP,
                                             _D, _VP]),
@@ -306,6 +307,11 @@ class Batch:
         a, b = _I32(), _I64()
         _check(lib().vfps_batch_usage(self._b, ctypes.byref(a), ctypes.byref(b)), "vfps_batch_usage")
         return a.value, b.value
+
+    def launches_per_step(self) -> int:
+        k = _I32()
+        _check(lib().vfps_batch_launches_per_step(self._b, ctypes.byref(k)), "vfps_batch_launches_per_step")
+        return k.value
 
     def close(self):
         if getattr(self, "_b", None):
