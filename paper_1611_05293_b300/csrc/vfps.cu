@@ -110,8 +110,7 @@ size_t step_smem(const vfps_params* p, int W)
     int h = halo_for(p);
     size_t slab = (size_t)(W + 2 * h) * (p->n + 4) * es;
     size_t cols = (size_t)W * p->n * es;
-    int M = fft_length(p);
-    size_t fin = (size_t)(M + M / 2) * 2 * es + (size_t)W * 32 * 8;
+    size_t fin = vfps::finalise_smem(fft_length(p), p->n, W * 32, 2 * (int)es);
     return align_up(std::max(slab + cols, fin), 16);
 }
 
@@ -137,8 +136,7 @@ bool fast_eligible(const vfps_params* p)
 
 size_t fast_smem(const vfps_params* p, int W)
 {
-    int M = fft_length(p);
-    size_t fin = (size_t)(M + M / 2) * 8 + (size_t)W * 32 * 8;
+    size_t fin = vfps::finalise_smem(fft_length(p), p->n, W * 32, 8);
     return align_up(std::max(vfps::fast_ring_smem(p->n, halo_for(p), W), fin), 16);
 }
 
@@ -155,22 +153,55 @@ int num_sms()
     return g_num_sms;
 }
 
-// CTA width: the widest of 8, 4, 2 columns whose shared memory fits (the
-// kernels also use a few bytes of static shared memory; keep 1 KB for it).
-// *fast is set when the FP32 register-blocked kernel applies and fits.
-int choose_width(const vfps_params* p, int* fast = nullptr)
+int g_smem_per_sm = -1;
+
+int device_smem_per_sm()
 {
-    int lim = device_smem_limit() - 1024;
+    if (g_smem_per_sm < 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess) return 0;
+        g_smem_per_sm = v;
+    }
+    return g_smem_per_sm;
+}
+
+// CTA width in columns (8, 4 or 2) for one kernel: 0 if none fits.  The
+// kernels also use a few bytes of static shared memory; keep 1 KB for it.
+// Batches take the widest width that fits: fewest CTAs and the least halo
+// re-read per column.  With latency set (one simulation on its own) a step
+// lasts as long as its slowest CTA, so the narrowest width is taken whose
+// CTAs still all fit on the device at once (one wave: ceil(n/W) <= SMs x
+// CTAs per SM, the latter limited by shared memory and by 32 CTAs per SM).
+int pick_width(const vfps_params* p, bool fast, bool latency)
+{
+    const long long lim = device_smem_limit() - 1024;
+    const int widths[3] = {8, 4, 2};
+    int best = 0;
+    for (int W : widths) {
+        const long long need = (long long)(fast ? fast_smem(p, W) : step_smem(p, W));
+        if (need > lim) continue;
+        if (!best) best = W;
+        if (latency) {
+            const long long per_sm = std::min<long long>(32, device_smem_per_sm() / (need + 1024));
+            if ((p->n + W - 1) / W <= (long long)num_sms() * per_sm) best = W;
+        }
+    }
+    return best;
+}
+
+// *fast is set when the FP32 register-blocked kernel applies and fits.
+int choose_width(const vfps_params* p, int* fast = nullptr, bool latency = false)
+{
     if (fast) *fast = 0;
-    if (fast_eligible(p))
-        for (int W : {8, 4, 2})
-            if ((long long)fast_smem(p, W) <= lim) {
-                if (fast) *fast = 1;
-                return W;
-            }
-    for (int W : {8, 4, 2})
-        if ((long long)step_smem(p, W) <= lim) return W;
-    return 0;
+    if (fast_eligible(p)) {
+        const int W = pick_width(p, true, latency);
+        if (W) {
+            if (fast) *fast = 1;
+            return W;
+        }
+    }
+    return pick_width(p, false, latency);
 }
 
 // ----------------------------------------------------------------------------
@@ -240,7 +271,7 @@ void fill_desc(Instance& I)
     d.psi[1] = (T*)I.psi[1];
     d.zhat = (const typename C2<T>::type*)I.zhat;
     d.tw = (const typename C2<T>::type*)I.tw;
-    d.colsum = I.colsum;
+    d.colsum = reinterpret_cast<T*>(I.colsum);
     d.rho = I.rho;
     d.kick = (T*)I.kick;
     d.pring = I.pring;
@@ -398,12 +429,13 @@ int upload_impedance(Instance& I, int model, double Pi, double S, const double* 
     return VFPS_OK;
 }
 
-int create_instance(const vfps_params* p, const double* psi0, int ring, cudaStream_t s, Instance** out)
+int create_instance(const vfps_params* p, const double* psi0, int ring, cudaStream_t s, Instance** out,
+                    bool latency = false)
 {
     int rc = check_params(p);
     if (rc) return rc;
     int fast = 0;
-    int W = choose_width(p, &fast);
+    int W = choose_width(p, &fast, latency);
     if (W == 0) return VFPS_EINVAL;  // grid too large for the staged slab at this step angle
     std::unique_ptr<Instance, void (*)(Instance*)> I(new (std::nothrow) Instance(), destroy_instance);
     if (!I) return VFPS_ENOMEM;
@@ -489,21 +521,38 @@ struct Group {
     cudaStream_t stream = nullptr;  // batch groups: their own (forked) stream
 };
 
+// Launch with programmatic stream serialisation: the kernel may start while
+// the previous kernel of the stream finishes; it waits (griddepcontrol.wait)
+// before reading anything that kernel produced.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t s, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 template <typename T, int NI, int W>
 int launch_step_t(const Group& g, cudaStream_t s)
 {
-    auto k = step_kernel<T, NI, W>;
-    k<<<g.ntiles, W * 32, g.smem, s>>>((const Desc<T>*)g.ddescs, g.dtiles);
-    CU(cudaGetLastError());
+    CU(launch_pdl(step_kernel<T, NI, W>, g.ntiles, W * 32, g.smem, s, (const Desc<T>*)g.ddescs,
+                  (const int2*)g.dtiles));
     return VFPS_OK;
 }
 
 template <typename T, int W>
 int launch_project_t(const Group& g, cudaStream_t s)
 {
-    auto k = project_kernel<T, W>;
-    k<<<g.ntiles, W * 32, g.smem, s>>>((const Desc<T>*)g.ddescs, g.dtiles);
-    CU(cudaGetLastError());
+    CU(launch_pdl(project_kernel<T, W>, g.ntiles, W * 32, g.smem, s, (const Desc<T>*)g.ddescs,
+                  (const int2*)g.dtiles));
     return VFPS_OK;
 }
 
@@ -532,8 +581,8 @@ int launch_step_ni(const Group& g, cudaStream_t s)
 template <int W>
 int launch_fast_t(const Group& g, cudaStream_t s)
 {
-    step_kernel_f32<W><<<g.ntiles / g.tps, W * 32, g.smem, s>>>((const Desc<float>*)g.ddescs, g.dtiles, g.tps);
-    CU(cudaGetLastError());
+    CU(launch_pdl(step_kernel_f32<W>, g.ntiles / g.tps, W * 32, g.smem, s, (const Desc<float>*)g.ddescs,
+                  (const int2*)g.dtiles, g.tps));
     return VFPS_OK;
 }
 
@@ -746,7 +795,7 @@ int vfps_create(const vfps_params* params, const double* psi0, void* cuda_stream
     }
     Instance* I = nullptr;
     int rc = init_kernels();
-    if (rc == VFPS_OK) rc = create_instance(params, psi0, kRingDefault, h->stream, &I);
+    if (rc == VFPS_OK) rc = create_instance(params, psi0, kRingDefault, h->stream, &I, true);
     if (rc) {
         if (h->own_stream) cudaStreamDestroy(h->stream);
         return rc;
@@ -1355,7 +1404,7 @@ extern "C" int vfps_step_static(const vfps_params* params, int model, double Pi,
     if (model < 0 || model > 2 || (model == 2 && !(Pi > 0.0)) || !std::isfinite(S_csr))
         return static_fail("vfps_step_static: impedance model 0, 1 or 2 (Pi > 0) and a finite S_csr");
     int fast = 0;
-    const int W = choose_width(params, &fast);
+    const int W = choose_width(params, &fast, true);
     if (W == 0) return static_fail("vfps_step_static: grid too large for the staged slab at this step angle");
     if (fast && (((uintptr_t)psi_in | (uintptr_t)psi_out) & 15))
         return static_fail("vfps_step_static: psi buffers must be 16-byte aligned");

@@ -146,17 +146,7 @@ __device__ __forceinline__ float kick_fp_column(const float* __restrict__ colA_c
     return lsum;
 }
 
-// ----------------------------------------------------------------------------
-// Asynchronous 16-byte global -> shared copy (Ampere-style cp.async); with
-// src_bytes = 0 nothing is read and the 16 bytes are zero-filled.
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc, int src_bytes)
-{
-    unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gsrc), "r"(src_bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 
 // Rotation of one cell from the column ring (general path; same arithmetic
 // as rotate_cell, with slab column col stored in ring slot col & (R-1)).
@@ -287,21 +277,13 @@ step_kernel_f32(const Desc<float>* __restrict__ descs, const int2* __restrict__ 
     float* ring = reinterpret_cast<float*>(smem);
     float* colA = ring + R * P;
     float4* gtab = reinterpret_cast<float4*>(colA + W * PA);
-
-    const int par = D.st->parity;
-    const float* __restrict__ in = D.psi[par];
-    float* __restrict__ out = D.psi[par ^ 1];
+    pdl_trigger();
 
     // padding rows of every ring slot: zero for the whole strip
     for (int i = threadIdx.x; i < R * 2 * RP; i += blockDim.x) {
         const int slot = i / (2 * RP), r = i % (2 * RP);
         ring[slot * P + (r < RP ? r : n + r)] = 0.f;
     }
-    // window of tile 0, then the new columns of tile 1
-    load_columns<W>(ring, R, P, RP, in, ld, n, xs - h, W + 2 * h);
-    cp_async_commit();
-    if (T > 1) load_columns<W>(ring, R, P, RP, in, ld, n, xs + W + h, W);
-    cp_async_commit();
     for (int i = threadIdx.x; i < W * 2 * kColPad; i += blockDim.x) {
         const int w = i / (2 * kColPad), r = i % (2 * kColPad);
         colA[w * PA + (r < kColPad ? r : n + r)] = 0.f;
@@ -311,6 +293,16 @@ step_kernel_f32(const Desc<float>* __restrict__ descs, const int2* __restrict__ 
         gtab[y] = make_float4(D.ga[0] + D.gb[0] * yf, D.ga[1] + D.gb[1] * yf, D.ga[2] + D.gb[2] * yf,
                               D.ga[3] + D.gb[3] * yf);
     }
+    // what the previous step wrote (state word, psi, kick) is read from here on
+    pdl_wait();
+    const int par = D.st->parity;
+    const float* __restrict__ in = D.psi[par];
+    float* __restrict__ out = D.psi[par ^ 1];
+    // window of tile 0, then the new columns of tile 1
+    load_columns<W>(ring, R, P, RP, in, ld, n, xs - h, W + 2 * h);
+    cp_async_commit();
+    if (T > 1) load_columns<W>(ring, R, P, RP, in, ld, n, xs + W + h, W);
+    cp_async_commit();
     const float scale = float(D.st->scale);
     const float cm1 = D.cm1, sn = D.sn, c = D.c;
 
@@ -382,7 +374,7 @@ step_kernel_f32(const Desc<float>* __restrict__ descs, const int2* __restrict__ 
                     lsum += v;
                 }
             }
-            double csum = double(lsum);
+            float csum = lsum;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) csum += __shfl_down_sync(0xffffffffu, csum, o);
             if (lane == 0) {

@@ -11,7 +11,7 @@
 //            ping-pong buffers, device-side parity flips every step
 //   zhat     M/2+1 complex T, dimensionless impedance at kappa_k
 //   tw       M/2 complex T, exp(-2 pi i k/M)
-//   colsum   n doubles, sum_y psi_c[x][y] of the step just written (scratch)
+//   colsum   n values of T, sum_y psi_c[x][y] of the step just written (scratch)
 //   rho      n doubles, profile of the current (renormalised) state
 //   kick     n T, p-shift of column x in grid cells for the next step
 //   pring    ring of CSR powers, pring[t] = P(psi_t)
@@ -46,7 +46,7 @@ struct Desc {
     T* psi[2];
     const typename C2<T>::type* zhat;
     const typename C2<T>::type* tw;
-    double* colsum;
+    T* colsum;                         // n column sums (scratch)
     double* rho;
     T* kick;
     double* pring;
@@ -136,19 +136,41 @@ __device__ __forceinline__ T rotate_cell(const T* __restrict__ slab, int P, int 
 }
 
 // ----------------------------------------------------------------------------
-// Block-wide FP64 sum in a fixed order (deterministic), result to all threads.
-__device__ __forceinline__ double block_sum(double v, double* red)
+// Programmatic dependent launch: a kernel lets the next kernel of its stream
+// start as soon as all its CTAs are running (launch_dependents), and waits for
+// the previous kernel to finish and flush (wait) only before touching what
+// that kernel produced.  Without a programmatic dependency both are no-ops.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// 8- and 16-byte asynchronous global -> shared copies (cp.async).
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc)
 {
-    int tid = threadIdx.x;
-    red[tid] = v;
-    __syncthreads();
-    for (int s = blockDim.x >> 1; s > 0; s >>= 1) {
-        if (tid < s) red[tid] += red[tid + s];
-        __syncthreads();
-    }
-    double r = red[0];
-    __syncthreads();
-    return r;
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc, int src_bytes)
+{
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gsrc), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Sum of v[0..count) in an order fixed by count alone (not by the block
+// size, so a simulation gives the same bits whatever CTA width runs it):
+// lane l adds v[l], v[l+32], ... in order, then a shuffle tree.  Called by
+// one whole warp; v is in shared memory and complete; lane 0 has the sum.
+template <typename T>
+__device__ __forceinline__ T warp_fixed_sum(const T* v, int count)
+{
+    const int lane = threadIdx.x & 31;
+    T acc = T(0);
+    for (int i = lane; i < count; i += 32) acc += v[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    return acc;
 }
 
 template <typename T2> __device__ __forceinline__ T2 cadd(T2 a, T2 b) { return {a.x + b.x, a.y + b.y}; }
@@ -165,106 +187,256 @@ template <typename T2> __device__ __forceinline__ T2 cmulc(T2 a, T2 b)  // a * c
 // ----------------------------------------------------------------------------
 // Finaliser: from the column sums of the state just written, compute the
 // charge, the pending scale, the profile rho, its zero-padded M-point
-// transform, the CSR power, and the wake/kick of the next step.
-//   forward:  decimation-in-frequency radix-2 FFT, natural -> bit-reversed;
-//   multiply by Zhat (Hermitian extension, DC and Nyquist dropped) in the
-//             bit-reversed order, using rho~_{M-k} = conj(rho~_k) for real rho;
-//   inverse:  decimation-in-time radix-2, bit-reversed -> natural.
+// transform, the CSR power, and the wake/kick of the next step
+// (Sec. II.B, Eq. wakepotential; Sec. IV.C for the power).
+//
+// rho is real, so one H = M/2 point complex transform does the work of the
+// M-point one: z_j = rho_2j + i rho_2j+1 is transformed, split into the
+// transforms of the even and odd samples (E_k = (Z_k + conj Z_{H-k})/2,
+// O_k = (Z_k - conj Z_{H-k})/(2i)), and recombined, rho~_k = E_k + w^k O_k,
+// w = exp(-2 pi i/M).  The wake spectrum B_k = Zhat_k rho~_k (k = 1..H-1;
+// DC and Nyquist dropped, B_{M-k} = conj B_k) is folded back the same way,
+// Y_k = (B_k + conj B_{H-k}) + i w^-k (B_k - conj B_{H-k}), so that the
+// inverse H-point transform of Y gives V_2j + i V_2j+1.  Both transforms
+// are Stockham radix-8 passes (a radix-4 or -2 pass last), natural order in
+// and out, one barrier per pass.  Each output element is computed by the
+// same operations whatever thread computes it, and the two sums use the
+// fixed order of warp_fixed_sum, so the bits do not depend on the CTA width.
+//
 // is_step = 1 after a time step (ring slot t+1, t advances); 0 for the
 // prologue that only (re)computes the wake of the current state.
+// Shared memory (bytes) for FFT length M and n columns: two H-point complex
+// buffers, twiddles (H) and impedance (H+1) complex values, the column sums
+// zero-padded to M, H/2+1 power terms and a reduction area.
+__host__ __device__ inline size_t finalise_smem(int M, int n, int nt, int complex_bytes)
+{
+    (void)nt;
+    (void)n;
+    const size_t H = (size_t)M / 2, es = (size_t)complex_bytes / 2;
+    return (4 * H + 2) * complex_bytes + (size_t)M * es + (H / 2 + 4) * es + 64;
+}
+
+template <typename T2, bool INV>
+__device__ __forceinline__ T2 mul_mi(T2 a)  // a * (-i), or a * (+i) for the inverse
+{
+    return INV ? T2{-a.y, a.x} : T2{a.y, -a.x};
+}
+
+template <typename T2, bool INV>
+__device__ __forceinline__ void dft4(T2& x0, T2& x1, T2& x2, T2& x3)
+{
+    const T2 t0 = cadd(x0, x2), t1 = csub(x0, x2), t2 = cadd(x1, x3), t3 = mul_mi<T2, INV>(csub(x1, x3));
+    x0 = cadd(t0, t2);
+    x2 = csub(t0, t2);
+    x1 = cadd(t1, t3);
+    x3 = csub(t1, t3);
+}
+
+// In-register R-point DFT (R = 2, 4, 8), exponent sign - (forward) or +.
+template <typename T, int R, bool INV>
+__device__ __forceinline__ void dft_r(typename C2<T>::type* v)
+{
+    using T2 = typename C2<T>::type;
+    if constexpr (R == 2) {
+        const T2 a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    } else if constexpr (R == 4) {
+        dft4<T2, INV>(v[0], v[1], v[2], v[3]);
+    } else {
+        dft4<T2, INV>(v[0], v[2], v[4], v[6]);  // E_0..E_3 of the even samples
+        dft4<T2, INV>(v[1], v[3], v[5], v[7]);  // O_0..O_3 of the odd samples
+        const T c = T(0.70710678118654752440);  // cos(pi/4)
+        const T2 o1 = v[3], o3 = v[7];
+        const T2 w1 = INV ? T2{c * (o1.x - o1.y), c * (o1.x + o1.y)} : T2{c * (o1.x + o1.y), c * (o1.y - o1.x)};
+        const T2 w2 = mul_mi<T2, INV>(v[5]);
+        const T2 w3 = INV ? T2{-c * (o3.x + o3.y), c * (o3.x - o3.y)} : T2{c * (o3.y - o3.x), -c * (o3.x + o3.y)};
+        const T2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6], o0 = v[1];
+        v[0] = cadd(e0, o0);
+        v[4] = csub(e0, o0);
+        v[1] = cadd(e1, w1);
+        v[5] = csub(e1, w1);
+        v[2] = cadd(e2, w2);
+        v[6] = csub(e2, w2);
+        v[3] = cadd(e3, w3);
+        v[7] = csub(e3, w3);
+    }
+}
+
+// One Stockham pass of an H-point transform: sub-transforms of length Ns are
+// combined R at a time into length Ns*R.  tw[m] = exp(-2 pi i m/M), m < H.
+template <typename T, int R, bool INV>
+__device__ __forceinline__ void fft_pass(const typename C2<T>::type* __restrict__ src,
+                                         typename C2<T>::type* __restrict__ dst,
+                                         const typename C2<T>::type* __restrict__ tw, int H, int Ns)
+{
+    using T2 = typename C2<T>::type;
+    const int Q = H / R;
+    const int mstep = 2 * H / (Ns * R);  // twiddle r*k of this pass is exp(-2 pi i r k mstep/M)
+    for (int j = threadIdx.x; j < Q; j += blockDim.x) {
+        const int k = j & (Ns - 1);
+        T2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = src[j + r * Q];
+        if (Ns > 1) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                const int m = r * k * mstep;  // < 2H
+                T2 w = tw[m < H ? m : m - H];
+                if (m >= H) w = T2{-w.x, -w.y};
+                if (INV) w.y = -w.y;
+                v[r] = cmul(v[r], w);
+            }
+        }
+        dft_r<T, R, INV>(v);
+        const int base = (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) dst[base + r * Ns] = v[r];
+    }
+}
+
+// H-point transform from src into one of the buffers x, y (out of place
+// every pass); returns the buffer that holds the result.  after_first runs
+// between the first pass and its barrier.
+template <typename T, bool INV, typename F>
+__device__ __forceinline__ typename C2<T>::type* fft_h(const typename C2<T>::type* src,
+                                                       typename C2<T>::type* x, typename C2<T>::type* y,
+                                                       const typename C2<T>::type* tw, int H, F after_first)
+{
+    using T2 = typename C2<T>::type;
+    const T2* in = src;
+    T2* out = x;
+    T2* other = y;
+    int Ns = 1;
+    bool first = true;
+    while (Ns < H) {
+        const int left = H / Ns;
+        if (left >= 8) {
+            fft_pass<T, 8, INV>(in, out, tw, H, Ns);
+            Ns *= 8;
+        } else if (left == 4) {
+            fft_pass<T, 4, INV>(in, out, tw, H, Ns);
+            Ns *= 4;
+        } else {
+            fft_pass<T, 2, INV>(in, out, tw, H, Ns);
+            Ns *= 2;
+        }
+        if (first) after_first();
+        first = false;
+        __syncthreads();
+        in = out;
+        T2* t = out;
+        out = other;
+        other = t;
+    }
+    return const_cast<T2*>(in);
+}
+
 template <typename T>
 __device__ void finalise(const Desc<T>& D, unsigned char* smem, int is_step)
 {
     using T2 = typename C2<T>::type;
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int n = D.n, M = D.M, K = M / 2, logM = D.logM;
-    T2* a = reinterpret_cast<T2*>(smem);
-    T2* tw = a + M;
-    double* red = reinterpret_cast<double*>(tw + K);
+    const int n = D.n, M = D.M, H = M / 2;
+    T2* bufA = reinterpret_cast<T2*>(smem);
+    T2* bufB = bufA + H;
+    T2* tw = bufB + H;
+    T2* zh = tw + H;
+    T* cs = reinterpret_cast<T*>(zh + H + 2);  // M values: column sums, then zeros
+    T* pterm = cs + M;                          // H/2+1 power terms
+    double* red = reinterpret_cast<double*>(pterm + H / 2 + 4);
 
-    // charge Q = Delta^2 sum psi_c; colsum was written by other CTAs
-    double part = 0.0;
-    for (int x = tid; x < n; x += nt) part += __ldcg(D.colsum + x);
-    double Q = D.delta * D.delta * block_sum(part, red);
-    bool bad = !(Q > 0.0) || !isfinite(Q);
-    double s_new = (D.renorm && !bad) ? 1.0 / Q : 1.0;
-
-    for (int x = tid; x < M; x += nt) {
-        double r = 0.0;
-        if (x < n) {
-            r = s_new * D.delta * __ldcg(D.colsum + x);
-            D.rho[x] = r;
+    // one round of asynchronous copies: twiddles, impedance, column sums
+    // (written by the other CTAs of this step; .cg keeps L1 out of the way)
+    {
+        constexpr int CB = sizeof(T2);
+        const char* gtw = reinterpret_cast<const char*>(D.tw);
+        const char* gzh = reinterpret_cast<const char*>(D.zhat);
+        const char* gcs = reinterpret_cast<const char*>(D.colsum);
+        const int ntw = H * CB / 16, zbytes = (H + 1) * CB, nzh = (zbytes + 15) / 16;
+        const int cbytes = n * (int)sizeof(T), ncs = M * (int)sizeof(T) / 16;
+        for (int i = tid; i < ntw; i += nt) cp_async16(reinterpret_cast<char*>(tw) + 16 * i, gtw + 16 * i, 16);
+        for (int i = tid; i < nzh; i += nt)
+            cp_async16(reinterpret_cast<char*>(zh) + 16 * i, gzh + 16 * i, min(16, zbytes - 16 * i));
+        for (int i = tid; i < ncs; i += nt) {
+            const int b = max(0, min(16, cbytes - 16 * i));
+            cp_async16(reinterpret_cast<char*>(cs) + 16 * i, b ? gcs + 16 * i : gcs, b);
         }
-        a[x] = T2{T(r), T(0)};
+        cp_async_commit();
+        cp_async_wait_0();
+        __syncthreads();
     }
-    for (int k = tid; k < K; k += nt) tw[k] = D.tw[k];
+
+    // forward transform of z_j = cs_2j + i cs_2j+1; meanwhile warp 0 sums
+    // the charge Q = Delta^2 sum cs into red[0]
+    T2* Z = fft_h<T, false>(reinterpret_cast<const T2*>(cs), bufA, bufB, tw, H, [&] {
+        if (tid < 32) {
+            const T s = warp_fixed_sum<T>(cs, n);
+            if (tid == 0) red[0] = double(s);
+        }
+    });
+    const T Q = T(D.delta * D.delta) * T(red[0]);
+    const bool bad = !(Q > T(0)) || !isfinite(Q);
+    const T s_new = (D.renorm && !bad) ? T(1) / Q : T(1);
+    const T sd = s_new * T(D.delta);  // rho_x = sd * cs_x
+    const T sk = sd * T(D.delta);     // rho~_k = Delta * DFT(rho)_k = sk * X_k
+
+    // per pair (k, H-k): split, multiply by the impedance, power, fold back
+    for (int p = tid; p <= H / 2; p += nt) {
+        T term = T(0);
+        if (p == 0) {
+            Z[0] = T2{T(0), T(0)};  // DC and Nyquist carry no wake
+        } else {
+            const int k = p, kk = H - p;
+            const T2 zk = Z[k], zkk = Z[kk];
+            const T2 E = {T(0.5) * (zk.x + zkk.x), T(0.5) * (zk.y - zkk.y)};
+            const T2 O = {T(0.5) * (zk.y + zkk.y), T(0.5) * (zkk.x - zk.x)};
+            const T2 w = tw[k];
+            const T2 WO = cmul(w, O);
+            const T2 rk = {sk * (E.x + WO.x), sk * (E.y + WO.y)};
+            const T2 rkk = {sk * (E.x - WO.x), sk * (WO.y - E.y)};
+            const T2 Zk = zh[k], Zkk = zh[kk];
+            const T2 Bk = cmul(Zk, rk), Bkk = cmul(Zkk, rkk);
+            term = T(2) * Zk.x * (rk.x * rk.x + rk.y * rk.y);
+            if (kk != k) term += T(2) * Zkk.x * (rkk.x * rkk.x + rkk.y * rkk.y);
+            const T2 S = {Bk.x + Bkk.x, Bk.y - Bkk.y};    // B_k + conj B_{H-k}
+            const T2 Df = {Bk.x - Bkk.x, Bk.y + Bkk.y};   // B_k - conj B_{H-k}
+            const T2 uD = cmulc(Df, w);                    // exp(+2 pi i k/M) * Df
+            const T2 iuD = {-uD.y, uD.x};
+            Z[k] = cadd(S, iuD);
+            if (kk != k) Z[kk] = T2{S.x - iuD.x, iuD.y - S.y};  // conj(S - i u Df)
+        }
+        pterm[p] = term;
+    }
     __syncthreads();
 
-    // forward DIF
-    for (int s = K; s >= 1; s >>= 1) {
-        int stride = K / s;  // M/(2s)
-        for (int b = tid; b < K; b += nt) {
-            int j = b & (s - 1);
-            int i = ((b - j) << 1) + j;
-            T2 u = a[i], v = a[i + s];
-            a[i] = cadd(u, v);
-            a[i + s] = cmul(csub(u, v), tw[j * stride]);
+    // inverse transform; meanwhile warp 0 sums the power terms into red[1]
+    T2* y = fft_h<T, true>(Z, Z == bufA ? bufB : bufA, Z, tw, H, [&] {
+        if (tid < 32) {
+            const T s = warp_fixed_sum<T>(pterm, H / 2 + 1);
+            if (tid == 0) red[1] = double(s);
         }
-        __syncthreads();
-    }
-
-    // power and wake spectrum (bit-reversed positions)
-    const T d = T(D.delta);
-    double pp = 0.0;
-    for (int pos = tid; pos < M; pos += nt) {
-        int k = (int)(__brev((unsigned)pos) >> (32 - logM));
-        T2 X = a[pos];
-        X.x *= d;
-        X.y *= d;  // rho~_k = Delta * X_k
-        T2 B = {T(0), T(0)};
-        if (k >= 1 && k < K) {
-            T2 z = D.zhat[k];
-            B = cmul(z, X);
-            pp += 2.0 * double(z.x) * (double(X.x) * double(X.x) + double(X.y) * double(X.y));
-        } else if (k > K) {
-            T2 z = D.zhat[M - k];
-            B = cmulc(X, z);  // conj(Z_{M-k}) rho~_k
-        }
-        a[pos] = B;
-    }
-    double P = D.dkappa * block_sum(pp, red);  // block_sum syncs
-
-    // inverse DIT with conjugate twiddles
-    for (int s = 1; s < M; s <<= 1) {
-        int stride = K / s;
-        for (int b = tid; b < K; b += nt) {
-            int j = b & (s - 1);
-            int i = ((b - j) << 1) + j;
-            T2 w = tw[j * stride];
-            w.y = -w.y;
-            T2 u = a[i], v = cmul(a[i + s], w);
-            a[i] = cadd(u, v);
-            a[i + s] = csub(u, v);
-        }
-        __syncthreads();
-    }
+    });
+    const T kpv = T(D.kick_per_v * D.dkappa);
     for (int x = tid; x < n; x += nt) {
-        double V = D.dkappa * double(a[x].x);
-        D.kick[x] = T(D.kick_per_v * V);
+        const T2 v = y[x >> 1];
+        D.kick[x] = kpv * ((x & 1) ? v.y : v.x);
+        D.rho[x] = double(sd * cs[x]);
     }
     if (tid == 0) {
+        const double P = D.dkappa * red[1];
         DevState* st = D.st;
         long long t = st->t;
         if (is_step) {
-            D.qring[t & D.ring_mask] = Q;
+            D.qring[t & D.ring_mask] = double(Q);
             D.pring[(t + 1) & D.ring_mask] = P;
             st->t = t + 1;
             st->parity ^= 1;
-            st->qlast = Q;
+            st->qlast = double(Q);
         } else {
             D.pring[t & D.ring_mask] = P;
         }
-        st->scale = s_new;
+        st->scale = double(s_new);
         if (bad || !isfinite(P)) st->status = -5;
         st->ticket = 0u;
     }
@@ -294,6 +466,8 @@ step_kernel(const Desc<T>* __restrict__ descs, const int2* __restrict__ tiles)
     T* colA = slab + SW * P;             // W columns of psi_a, n each
     T* colB = slab;                      // reuses the slab after the rotation
 
+    pdl_trigger();
+    pdl_wait();
     const int par = D.st->parity;
     const T scale = T(D.st->scale);
     const T* __restrict__ in = D.psi[par];
@@ -354,7 +528,7 @@ step_kernel(const Desc<T>* __restrict__ descs, const int2* __restrict__ tiles)
     __syncwarp();
 
     // Fokker-Planck -> psi_c, column sum
-    double csum = 0.0;
+    T csum = T(0);
     if (active) {
         const T* cb = colB + warp * n;
         T* dst = out + (size_t)x * ld;
@@ -373,7 +547,7 @@ step_kernel(const Desc<T>* __restrict__ descs, const int2* __restrict__ tiles)
             dst[y] = v;
             lsum += v;
         }
-        csum = double(lsum);
+        csum = lsum;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) csum += __shfl_down_sync(0xffffffffu, csum, o);
         if (lane == 0) {
@@ -407,10 +581,12 @@ project_kernel(const Desc<T>* __restrict__ descs, const int2* __restrict__ tiles
     const int n = D.n, ld = D.ld;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int x = tile.y + warp;
+    pdl_trigger();
+    pdl_wait();
     const T* in = D.psi[D.st->parity];
     if (x < n) {
-        double s = 0.0;
-        for (int y = lane; y < n; y += 32) s += double(in[(size_t)x * ld + y]);
+        T s = T(0);
+        for (int y = lane; y < n; y += 32) s += in[(size_t)x * ld + y];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
         if (lane == 0) {
