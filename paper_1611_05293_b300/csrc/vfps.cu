@@ -134,6 +134,9 @@ bool fast_eligible(const vfps_params* p)
     return p->precision == 0 && p->interp_points == 4 && p->clamp == 0 && (p->n % 4) == 0;
 }
 
+// Rows per lane of the FP32 kernel's kick/FP blocks: 8 where n allows.
+int fast_kr(int n) { return (n % 8 == 0) ? 8 : 4; }
+
 size_t fast_smem(const vfps_params* p, int W)
 {
     size_t fin = vfps::finalise_smem(fft_length(p), p->n, W * 32, 8);
@@ -221,6 +224,8 @@ struct Instance {
     double* colsum = nullptr;
     double* rho = nullptr;
     void* kick = nullptr;
+    void* kickw = nullptr;   // FP32: float4 per column
+    int* kicks = nullptr;    // FP32: int per column
     double* pring = nullptr;
     double* qring = nullptr;
     DevState* st = nullptr;
@@ -260,6 +265,8 @@ size_t instance_bytes(const vfps_params* p, int ring, size_t* offs)
     take(9, sizeof(DevState));           // state
     take(10, sizeof(Desc<double>));      // descriptor
     take(11, sizeof(int2) * (size_t)((n + 1) / 2 + 1));  // tiles (W >= 2)
+    take(12, (size_t)n * 16);            // kick weights (FP32 path)
+    take(13, (size_t)n * 4);             // kick shifts (FP32 path)
     return align_up(o, kAlign);
 }
 
@@ -274,6 +281,8 @@ void fill_desc(Instance& I)
     d.colsum = reinterpret_cast<T*>(I.colsum);
     d.rho = I.rho;
     d.kick = (T*)I.kick;
+    d.kickw = (float4*)I.kickw;
+    d.kicks = I.kicks;
     d.pring = I.pring;
     d.qring = I.qring;
     d.st = I.st;
@@ -449,7 +458,7 @@ int create_instance(const vfps_params* p, const double* psi0, int ring, cudaStre
     I->ring = ring;
     I->delta = 2.0 * p->half_width / (p->n - 1);
     I->phi = 2.0 * kPi / p->steps_per_period;
-    size_t offs[12];
+    size_t offs[14];
     I->dbytes = instance_bytes(p, ring, offs);
     if (cudaMalloc(&I->dmem, I->dbytes) != cudaSuccess) {
         cudaGetLastError();
@@ -469,6 +478,8 @@ int create_instance(const vfps_params* p, const double* psi0, int ring, cudaStre
     I->st = (DevState*)(b + offs[9]);
     I->ddesc = b + offs[10];
     I->dtiles = (int2*)(b + offs[11]);
+    I->kickw = b + offs[12];
+    I->kicks = (int*)(b + offs[13]);
     // twiddles exp(-2 pi i k/M), FP64 on the host
     {
         int K = I->M / 2;
@@ -514,6 +525,7 @@ int create_instance(const vfps_params* p, const double* psi0, int ring, cudaStre
 struct Group {
     int prec = 0, ni = 4, W = 8, fast = 0;
     int tps = 1;  // FP32 streaming kernel: consecutive tiles per CTA
+    int kr = 4;   // FP32 streaming kernel: rows per lane of the kick/FP blocks
     size_t smem = 0;
     int ntiles = 0;
     void* ddescs = nullptr;  // array of Desc<T>
@@ -581,8 +593,12 @@ int launch_step_ni(const Group& g, cudaStream_t s)
 template <int W>
 int launch_fast_t(const Group& g, cudaStream_t s)
 {
-    CU(launch_pdl(step_kernel_f32<W>, g.ntiles / g.tps, W * 32, g.smem, s, (const Desc<float>*)g.ddescs,
-                  (const int2*)g.dtiles, g.tps));
+    if (g.kr == 8)
+        CU(launch_pdl(step_kernel_f32<W, 8>, g.ntiles / g.tps, W * 32, g.smem, s, (const Desc<float>*)g.ddescs,
+                      (const int2*)g.dtiles, g.tps));
+    else
+        CU(launch_pdl(step_kernel_f32<W, 4>, g.ntiles / g.tps, W * 32, g.smem, s, (const Desc<float>*)g.ddescs,
+                      (const int2*)g.dtiles, g.tps));
     return VFPS_OK;
 }
 
@@ -662,9 +678,12 @@ int init_kernels()
     if (lim <= 0) return VFPS_ECUDA;
     CU(set_smem_attr_all<float>(lim));
     CU(set_smem_attr_all<double>(lim));
-    CU(set_smem_attr_one(step_kernel_f32<8>, lim));
-    CU(set_smem_attr_one(step_kernel_f32<4>, lim));
-    CU(set_smem_attr_one(step_kernel_f32<2>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<8, 8>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<4, 8>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<2, 8>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<8, 4>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<4, 4>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<2, 4>, lim));
     g_kernels_ready = 1;
     return VFPS_OK;
 }
@@ -677,6 +696,7 @@ Group single_group(const Instance& I)
     g.ni = I.p.interp_points;
     g.W = I.W;
     g.fast = I.fast;
+    g.kr = fast_kr(I.p.n);
     g.smem = I.fast ? std::max(fast_smem(&I.p, I.W), step_smem(&I.p, I.W)) : step_smem(&I.p, I.W);
     g.ntiles = I.ntiles;
     g.ddescs = I.ddesc;
@@ -1071,6 +1091,7 @@ int rebuild_groups(vfps_batch* b)
             if (g.fast) g.smem = std::max(g.smem, fast_smem(&I->p, I->W));
         }
         g.ntiles = nt;
+        g.kr = fast_kr(kv.second[0]->p.n);  // a group shares n
         if (g.fast) {
             // a strip of tps consecutive tiles per CTA: the largest divisor of
             // the tiles per instance that still leaves ~3 CTAs per resident slot
@@ -1102,7 +1123,7 @@ extern "C" {
 int64_t vfps_batch_slot_bytes(const vfps_params* params)
 {
     if (check_params(params)) return -1;
-    size_t offs[12];
+    size_t offs[14];
     return (int64_t)instance_bytes(params, kRingDefault / 2, offs);
 }
 
@@ -1138,7 +1159,7 @@ int vfps_batch_add(vfps_batch* b, const vfps_params* params, const double* psi0,
             break;
         }
     if (free_slot < 0) return VFPS_EBUSY;
-    size_t offs[12];
+    size_t offs[14];
     long long need = (long long)instance_bytes(params, kRingDefault / 2, offs);
     if (b->budget > 0 && b->used + need > b->budget) return VFPS_EBUSY;
     size_t fr = 0, tot = 0;
@@ -1331,7 +1352,9 @@ constexpr size_t kOffState = kOffTiles + sa(sizeof(int2) * (kStaticMaxN / 2 + 1)
 constexpr size_t kOffColsum = kOffState + sa(sizeof(DevState));
 constexpr size_t kOffRho = kOffColsum + sa(sizeof(double) * kStaticMaxN);
 constexpr size_t kOffKick = kOffRho + sa(sizeof(double) * kStaticMaxN);
-constexpr size_t kOffZhat = kOffKick + sa(sizeof(float) * kStaticMaxN);
+constexpr size_t kOffKickW = kOffKick + sa(sizeof(float) * kStaticMaxN);
+constexpr size_t kOffKickS = kOffKickW + sa(sizeof(float4) * kStaticMaxN);
+constexpr size_t kOffZhat = kOffKickS + sa(sizeof(int) * kStaticMaxN);
 constexpr size_t kOffTw = kOffZhat + sa(sizeof(float2) * (kStaticMaxFFT / 2 + 1));
 constexpr size_t kOffRings = kOffTw + sa(sizeof(float2) * (kStaticMaxFFT / 2));
 constexpr size_t STATIC_SCRATCH_BYTES = kOffRings + sa(sizeof(double) * 4);
@@ -1438,6 +1461,8 @@ extern "C" int vfps_step_static(const vfps_params* params, int model, double Pi,
     I.colsum = (double*)(d + kOffColsum);
     I.rho = (double*)(d + kOffRho);
     I.kick = d + kOffKick;
+    I.kickw = d + kOffKickW;
+    I.kicks = (int*)(d + kOffKickS);
     I.pring = (double*)(d + kOffRings);
     I.qring = (double*)(d + kOffRings) + 2;
     I.st = (DevState*)(d + kOffState);
@@ -1467,6 +1492,7 @@ extern "C" int vfps_step_static(const vfps_params* params, int model, double Pi,
     g.ni = params->interp_points;
     g.W = W;
     g.fast = fast;
+    g.kr = fast_kr(params->n);
     g.ntiles = I.ntiles;
     g.smem = fast ? std::max(fast_smem(params, W), step_smem(params, W)) : step_smem(params, W);
     g.ddescs = d + kOffDesc;

@@ -4,22 +4,26 @@
 // rotation (2-D cubic Lagrange, Sec. III.A-B), kick along p, Fokker-Planck
 // step (Eq. cubic diff), column sums, and the same last-CTA finaliser.
 //
-// Work of one lane: four consecutive rows y0..y0+3 of its warp's column x.
-//  * Rotation.  Along a column the source point moves by (-sin phi, ~1)
-//    cells per row, so the four outputs share one window of 5 source
-//    columns x 12 rows, read with 15 LDS.128.  The y-node offset
+// Work of one lane: blocks of consecutive rows of its warp's column x.
+//  * Rotation, four rows y0..y0+3.  Along a column the source point moves
+//    by (-sin phi, ~1) cells per row, so the four outputs share one window
+//    of 5 source columns x 12 rows, read with 15 LDS.128.  The y-node offset
 //    floor(dy) is the same for all four rows and, almost always, for the
-//    whole warp (dy changes by cos phi - 1 ~ 1e-5 per row): the window's
-//    row alignment is then warp-uniform and selects a compile-time
-//    register layout.  The x-node may step back by one inside the block
-//    (dx changes by -sin phi per row); a 5-column weight vector with a zero
-//    at one end covers both cases.  A warp whose rows do not meet these
-//    conditions computes its block cell by cell (rotate_cell).
-//  * Kick and Fokker-Planck.  The column's kick shift s + t is uniform, so
-//    psi_b(y0-1..y0+5) comes from one 16-row window of the psi_a column
-//    (zero-padded rows), and psi_c(y0..y0+3) from psi_b and the per-row FP
-//    weights g(y) held in shared memory.  One STG.128 writes the block.
-//  * Pairs of rows go through packed FP32x2 FMAs (__ffma2_rn, sm_100+).
+//    whole column (dy changes by cos phi - 1 ~ 1e-5 per row): the window's
+//    row alignment is then uniform and selects a compile-time register
+//    layout.  The x-node may step back by one inside the block (dx changes
+//    by -sin phi per row); a 5-column weight vector with a zero at one end
+//    covers both cases.  A column that does not meet these conditions is
+//    computed cell by cell (rotate_cell_ring).
+//  * Kick and Fokker-Planck, KR rows y0..y0+KR-1 (KR = 8, or 4 when n is
+//    not a multiple of 8).  The column's kick shift s and weights are
+//    uniform and come from a per-column table the finaliser of the previous
+//    step wrote, with the pending renormalisation factor folded into the
+//    weights; psi_b(y0-1..y0+KR+1) comes from one window of the psi_a column
+//    (zero-padded rows), and psi_c(y0..y0+KR-1) from psi_b and the per-row
+//    FP weights g_k(y), held as four planar rows in shared memory so that
+//    the lanes' 16-byte reads do not conflict.
+//  * Weight pairs of rows go through packed FP32x2 arithmetic (sm_100+).
 #pragma once
 #include "vfps_kernels.cuh"
 
@@ -42,20 +46,19 @@ __host__ inline size_t fast_smem_bytes(int n, int h, int W)
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
-// Cubic Lagrange weights (nodes -1, 0, 1, 2) for two fractions at once.
+// Cubic Lagrange weights (nodes -1, 0, 1, 2) for two fractions at once,
+// each weight as a product of two factors that are one FMA from t:
+//   w0 = t(t-1) (2-t)/6,  w1 = (t^2-1) (t-2)/2,  w2 = t(t+1) (2-t)/2,
+//   w3 = t(t-1) (t+1)/6.
 __device__ __forceinline__ void lagrange2(float2 t, float2 w[4])
 {
-    const float2 one = f2(1.f, 1.f), two = f2(2.f, 2.f);
-    float2 tm1 = __fadd2_rn(t, f2(-1.f, -1.f));
-    float2 tm2 = __fadd2_rn(t, f2(-2.f, -2.f));
-    float2 tp1 = __fadd2_rn(t, one);
-    float2 a = __fmul2_rn(t, tm1);
-    float2 b = __fmul2_rn(tp1, t);
-    w[0] = __fmul2_rn(__fmul2_rn(a, tm2), f2(-1.f / 6.f, -1.f / 6.f));
-    w[1] = __fmul2_rn(__fmul2_rn(__fmul2_rn(tp1, tm1), tm2), f2(0.5f, 0.5f));
-    w[2] = __fmul2_rn(__fmul2_rn(b, tm2), f2(-0.5f, -0.5f));
-    w[3] = __fmul2_rn(__fmul2_rn(b, tm1), f2(1.f / 6.f, 1.f / 6.f));
-    (void)two;
+    const float2 p = __ffma2_rn(t, t, f2(-t.x, -t.y));                    // t(t-1)
+    const float2 r = __ffma2_rn(t, t, f2(-1.f, -1.f));                    // t^2-1
+    const float2 q = __ffma2_rn(t, t, t);                                  // t(t+1)
+    w[0] = __fmul2_rn(p, __ffma2_rn(t, f2(-1.f / 6.f, -1.f / 6.f), f2(1.f / 3.f, 1.f / 3.f)));
+    w[1] = __fmul2_rn(r, __ffma2_rn(t, f2(0.5f, 0.5f), f2(-1.f, -1.f)));
+    w[2] = __fmul2_rn(q, __ffma2_rn(t, f2(-0.5f, -0.5f), f2(1.f, 1.f)));
+    w[3] = __fmul2_rn(p, __ffma2_rn(t, f2(1.f / 6.f, 1.f / 6.f), f2(1.f / 6.f, 1.f / 6.f)));
 }
 
 // Rotation of four rows from a 5 x 12 register window: 5 consecutive slab
@@ -103,50 +106,63 @@ __device__ __forceinline__ void rotate_block(const float* __restrict__ ring, int
     for (int k = 0; k < 4; ++k) out[k] = acc[k];
 }
 
-// Kick + Fokker-Planck for the lane's row blocks of one column; the psi_a
-// window starts O2 rows above the first row the kick of row y0-1 needs.
-template <int O2>
-__device__ __forceinline__ float kick_fp_column(const float* __restrict__ colA_col, const float4* __restrict__ gtab,
-                                                float* __restrict__ dst, int n, int s, int A2,
-                                                const float w[4], int lane)
+// Kick + Fokker-Planck for the lane's blocks of KR rows of one column.  The
+// psi_a window starts O2 rows above the first row the kick of row y0-1
+// needs; w are the column's kick weights (pending scale included), s its
+// node shift; g holds the FP weights g_k(y) as four planar rows of n.
+template <int O2, int KR>
+__device__ __forceinline__ float kick_fp_column(const float* __restrict__ colA_col, const float* __restrict__ g,
+                                                float* __restrict__ dst, int n, int s, int A2, float4 w, int lane)
 {
+    constexpr int NB = KR + 3;                  // psi_b rows y0-1 .. y0+KR+1
+    constexpr int NV = (O2 + NB + 3 + 3) / 4;   // float4 reads of the window
+    // psi_b(y) is 0 off the grid and where its source is > 1 cell outside
+    const int lo = max(0, -1 - s), hi = min(n - 1, n - 1 - s);
     float lsum = 0.f;
-    for (int y0 = 4 * lane; y0 < n; y0 += 128) {
+    for (int y0 = KR * lane; y0 < n; y0 += 32 * KR) {
         const float4* wp = reinterpret_cast<const float4*>(colA_col + y0 + A2 - O2);
-        float4 q0 = wp[0], q1 = wp[1], q2 = wp[2], q3 = wp[3];
-        const float win[16] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w,
-                               q2.x, q2.y, q2.z, q2.w, q3.x, q3.y, q3.z, q3.w};
-        // psi_b(y0 + j - 1), j = 0..6: nodes y0+j+s-2 .. y0+j+s+1
-        float b[7];
+        float win[4 * NV];
 #pragma unroll
-        for (int j = 0; j < 7; ++j) {
-            float v = w[0] * win[O2 + j];
-            v = fmaf(w[1], win[O2 + j + 1], v);
-            v = fmaf(w[2], win[O2 + j + 2], v);
-            b[j] = fmaf(w[3], win[O2 + j + 3], v);
+        for (int v = 0; v < NV; ++v) {
+            const float4 q = wp[v];
+            win[4 * v] = q.x;
+            win[4 * v + 1] = q.y;
+            win[4 * v + 2] = q.z;
+            win[4 * v + 3] = q.w;
         }
-        // zero psi_b off the grid and where the kick source is > 1 cell outside
+        // psi_b(y0 + j - 1): nodes y0+j+s-2 .. y0+j+s+1
+        const int jlo = lo - y0 + 1, jhi = hi - y0 + 1;
+        float b[NB];
 #pragma unroll
-        for (int j = 0; j < 7; ++j) {
-            int y = y0 + j - 1;
-            int m = y + s;
-            bool ok = (y >= 0) && (y < n) && (m >= -1) && (m <= n - 1);
-            b[j] = ok ? b[j] : 0.f;
+        for (int j = 0; j < NB; ++j) {
+            float v = w.x * win[O2 + j];
+            v = fmaf(w.y, win[O2 + j + 1], v);
+            v = fmaf(w.z, win[O2 + j + 2], v);
+            v = fmaf(w.w, win[O2 + j + 3], v);
+            b[j] = (j >= jlo && j <= jhi) ? v : 0.f;
         }
-        float c[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            float4 g = gtab[y0 + k];
-            float inc = g.x * b[k] + g.y * b[k + 1] + g.z * b[k + 2] + g.w * b[k + 3];
-            c[k] = b[k + 1] + inc;
+        for (int q4 = 0; q4 < KR / 4; ++q4) {
+            const int y = y0 + 4 * q4;
+            const float4 g0 = *reinterpret_cast<const float4*>(g + y);
+            const float4 g1 = *reinterpret_cast<const float4*>(g + n + y);
+            const float4 g2 = *reinterpret_cast<const float4*>(g + 2 * n + y);
+            const float4 g3 = *reinterpret_cast<const float4*>(g + 3 * n + y);
+            const float ga[4] = {g0.x, g0.y, g0.z, g0.w}, gb[4] = {g1.x, g1.y, g1.z, g1.w};
+            const float gc[4] = {g2.x, g2.y, g2.z, g2.w}, gd[4] = {g3.x, g3.y, g3.z, g3.w};
+            float c[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float* bb = b + 4 * q4 + k;
+                const float inc = ga[k] * bb[0] + gb[k] * bb[1] + gc[k] * bb[2] + gd[k] * bb[3];
+                c[k] = bb[1] + inc;
+            }
+            *reinterpret_cast<float4*>(dst + y) = make_float4(c[0], c[1], c[2], c[3]);
+            lsum += (c[0] + c[1]) + (c[2] + c[3]);
         }
-        *reinterpret_cast<float4*>(dst + y0) = make_float4(c[0], c[1], c[2], c[3]);
-        lsum += (c[0] + c[1]) + (c[2] + c[3]);
     }
     return lsum;
 }
-
-
 
 // Rotation of one cell from the column ring (general path; same arithmetic
 // as rotate_cell, with slab column col stored in ring slot col & (R-1)).
@@ -217,7 +233,7 @@ __host__ inline size_t fast_ring_smem(int n, int h, int W)
 template <int O>
 __device__ __forceinline__ void rotate_column(const float* __restrict__ ring, int R, int P, int RP, int A,
                                               float* __restrict__ ca, int x, int n, int lane, float xc, float c,
-                                              float sn, float cm1, int FY, float scale)
+                                              float sn, float cm1, int FY)
 {
     const float2 msn2 = f2(-sn, -sn), cm12 = f2(cm1, cm1);
     const float2 snxc = f2(sn * xc, sn * xc), cmxc = f2(cm1 * xc, cm1 * xc);
@@ -246,7 +262,7 @@ __device__ __forceinline__ void rotate_column(const float* __restrict__ ring, in
                 if (mx <= -2 || mx >= n || my <= -2 || my >= n) r[k] = 0.f;
             }
         }
-        *reinterpret_cast<float4*>(ca + y0) = make_float4(scale * r[0], scale * r[1], scale * r[2], scale * r[3]);
+        *reinterpret_cast<float4*>(ca + y0) = make_float4(r[0], r[1], r[2], r[3]);
     }
 }
 
@@ -256,8 +272,10 @@ __device__ __forceinline__ void rotate_column(const float* __restrict__ ring, in
 // slots (R >= 2W + 2h): while tile j is computed, the W new columns of tile
 // j+1 are resident or landing and those of tile j+2 are requested, so each
 // column of psi is read from HBM once per strip and the copies overlap the
-// arithmetic.  The pending scale multiplies psi_a after the rotation.
-template <int W>
+// arithmetic.  psi_a stays unscaled; the pending renormalisation factor is
+// part of the kick weights.  The column sums of a strip are made visible
+// with one fence per thread before the CTA takes its ticket.
+template <int W, int KR>
 __global__ void __launch_bounds__(W * 32, 32 / W)
 step_kernel_f32(const Desc<float>* __restrict__ descs, const int2* __restrict__ tiles, int tps)
 {
@@ -273,27 +291,33 @@ step_kernel_f32(const Desc<float>* __restrict__ descs, const int2* __restrict__ 
     const int PA = n + 2 * kColPad;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int T = min(tps, (n - xs + W - 1) / W);
+    const float cm1 = D.cm1, sn = D.sn, c = D.c;
+    const float4* __restrict__ kickw = D.kickw;
+    const int* __restrict__ kicks = D.kicks;
+    float* __restrict__ colsum = D.colsum;
 
     float* ring = reinterpret_cast<float*>(smem);
     float* colA = ring + R * P;
-    float4* gtab = reinterpret_cast<float4*>(colA + W * PA);
+    float* gtab = colA + W * PA;  // g_0(y) .. g_3(y), n each
     pdl_trigger();
 
-    // padding rows of every ring slot: zero for the whole strip
-    for (int i = threadIdx.x; i < R * 2 * RP; i += blockDim.x) {
-        const int slot = i / (2 * RP), r = i % (2 * RP);
-        ring[slot * P + (r < RP ? r : n + r)] = 0.f;
-    }
-    for (int i = threadIdx.x; i < W * 2 * kColPad; i += blockDim.x) {
-        const int w = i / (2 * kColPad), r = i % (2 * kColPad);
-        colA[w * PA + (r < kColPad ? r : n + r)] = 0.f;
+    // padding rows of every ring slot and of this warp's psi_a column: zero
+    // for the whole strip
+    for (int slot = warp; slot < R; slot += W)
+        for (int r = lane; r < RP; r += 32) {
+            ring[slot * P + r] = 0.f;
+            ring[slot * P + RP + n + r] = 0.f;
+        }
+    for (int r = lane; r < kColPad; r += 32) {
+        colA[warp * PA + r] = 0.f;
+        colA[warp * PA + kColPad + n + r] = 0.f;
     }
     for (int y = threadIdx.x; y < n; y += blockDim.x) {
         const float yf = float(y);
-        gtab[y] = make_float4(D.ga[0] + D.gb[0] * yf, D.ga[1] + D.gb[1] * yf, D.ga[2] + D.gb[2] * yf,
-                              D.ga[3] + D.gb[3] * yf);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) gtab[k * n + y] = D.ga[k] + D.gb[k] * yf;
     }
-    // what the previous step wrote (state word, psi, kick) is read from here on
+    // what the previous step wrote (state word, psi, kick table) is read from here on
     pdl_wait();
     const int par = D.st->parity;
     const float* __restrict__ in = D.psi[par];
@@ -303,14 +327,12 @@ step_kernel_f32(const Desc<float>* __restrict__ descs, const int2* __restrict__ 
     cp_async_commit();
     if (T > 1) load_columns<W>(ring, R, P, RP, in, ld, n, xs + W + h, W);
     cp_async_commit();
-    const float scale = float(D.st->scale);
-    const float cm1 = D.cm1, sn = D.sn, c = D.c;
 
     for (int j = 0; j < T; ++j) {
-        cp_async_wait_1();
-        __syncthreads();
         const int x = xs + j * W + warp;
         const bool active = x < n;
+        cp_async_wait_1();
+        __syncthreads();
         float* ca = colA + warp * PA + kColPad;
         if (active) {
             const float xc = float(x) - c;
@@ -322,36 +344,33 @@ step_kernel_f32(const Desc<float>* __restrict__ descs, const int2* __restrict__ 
                 const int FY = int(fy_top);
                 const int A = FY - 1 + RP;
                 switch (A & 3) {
-                case 0: rotate_column<0>(ring, R, P, RP, A, ca, x, n, lane, xc, c, sn, cm1, FY, scale); break;
-                case 1: rotate_column<1>(ring, R, P, RP, A, ca, x, n, lane, xc, c, sn, cm1, FY, scale); break;
-                case 2: rotate_column<2>(ring, R, P, RP, A, ca, x, n, lane, xc, c, sn, cm1, FY, scale); break;
-                default: rotate_column<3>(ring, R, P, RP, A, ca, x, n, lane, xc, c, sn, cm1, FY, scale); break;
+                case 0: rotate_column<0>(ring, R, P, RP, A, ca, x, n, lane, xc, c, sn, cm1, FY); break;
+                case 1: rotate_column<1>(ring, R, P, RP, A, ca, x, n, lane, xc, c, sn, cm1, FY); break;
+                case 2: rotate_column<2>(ring, R, P, RP, A, ca, x, n, lane, xc, c, sn, cm1, FY); break;
+                default: rotate_column<3>(ring, R, P, RP, A, ca, x, n, lane, xc, c, sn, cm1, FY); break;
                 }
             } else {
-                for (int y = lane; y < n; y += 32)
-                    ca[y] = scale * rotate_cell_ring(ring, R, P, RP, x, y, n, cm1, sn, c);
+                for (int y = lane; y < n; y += 32) ca[y] = rotate_cell_ring(ring, R, P, RP, x, y, n, cm1, sn, c);
             }
         }
         __syncwarp();
         if (active) {
-            const float ks = -D.kick[x];
-            const float fk = floorf(ks);
-            const int s = int(fk);
-            float w[4];
-            lagrange_w<float, 4>(ks - fk, w);
+            const float4 kw = kickw[x];
+            const int s = kicks[x];
             float* dst = out + (size_t)x * ld;
             float lsum = 0.f;
             if (s >= -4 && s <= 4) {
                 const int A2 = s - 2 + kColPad;  // column index of row y0+s-2, minus y0
                 const float* colcol = colA + warp * PA;
                 switch (A2 & 3) {
-                case 0: lsum = kick_fp_column<0>(colcol, gtab, dst, n, s, A2, w, lane); break;
-                case 1: lsum = kick_fp_column<1>(colcol, gtab, dst, n, s, A2, w, lane); break;
-                case 2: lsum = kick_fp_column<2>(colcol, gtab, dst, n, s, A2, w, lane); break;
-                default: lsum = kick_fp_column<3>(colcol, gtab, dst, n, s, A2, w, lane); break;
+                case 0: lsum = kick_fp_column<0, KR>(colcol, gtab, dst, n, s, A2, kw, lane); break;
+                case 1: lsum = kick_fp_column<1, KR>(colcol, gtab, dst, n, s, A2, kw, lane); break;
+                case 2: lsum = kick_fp_column<2, KR>(colcol, gtab, dst, n, s, A2, kw, lane); break;
+                default: lsum = kick_fp_column<3, KR>(colcol, gtab, dst, n, s, A2, kw, lane); break;
                 }
             } else {
                 // large kick: plain per-row evaluation with bounds
+                const float w[4] = {kw.x, kw.y, kw.z, kw.w};
                 for (int y = lane; y < n; y += 32) {
                     float b[4];
 #pragma unroll
@@ -368,8 +387,8 @@ step_kernel_f32(const Desc<float>* __restrict__ descs, const int2* __restrict__ 
                         }
                         b[d] = v;
                     }
-                    const float4 g = gtab[y];
-                    const float v = b[1] + (g.x * b[0] + g.y * b[1] + g.z * b[2] + g.w * b[3]);
+                    const float v = b[1] + (gtab[y] * b[0] + gtab[n + y] * b[1] + gtab[2 * n + y] * b[2] +
+                                            gtab[3 * n + y] * b[3]);
                     dst[y] = v;
                     lsum += v;
                 }
@@ -377,16 +396,14 @@ step_kernel_f32(const Desc<float>* __restrict__ descs, const int2* __restrict__ 
             float csum = lsum;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) csum += __shfl_down_sync(0xffffffffu, csum, o);
-            if (lane == 0) {
-                D.colsum[x] = csum;
-                __threadfence();
-            }
+            if (lane == 0) colsum[x] = csum;
         }
         __syncthreads();  // the ring slots of columns xs+jW-h .. xs+jW+W-h-1 are free
         if (j + 2 < T) load_columns<W>(ring, R, P, RP, in, ld, n, xs + (j + 2) * W + h, W);
         cp_async_commit();
     }
     cp_async_wait_0();
+    __threadfence();  // this thread's column sums, before the ticket
     __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned prev = atomicAdd(&D.st->ticket, 1u);

@@ -14,6 +14,8 @@
 //   colsum   n values of T, sum_y psi_c[x][y] of the step just written (scratch)
 //   rho      n doubles, profile of the current (renormalised) state
 //   kick     n T, p-shift of column x in grid cells for the next step
+//   kickw    n float4 (FP32 instances): cubic weights of that shift times the
+//            pending scale; kicks: n ints, the node shift floor(-kick)
 //   pring    ring of CSR powers, pring[t] = P(psi_t)
 //   qring    ring of charges before renormalisation, qring[t] = Q of step t
 //   st       DevState: pending scale, step count, ticket, parity, status
@@ -49,6 +51,8 @@ struct Desc {
     T* colsum;                         // n column sums (scratch)
     double* rho;
     T* kick;
+    float4* kickw;                     // FP32 path: per-column kick weights x pending scale
+    int* kicks;                        // FP32 path: per-column kick node shift
     double* pring;
     double* qring;
     DevState* st;
@@ -420,8 +424,17 @@ __device__ void finalise(const Desc<T>& D, unsigned char* smem, int is_step)
     const T kpv = T(D.kick_per_v * D.dkappa);
     for (int x = tid; x < n; x += nt) {
         const T2 v = y[x >> 1];
-        D.kick[x] = kpv * ((x & 1) ? v.y : v.x);
+        const T k = kpv * ((x & 1) ? v.y : v.x);
+        D.kick[x] = k;
         D.rho[x] = double(sd * cs[x]);
+        if constexpr (sizeof(T) == 4) {
+            // psi_b(y) = sum_k w_k psi_a(y + s - 1 + k): source y - kick, s = floor(-kick)
+            const float ks = -k, fk = floorf(ks);
+            float w[4];
+            lagrange_w<float, 4>(ks - fk, w);
+            D.kickw[x] = make_float4(s_new * w[0], s_new * w[1], s_new * w[2], s_new * w[3]);
+            D.kicks[x] = int(fk);
+        }
     }
     if (tid == 0) {
         const double P = D.dkappa * red[1];
