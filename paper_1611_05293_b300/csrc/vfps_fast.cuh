@@ -35,13 +35,30 @@ constexpr int kColPad = 16;  // zero rows above and below each psi_a column
 // 12-row window, rounded to a multiple of 4 for 16-byte rows.
 __host__ __device__ inline int fast_row_pad(int h) { return ((h + 4 + 3) / 4) * 4; }
 
-__host__ inline size_t fast_smem_bytes(int n, int h, int W)
+// Pitch of a ring slot (rows -RP .. n+RP-1), rounded up to 32 floats: lanes
+// of one warp that straddle two slots then still read distinct banks.
+__host__ __device__ inline int ring_pitch(int n, int RP) { return (n + 2 * RP + 31) & ~31; }
+
+// Pitch of a psi_a column (kColPad zero rows above, >= kColPad below),
+// congruent to 32 floats modulo 64 (its half, in 16-byte chunks, is 4 mod 8).
+__host__ __device__ inline int cola_pitch(int n) { return ((n + 63) & ~63) + 32; }
+
+// Layout of the psi_a columns and FP-weight rows for 8-row kick blocks.  A
+// lane of an 8-row block reads every other 16-byte chunk, which on a plain
+// layout puts two lanes on each bank.  Chunk c of a row of HC2 chunks is
+// therefore stored at c/2 + (c&1)*HC2/2: even chunks in the first half, odd
+// ones in the second, so those reads hit consecutive chunks; lanes writing
+// consecutive chunks alternate between halves that start 4 banks apart
+// (psi_a columns, HC2/2 = 4 mod 8).  4-row blocks keep the plain layout.
+template <int KR>
+__device__ __forceinline__ int split_idx(int e, int half_chunks)
 {
-    int RP = fast_row_pad(h);
-    size_t slab = (size_t)(W + 2 * h) * (n + 2 * RP) * 4;
-    size_t cols = (size_t)W * (n + 2 * kColPad) * 4;
-    size_t gtab = (size_t)n * 16;
-    return slab + cols + gtab;
+    if constexpr (KR == 8) {
+        const int c = e >> 2;
+        return (((c >> 1) + (c & 1) * half_chunks) << 2) | (e & 3);
+    } else {
+        return e;
+    }
 }
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
@@ -108,11 +125,14 @@ __device__ __forceinline__ void rotate_block(const float* __restrict__ ring, int
 
 // Kick + Fokker-Planck for the lane's blocks of KR rows of one column.  The
 // psi_a window starts O2 rows above the first row the kick of row y0-1
-// needs; w are the column's kick weights (pending scale included), s its
-// node shift; g holds the FP weights g_k(y) as four planar rows of n.
-template <int O2, int KR>
-__device__ __forceinline__ float kick_fp_column(const float* __restrict__ colA_col, const float* __restrict__ g,
-                                                float* __restrict__ dst, int n, int s, int A2, float4 w, int lane)
+// needs (A2 = s - 2 + kColPad: column index of row y0+s-2, minus y0; PAR =
+// parity of its 16-byte chunk, fixed per column for 8-row blocks); w are the
+// column's kick weights (pending scale included), s its node shift; g holds
+// the FP weights g_k(y) as four rows of n (split layout for KR = 8).
+template <int O2, int PAR, int KR>
+__device__ __forceinline__ float kick_fp_column(const float* __restrict__ colcol, int HC,
+                                                const float* __restrict__ g, float* __restrict__ dst, int n, int s,
+                                                int A2, float4 w, int lane)
 {
     constexpr int NB = KR + 3;                  // psi_b rows y0-1 .. y0+KR+1
     constexpr int NV = (O2 + NB + 3 + 3) / 4;   // float4 reads of the window
@@ -120,15 +140,29 @@ __device__ __forceinline__ float kick_fp_column(const float* __restrict__ colA_c
     const int lo = max(0, -1 - s), hi = min(n - 1, n - 1 - s);
     float lsum = 0.f;
     for (int y0 = KR * lane; y0 < n; y0 += 32 * KR) {
-        const float4* wp = reinterpret_cast<const float4*>(colA_col + y0 + A2 - O2);
         float win[4 * NV];
+        if constexpr (KR == 8) {
+            // chunk of window row 4v: (y0 + A2 - O2)/4 + v = 2*(y0/8 + m) + PAR + v
+            const float* b0 = colcol + 4 * ((y0 >> 3) + ((A2 >> 2) >> 1));
+            const float* b1 = b0 + 4 * HC;
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            const float4 q = wp[v];
-            win[4 * v] = q.x;
-            win[4 * v + 1] = q.y;
-            win[4 * v + 2] = q.z;
-            win[4 * v + 3] = q.w;
+            for (int v = 0; v < NV; ++v) {
+                const float4 q = *reinterpret_cast<const float4*>(((PAR + v) & 1 ? b1 : b0) + 4 * ((PAR + v) >> 1));
+                win[4 * v] = q.x;
+                win[4 * v + 1] = q.y;
+                win[4 * v + 2] = q.z;
+                win[4 * v + 3] = q.w;
+            }
+        } else {
+            const float4* wp = reinterpret_cast<const float4*>(colcol + y0 + A2 - O2);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                const float4 q = wp[v];
+                win[4 * v] = q.x;
+                win[4 * v + 1] = q.y;
+                win[4 * v + 2] = q.z;
+                win[4 * v + 3] = q.w;
+            }
         }
         // psi_b(y0 + j - 1): nodes y0+j+s-2 .. y0+j+s+1
         const int jlo = lo - y0 + 1, jhi = hi - y0 + 1;
@@ -144,10 +178,11 @@ __device__ __forceinline__ float kick_fp_column(const float* __restrict__ colA_c
 #pragma unroll
         for (int q4 = 0; q4 < KR / 4; ++q4) {
             const int y = y0 + 4 * q4;
-            const float4 g0 = *reinterpret_cast<const float4*>(g + y);
-            const float4 g1 = *reinterpret_cast<const float4*>(g + n + y);
-            const float4 g2 = *reinterpret_cast<const float4*>(g + 2 * n + y);
-            const float4 g3 = *reinterpret_cast<const float4*>(g + 3 * n + y);
+            const int gi = (KR == 8) ? 4 * (y0 >> 3) + q4 * (n >> 1) : y;  // split_idx<KR>(y, n/8)
+            const float4 g0 = *reinterpret_cast<const float4*>(g + gi);
+            const float4 g1 = *reinterpret_cast<const float4*>(g + n + gi);
+            const float4 g2 = *reinterpret_cast<const float4*>(g + 2 * n + gi);
+            const float4 g3 = *reinterpret_cast<const float4*>(g + 3 * n + gi);
             const float ga[4] = {g0.x, g0.y, g0.z, g0.w}, gb[4] = {g1.x, g1.y, g1.z, g1.w};
             const float gc[4] = {g2.x, g2.y, g2.z, g2.w}, gd[4] = {g3.x, g3.y, g3.z, g3.w};
             float c[4];
@@ -223,17 +258,17 @@ __host__ __device__ inline int ring_slots(int W, int h)
 __host__ inline size_t fast_ring_smem(int n, int h, int W)
 {
     const int RP = fast_row_pad(h);
-    return (size_t)ring_slots(W, h) * (n + 2 * RP) * 4 + (size_t)W * (n + 2 * kColPad) * 4 + (size_t)n * 16;
+    return (size_t)ring_slots(W, h) * ring_pitch(n, RP) * 4 + (size_t)W * cola_pitch(n) * 4 + (size_t)n * 16;
 }
 
 // Rotation of one column x (rows 0..n-1, four per lane and pass) when the
 // y-node offset FY is the same on every row (window alignment O = A & 3,
 // A = FY - 1 + RP) and the x-node steps back by at most one inside a block
 // of four rows (sin phi < 1/3).
-template <int O>
+template <int O, int KR>
 __device__ __forceinline__ void rotate_column(const float* __restrict__ ring, int R, int P, int RP, int A,
-                                              float* __restrict__ ca, int x, int n, int lane, float xc, float c,
-                                              float sn, float cm1, int FY)
+                                              float* __restrict__ colcol, int HC, int x, int n, int lane, float xc,
+                                              float c, float sn, float cm1, int FY)
 {
     const float2 msn2 = f2(-sn, -sn), cm12 = f2(cm1, cm1);
     const float2 snxc = f2(sn * xc, sn * xc), cmxc = f2(cm1 * xc, cm1 * xc);
@@ -262,7 +297,7 @@ __device__ __forceinline__ void rotate_column(const float* __restrict__ ring, in
                 if (mx <= -2 || mx >= n || my <= -2 || my >= n) r[k] = 0.f;
             }
         }
-        *reinterpret_cast<float4*>(ca + y0) = make_float4(r[0], r[1], r[2], r[3]);
+        *reinterpret_cast<float4*>(colcol + split_idx<KR>(kColPad + y0, HC)) = make_float4(r[0], r[1], r[2], r[3]);
     }
 }
 
@@ -286,9 +321,10 @@ step_kernel_f32(const Desc<float>* __restrict__ descs, const int2* __restrict__ 
     const int xs = first.y;
     const int n = D.n, ld = D.ld, h = D.h;
     const int RP = fast_row_pad(h);
-    const int P = n + 2 * RP;
+    const int P = ring_pitch(n, RP);
     const int R = ring_slots(W, h);
-    const int PA = n + 2 * kColPad;
+    const int PA = cola_pitch(n);
+    const int HC = PA / 8;  // chunks in half a psi_a column (split layout)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int T = min(tps, (n - xs + W - 1) / W);
     const float cm1 = D.cm1, sn = D.sn, c = D.c;
@@ -298,7 +334,8 @@ step_kernel_f32(const Desc<float>* __restrict__ descs, const int2* __restrict__ 
 
     float* ring = reinterpret_cast<float*>(smem);
     float* colA = ring + R * P;
-    float* gtab = colA + W * PA;  // g_0(y) .. g_3(y), n each
+    float* gtab = colA + W * PA;  // g_0(y) .. g_3(y), n each (split layout for KR = 8)
+    float* colcol = colA + warp * PA;  // this warp's psi_a column, padded
     pdl_trigger();
 
     // padding rows of every ring slot and of this warp's psi_a column: zero
@@ -308,14 +345,12 @@ step_kernel_f32(const Desc<float>* __restrict__ descs, const int2* __restrict__ 
             ring[slot * P + r] = 0.f;
             ring[slot * P + RP + n + r] = 0.f;
         }
-    for (int r = lane; r < kColPad; r += 32) {
-        colA[warp * PA + r] = 0.f;
-        colA[warp * PA + kColPad + n + r] = 0.f;
-    }
+    for (int r = lane; r < PA - n; r += 32) colcol[split_idx<KR>(r < kColPad ? r : n + r, HC)] = 0.f;
     for (int y = threadIdx.x; y < n; y += blockDim.x) {
         const float yf = float(y);
+        const int gi = split_idx<KR>(y, n >> 3);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) gtab[k * n + y] = D.ga[k] + D.gb[k] * yf;
+        for (int k = 0; k < 4; ++k) gtab[k * n + gi] = D.ga[k] + D.gb[k] * yf;
     }
     // what the previous step wrote (state word, psi, kick table) is read from here on
     pdl_wait();
@@ -333,7 +368,6 @@ step_kernel_f32(const Desc<float>* __restrict__ descs, const int2* __restrict__ 
         const bool active = x < n;
         cp_async_wait_1();
         __syncthreads();
-        float* ca = colA + warp * PA + kColPad;
         if (active) {
             const float xc = float(x) - c;
             // dy is linear along the column: floor(dy) is the same on every row
@@ -344,13 +378,14 @@ step_kernel_f32(const Desc<float>* __restrict__ descs, const int2* __restrict__ 
                 const int FY = int(fy_top);
                 const int A = FY - 1 + RP;
                 switch (A & 3) {
-                case 0: rotate_column<0>(ring, R, P, RP, A, ca, x, n, lane, xc, c, sn, cm1, FY); break;
-                case 1: rotate_column<1>(ring, R, P, RP, A, ca, x, n, lane, xc, c, sn, cm1, FY); break;
-                case 2: rotate_column<2>(ring, R, P, RP, A, ca, x, n, lane, xc, c, sn, cm1, FY); break;
-                default: rotate_column<3>(ring, R, P, RP, A, ca, x, n, lane, xc, c, sn, cm1, FY); break;
+                case 0: rotate_column<0, KR>(ring, R, P, RP, A, colcol, HC, x, n, lane, xc, c, sn, cm1, FY); break;
+                case 1: rotate_column<1, KR>(ring, R, P, RP, A, colcol, HC, x, n, lane, xc, c, sn, cm1, FY); break;
+                case 2: rotate_column<2, KR>(ring, R, P, RP, A, colcol, HC, x, n, lane, xc, c, sn, cm1, FY); break;
+                default: rotate_column<3, KR>(ring, R, P, RP, A, colcol, HC, x, n, lane, xc, c, sn, cm1, FY); break;
                 }
             } else {
-                for (int y = lane; y < n; y += 32) ca[y] = rotate_cell_ring(ring, R, P, RP, x, y, n, cm1, sn, c);
+                for (int y = lane; y < n; y += 32)
+                    colcol[split_idx<KR>(kColPad + y, HC)] = rotate_cell_ring(ring, R, P, RP, x, y, n, cm1, sn, c);
             }
         }
         __syncwarp();
@@ -361,12 +396,15 @@ step_kernel_f32(const Desc<float>* __restrict__ descs, const int2* __restrict__ 
             float lsum = 0.f;
             if (s >= -4 && s <= 4) {
                 const int A2 = s - 2 + kColPad;  // column index of row y0+s-2, minus y0
-                const float* colcol = colA + warp * PA;
-                switch (A2 & 3) {
-                case 0: lsum = kick_fp_column<0, KR>(colcol, gtab, dst, n, s, A2, kw, lane); break;
-                case 1: lsum = kick_fp_column<1, KR>(colcol, gtab, dst, n, s, A2, kw, lane); break;
-                case 2: lsum = kick_fp_column<2, KR>(colcol, gtab, dst, n, s, A2, kw, lane); break;
-                default: lsum = kick_fp_column<3, KR>(colcol, gtab, dst, n, s, A2, kw, lane); break;
+                switch (KR == 8 ? (A2 & 7) : (A2 & 3)) {
+                case 0: lsum = kick_fp_column<0, 0, KR>(colcol, HC, gtab, dst, n, s, A2, kw, lane); break;
+                case 1: lsum = kick_fp_column<1, 0, KR>(colcol, HC, gtab, dst, n, s, A2, kw, lane); break;
+                case 2: lsum = kick_fp_column<2, 0, KR>(colcol, HC, gtab, dst, n, s, A2, kw, lane); break;
+                case 3: lsum = kick_fp_column<3, 0, KR>(colcol, HC, gtab, dst, n, s, A2, kw, lane); break;
+                case 4: lsum = kick_fp_column<0, 1, KR>(colcol, HC, gtab, dst, n, s, A2, kw, lane); break;
+                case 5: lsum = kick_fp_column<1, 1, KR>(colcol, HC, gtab, dst, n, s, A2, kw, lane); break;
+                case 6: lsum = kick_fp_column<2, 1, KR>(colcol, HC, gtab, dst, n, s, A2, kw, lane); break;
+                default: lsum = kick_fp_column<3, 1, KR>(colcol, HC, gtab, dst, n, s, A2, kw, lane); break;
                 }
             } else {
                 // large kick: plain per-row evaluation with bounds
@@ -382,13 +420,14 @@ step_kernel_f32(const Desc<float>* __restrict__ descs, const int2* __restrict__ 
 #pragma unroll
                             for (int k = 0; k < 4; ++k) {
                                 const int rr = mm - 1 + k;
-                                if (rr >= 0 && rr < n) v += w[k] * ca[rr];
+                                if (rr >= 0 && rr < n) v += w[k] * colcol[split_idx<KR>(kColPad + rr, HC)];
                             }
                         }
                         b[d] = v;
                     }
-                    const float v = b[1] + (gtab[y] * b[0] + gtab[n + y] * b[1] + gtab[2 * n + y] * b[2] +
-                                            gtab[3 * n + y] * b[3]);
+                    const int gi = split_idx<KR>(y, n >> 3);
+                    const float v = b[1] + (gtab[gi] * b[0] + gtab[n + gi] * b[1] + gtab[2 * n + gi] * b[2] +
+                                            gtab[3 * n + gi] * b[3]);
                     dst[y] = v;
                     lsum += v;
                 }
