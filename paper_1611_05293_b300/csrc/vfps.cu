@@ -526,6 +526,7 @@ struct Group {
     int prec = 0, ni = 4, W = 8, fast = 0;
     int tps = 1;  // FP32 streaming kernel: consecutive tiles per CTA
     int kr = 4;   // FP32 streaming kernel: rows per lane of the kick/FP blocks
+    int n = 0;    // grid size shared by the group's instances
     size_t smem = 0;
     int ntiles = 0;
     void* ddescs = nullptr;  // array of Desc<T>
@@ -590,16 +591,25 @@ int launch_step_ni(const Group& g, cudaStream_t s)
     return VFPS_EINVAL;
 }
 
+template <int W, int KR, int NC>
+int launch_fast_k(const Group& g, cudaStream_t s)
+{
+    CU(launch_pdl(step_kernel_f32<W, KR, NC>, g.ntiles / g.tps, W * 32, g.smem, s, (const Desc<float>*)g.ddescs,
+                  (const int2*)g.dtiles, g.tps));
+    return VFPS_OK;
+}
+
+// The hot grid sizes (N = 256 scans, N = 1024 single runs) have their own
+// compiled instances with n fixed at compile time.
 template <int W>
 int launch_fast_t(const Group& g, cudaStream_t s)
 {
-    if (g.kr == 8)
-        CU(launch_pdl(step_kernel_f32<W, 8>, g.ntiles / g.tps, W * 32, g.smem, s, (const Desc<float>*)g.ddescs,
-                      (const int2*)g.dtiles, g.tps));
-    else
-        CU(launch_pdl(step_kernel_f32<W, 4>, g.ntiles / g.tps, W * 32, g.smem, s, (const Desc<float>*)g.ddescs,
-                      (const int2*)g.dtiles, g.tps));
-    return VFPS_OK;
+    if (g.kr == 8) {
+        if (g.n == 256) return launch_fast_k<W, 8, 256>(g, s);
+        if (g.n == 1024) return launch_fast_k<W, 8, 1024>(g, s);
+        return launch_fast_k<W, 8, 0>(g, s);
+    }
+    return launch_fast_k<W, 4, 0>(g, s);
 }
 
 int launch_step(const Group& g, cudaStream_t s)
@@ -678,12 +688,18 @@ int init_kernels()
     if (lim <= 0) return VFPS_ECUDA;
     CU(set_smem_attr_all<float>(lim));
     CU(set_smem_attr_all<double>(lim));
-    CU(set_smem_attr_one(step_kernel_f32<8, 8>, lim));
-    CU(set_smem_attr_one(step_kernel_f32<4, 8>, lim));
-    CU(set_smem_attr_one(step_kernel_f32<2, 8>, lim));
-    CU(set_smem_attr_one(step_kernel_f32<8, 4>, lim));
-    CU(set_smem_attr_one(step_kernel_f32<4, 4>, lim));
-    CU(set_smem_attr_one(step_kernel_f32<2, 4>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<8, 8, 0>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<4, 8, 0>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<2, 8, 0>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<8, 4, 0>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<4, 4, 0>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<2, 4, 0>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<8, 8, 256>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<4, 8, 256>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<2, 8, 256>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<8, 8, 1024>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<4, 8, 1024>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<2, 8, 1024>, lim));
     g_kernels_ready = 1;
     return VFPS_OK;
 }
@@ -697,6 +713,7 @@ Group single_group(const Instance& I)
     g.W = I.W;
     g.fast = I.fast;
     g.kr = fast_kr(I.p.n);
+    g.n = I.p.n;
     g.smem = I.fast ? std::max(fast_smem(&I.p, I.W), step_smem(&I.p, I.W)) : step_smem(&I.p, I.W);
     g.ntiles = I.ntiles;
     g.ddescs = I.ddesc;
@@ -1092,6 +1109,7 @@ int rebuild_groups(vfps_batch* b)
         }
         g.ntiles = nt;
         g.kr = fast_kr(kv.second[0]->p.n);  // a group shares n
+        g.n = kv.second[0]->p.n;
         if (g.fast) {
             // a strip of tps consecutive tiles per CTA: the largest divisor of
             // the tiles per instance that still leaves two CTAs per SM (long
@@ -1495,6 +1513,7 @@ extern "C" int vfps_step_static(const vfps_params* params, int model, double Pi,
     g.W = W;
     g.fast = fast;
     g.kr = fast_kr(params->n);
+    g.n = params->n;
     g.ntiles = I.ntiles;
     g.smem = fast ? std::max(fast_smem(params, W), step_smem(params, W)) : step_smem(params, W);
     g.ddescs = d + kOffDesc;

@@ -128,8 +128,11 @@ __device__ __forceinline__ void rotate_block(const float* __restrict__ ring, int
 // needs (A2 = s - 2 + kColPad: column index of row y0+s-2, minus y0; PAR =
 // parity of its 16-byte chunk, fixed per column for 8-row blocks); w are the
 // column's kick weights (pending scale included), s its node shift; g holds
-// the FP weights g_k(y) as four rows of n (split layout for KR = 8).
-template <int O2, int PAR, int KR>
+// the FP weights g_k(y) as four rows of n (split layout for KR = 8), with
+// the identity folded into the centre tap: psi_c(y) = sum_k g_k(y) psi_b(y-1+k).
+// SMALL: s is -1 or 0 (kicks under one cell), where the edge test reduces to
+// the rows just outside the grid.
+template <int O2, int PAR, int KR, bool SMALL>
 __device__ __forceinline__ float kick_fp_column(const float* __restrict__ colcol, int HC,
                                                 const float* __restrict__ g, float* __restrict__ dst, int n, int s,
                                                 int A2, float4 w, int lane)
@@ -165,15 +168,26 @@ __device__ __forceinline__ float kick_fp_column(const float* __restrict__ colcol
             }
         }
         // psi_b(y0 + j - 1): nodes y0+j+s-2 .. y0+j+s+1
-        const int jlo = lo - y0 + 1, jhi = hi - y0 + 1;
         float b[NB];
 #pragma unroll
         for (int j = 0; j < NB; ++j) {
             float v = w.x * win[O2 + j];
             v = fmaf(w.y, win[O2 + j + 1], v);
             v = fmaf(w.z, win[O2 + j + 2], v);
-            v = fmaf(w.w, win[O2 + j + 3], v);
-            b[j] = (j >= jlo && j <= jhi) ? v : 0.f;
+            b[j] = fmaf(w.w, win[O2 + j + 3], v);
+        }
+        if constexpr (SMALL) {
+            // s in {-1, 0}: every on-grid row has its source within one cell
+            // of the grid, so only the rows -1, n, n+1 are zeroed
+            if (y0 == 0) b[0] = 0.f;
+            if (y0 + KR == n) {
+                b[NB - 2] = 0.f;
+                b[NB - 1] = 0.f;
+            }
+        } else {
+            const int jlo = lo - y0 + 1, jhi = hi - y0 + 1;
+#pragma unroll
+            for (int j = 0; j < NB; ++j) b[j] = (j >= jlo && j <= jhi) ? b[j] : 0.f;
         }
 #pragma unroll
         for (int q4 = 0; q4 < KR / 4; ++q4) {
@@ -189,8 +203,7 @@ __device__ __forceinline__ float kick_fp_column(const float* __restrict__ colcol
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const float* bb = b + 4 * q4 + k;
-                const float inc = ga[k] * bb[0] + gb[k] * bb[1] + gc[k] * bb[2] + gd[k] * bb[3];
-                c[k] = bb[1] + inc;
+                c[k] = ga[k] * bb[0] + gb[k] * bb[1] + gc[k] * bb[2] + gd[k] * bb[3];
             }
             *reinterpret_cast<float4*>(dst + y) = make_float4(c[0], c[1], c[2], c[3]);
             lsum += (c[0] + c[1]) + (c[2] + c[3]);
@@ -310,7 +323,7 @@ __device__ __forceinline__ void rotate_column(const float* __restrict__ ring, in
 // arithmetic.  psi_a stays unscaled; the pending renormalisation factor is
 // part of the kick weights.  The column sums of a strip are made visible
 // with one fence per thread before the CTA takes its ticket.
-template <int W, int KR>
+template <int W, int KR, int NC>
 __global__ void __launch_bounds__(W * 32, 32 / W)
 step_kernel_f32(const Desc<float>* __restrict__ descs, const int2* __restrict__ tiles, int tps)
 {
@@ -319,7 +332,9 @@ step_kernel_f32(const Desc<float>* __restrict__ descs, const int2* __restrict__ 
     const int2 first = tiles[blockIdx.x * tps];
     const Desc<float>& D = descs[first.x];
     const int xs = first.y;
-    const int n = D.n, ld = D.ld, h = D.h;
+    // NC > 0: the grid size is a compile-time constant (the hot sizes), so
+    // loop bounds and pitches fold into the code; ld = n for FP32 then
+    const int n = NC ? NC : D.n, ld = NC ? NC : D.ld, h = D.h;
     const int RP = fast_row_pad(h);
     const int P = ring_pitch(n, RP);
     const int R = ring_slots(W, h);
@@ -350,7 +365,7 @@ step_kernel_f32(const Desc<float>* __restrict__ descs, const int2* __restrict__ 
         const float yf = float(y);
         const int gi = split_idx<KR>(y, n >> 3);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) gtab[k * n + gi] = D.ga[k] + D.gb[k] * yf;
+        for (int k = 0; k < 4; ++k) gtab[k * n + gi] = (k == 1 ? 1.f : 0.f) + (D.ga[k] + D.gb[k] * yf);
     }
     // what the previous step wrote (state word, psi, kick table) is read from here on
     pdl_wait();
@@ -396,15 +411,16 @@ step_kernel_f32(const Desc<float>* __restrict__ descs, const int2* __restrict__ 
             float lsum = 0.f;
             if (s >= -4 && s <= 4) {
                 const int A2 = s - 2 + kColPad;  // column index of row y0+s-2, minus y0
+                // A2 = s + 14 with |s| <= 4: (A2 & 7) = 5 and 6 are s = -1 and 0 only
                 switch (KR == 8 ? (A2 & 7) : (A2 & 3)) {
-                case 0: lsum = kick_fp_column<0, 0, KR>(colcol, HC, gtab, dst, n, s, A2, kw, lane); break;
-                case 1: lsum = kick_fp_column<1, 0, KR>(colcol, HC, gtab, dst, n, s, A2, kw, lane); break;
-                case 2: lsum = kick_fp_column<2, 0, KR>(colcol, HC, gtab, dst, n, s, A2, kw, lane); break;
-                case 3: lsum = kick_fp_column<3, 0, KR>(colcol, HC, gtab, dst, n, s, A2, kw, lane); break;
-                case 4: lsum = kick_fp_column<0, 1, KR>(colcol, HC, gtab, dst, n, s, A2, kw, lane); break;
-                case 5: lsum = kick_fp_column<1, 1, KR>(colcol, HC, gtab, dst, n, s, A2, kw, lane); break;
-                case 6: lsum = kick_fp_column<2, 1, KR>(colcol, HC, gtab, dst, n, s, A2, kw, lane); break;
-                default: lsum = kick_fp_column<3, 1, KR>(colcol, HC, gtab, dst, n, s, A2, kw, lane); break;
+                case 0: lsum = kick_fp_column<0, 0, KR, false>(colcol, HC, gtab, dst, n, s, A2, kw, lane); break;
+                case 1: lsum = kick_fp_column<1, 0, KR, false>(colcol, HC, gtab, dst, n, s, A2, kw, lane); break;
+                case 2: lsum = kick_fp_column<2, 0, KR, false>(colcol, HC, gtab, dst, n, s, A2, kw, lane); break;
+                case 3: lsum = kick_fp_column<3, 0, KR, false>(colcol, HC, gtab, dst, n, s, A2, kw, lane); break;
+                case 4: lsum = kick_fp_column<0, 1, KR, false>(colcol, HC, gtab, dst, n, s, A2, kw, lane); break;
+                case 5: lsum = kick_fp_column<1, 1, KR, KR == 8>(colcol, HC, gtab, dst, n, s, A2, kw, lane); break;
+                case 6: lsum = kick_fp_column<2, 1, KR, KR == 8>(colcol, HC, gtab, dst, n, s, A2, kw, lane); break;
+                default: lsum = kick_fp_column<3, 1, KR, false>(colcol, HC, gtab, dst, n, s, A2, kw, lane); break;
                 }
             } else {
                 // large kick: plain per-row evaluation with bounds
@@ -426,8 +442,8 @@ step_kernel_f32(const Desc<float>* __restrict__ descs, const int2* __restrict__ 
                         b[d] = v;
                     }
                     const int gi = split_idx<KR>(y, n >> 3);
-                    const float v = b[1] + (gtab[gi] * b[0] + gtab[n + gi] * b[1] + gtab[2 * n + gi] * b[2] +
-                                            gtab[3 * n + gi] * b[3]);
+                    const float v = gtab[gi] * b[0] + gtab[n + gi] * b[1] + gtab[2 * n + gi] * b[2] +
+                                    gtab[3 * n + gi] * b[3];
                     dst[y] = v;
                     lsum += v;
                 }
