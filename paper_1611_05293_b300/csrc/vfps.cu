@@ -224,8 +224,7 @@ struct Instance {
     double* colsum = nullptr;
     double* rho = nullptr;
     void* kick = nullptr;
-    void* kickw = nullptr;   // FP32: float4 per column
-    int* kicks = nullptr;    // FP32: int per column
+    void* kickw = nullptr;   // FP32: two float4 per column
     double* pring = nullptr;
     double* qring = nullptr;
     DevState* st = nullptr;
@@ -265,8 +264,7 @@ size_t instance_bytes(const vfps_params* p, int ring, size_t* offs)
     take(9, sizeof(DevState));           // state
     take(10, sizeof(Desc<double>));      // descriptor
     take(11, sizeof(int2) * (size_t)((n + 1) / 2 + 1));  // tiles (W >= 2)
-    take(12, (size_t)n * 16);            // kick weights (FP32 path)
-    take(13, (size_t)n * 4);             // kick shifts (FP32 path)
+    take(12, (size_t)n * 32);            // kick table (FP32 path)
     return align_up(o, kAlign);
 }
 
@@ -282,7 +280,6 @@ void fill_desc(Instance& I)
     d.rho = I.rho;
     d.kick = (T*)I.kick;
     d.kickw = (float4*)I.kickw;
-    d.kicks = I.kicks;
     d.pring = I.pring;
     d.qring = I.qring;
     d.st = I.st;
@@ -458,7 +455,7 @@ int create_instance(const vfps_params* p, const double* psi0, int ring, cudaStre
     I->ring = ring;
     I->delta = 2.0 * p->half_width / (p->n - 1);
     I->phi = 2.0 * kPi / p->steps_per_period;
-    size_t offs[14];
+    size_t offs[13];
     I->dbytes = instance_bytes(p, ring, offs);
     if (cudaMalloc(&I->dmem, I->dbytes) != cudaSuccess) {
         cudaGetLastError();
@@ -479,7 +476,6 @@ int create_instance(const vfps_params* p, const double* psi0, int ring, cudaStre
     I->ddesc = b + offs[10];
     I->dtiles = (int2*)(b + offs[11]);
     I->kickw = b + offs[12];
-    I->kicks = (int*)(b + offs[13]);
     // twiddles exp(-2 pi i k/M), FP64 on the host
     {
         int K = I->M / 2;
@@ -1143,7 +1139,7 @@ extern "C" {
 int64_t vfps_batch_slot_bytes(const vfps_params* params)
 {
     if (check_params(params)) return -1;
-    size_t offs[14];
+    size_t offs[13];
     return (int64_t)instance_bytes(params, kRingDefault / 2, offs);
 }
 
@@ -1179,7 +1175,7 @@ int vfps_batch_add(vfps_batch* b, const vfps_params* params, const double* psi0,
             break;
         }
     if (free_slot < 0) return VFPS_EBUSY;
-    size_t offs[14];
+    size_t offs[13];
     long long need = (long long)instance_bytes(params, kRingDefault / 2, offs);
     if (b->budget > 0 && b->used + need > b->budget) return VFPS_EBUSY;
     size_t fr = 0, tot = 0;
@@ -1373,8 +1369,7 @@ constexpr size_t kOffColsum = kOffState + sa(sizeof(DevState));
 constexpr size_t kOffRho = kOffColsum + sa(sizeof(double) * kStaticMaxN);
 constexpr size_t kOffKick = kOffRho + sa(sizeof(double) * kStaticMaxN);
 constexpr size_t kOffKickW = kOffKick + sa(sizeof(float) * kStaticMaxN);
-constexpr size_t kOffKickS = kOffKickW + sa(sizeof(float4) * kStaticMaxN);
-constexpr size_t kOffZhat = kOffKickS + sa(sizeof(int) * kStaticMaxN);
+constexpr size_t kOffZhat = kOffKickW + sa(2 * sizeof(float4) * kStaticMaxN);
 constexpr size_t kOffTw = kOffZhat + sa(sizeof(float2) * (kStaticMaxFFT / 2 + 1));
 constexpr size_t kOffRings = kOffTw + sa(sizeof(float2) * (kStaticMaxFFT / 2));
 constexpr size_t STATIC_SCRATCH_BYTES = kOffRings + sa(sizeof(double) * 4);
@@ -1482,7 +1477,6 @@ extern "C" int vfps_step_static(const vfps_params* params, int model, double Pi,
     I.rho = (double*)(d + kOffRho);
     I.kick = d + kOffKick;
     I.kickw = d + kOffKickW;
-    I.kicks = (int*)(d + kOffKickS);
     I.pring = (double*)(d + kOffRings);
     I.qring = (double*)(d + kOffRings) + 2;
     I.st = (DevState*)(d + kOffState);

@@ -268,10 +268,23 @@ __host__ __device__ inline int ring_slots(int W, int h)
     return r;
 }
 
+// Shared memory of the FP32 streaming kernel: ring, psi_a columns, FP
+// weights, and a 4-stage buffer of the tiles' kick-table entries.
 __host__ inline size_t fast_ring_smem(int n, int h, int W)
 {
     const int RP = fast_row_pad(h);
-    return (size_t)ring_slots(W, h) * ring_pitch(n, RP) * 4 + (size_t)W * cola_pitch(n) * 4 + (size_t)n * 16;
+    return (size_t)ring_slots(W, h) * ring_pitch(n, RP) * 4 + (size_t)W * cola_pitch(n) * 4 + (size_t)n * 16 +
+           (size_t)4 * W * 32;
+}
+
+// Copy the kick-table entries (two float4) of column x into dst (lanes 0 and
+// 1 of the calling warp); columns past the grid get zeros.
+__device__ __forceinline__ void load_kick(float4* dst, const float4* __restrict__ kickw, int x, int n, int lane)
+{
+    if (lane < 2) {
+        const bool ok = x < n;
+        cp_async16(dst + lane, ok ? kickw + 2 * x + lane : kickw, ok ? 16 : 0);
+    }
 }
 
 // Rotation of one column x (rows 0..n-1, four per lane and pass) when the
@@ -344,13 +357,13 @@ step_kernel_f32(const Desc<float>* __restrict__ descs, const int2* __restrict__ 
     const int T = min(tps, (n - xs + W - 1) / W);
     const float cm1 = D.cm1, sn = D.sn, c = D.c;
     const float4* __restrict__ kickw = D.kickw;
-    const int* __restrict__ kicks = D.kicks;
     float* __restrict__ colsum = D.colsum;
 
     float* ring = reinterpret_cast<float*>(smem);
     float* colA = ring + R * P;
     float* gtab = colA + W * PA;  // g_0(y) .. g_3(y), n each (split layout for KR = 8)
     float* colcol = colA + warp * PA;  // this warp's psi_a column, padded
+    float4* kbuf = reinterpret_cast<float4*>(gtab + 4 * n) + 2 * warp;  // stage k: kbuf + 2 W k
     pdl_trigger();
 
     // padding rows of every ring slot and of this warp's psi_a column: zero
@@ -374,8 +387,12 @@ step_kernel_f32(const Desc<float>* __restrict__ descs, const int2* __restrict__ 
     float* __restrict__ out = D.psi[par ^ 1];
     // window of tile 0, then the new columns of tile 1
     load_columns<W>(ring, R, P, RP, in, ld, n, xs - h, W + 2 * h);
+    load_kick(kbuf, kickw, xs + warp, n, lane);
     cp_async_commit();
-    if (T > 1) load_columns<W>(ring, R, P, RP, in, ld, n, xs + W + h, W);
+    if (T > 1) {
+        load_columns<W>(ring, R, P, RP, in, ld, n, xs + W + h, W);
+        load_kick(kbuf + 2 * W, kickw, xs + W + warp, n, lane);
+    }
     cp_async_commit();
 
     for (int j = 0; j < T; ++j) {
@@ -405,8 +422,9 @@ step_kernel_f32(const Desc<float>* __restrict__ descs, const int2* __restrict__ 
         }
         __syncwarp();
         if (active) {
-            const float4 kw = kickw[x];
-            const int s = kicks[x];
+            const float4* kj = kbuf + 2 * W * (j & 3);
+            const float4 kw = kj[0];
+            const int s = __float_as_int(kj[1].x);
             float* dst = out + (size_t)x * ld;
             float lsum = 0.f;
             if (s >= -4 && s <= 4) {
@@ -454,7 +472,10 @@ step_kernel_f32(const Desc<float>* __restrict__ descs, const int2* __restrict__ 
             if (lane == 0) colsum[x] = csum;
         }
         __syncthreads();  // the ring slots of columns xs+jW-h .. xs+jW+W-h-1 are free
-        if (j + 2 < T) load_columns<W>(ring, R, P, RP, in, ld, n, xs + (j + 2) * W + h, W);
+        if (j + 2 < T) {
+            load_columns<W>(ring, R, P, RP, in, ld, n, xs + (j + 2) * W + h, W);
+            load_kick(kbuf + 2 * W * ((j + 2) & 3), kickw, xs + (j + 2) * W + warp, n, lane);
+        }
         cp_async_commit();
     }
     cp_async_wait_0();

@@ -14,8 +14,9 @@
 //   colsum   n values of T, sum_y psi_c[x][y] of the step just written (scratch)
 //   rho      n doubles, profile of the current (renormalised) state
 //   kick     n T, p-shift of column x in grid cells for the next step
-//   kickw    n float4 (FP32 instances): cubic weights of that shift times the
-//            pending scale; kicks: n ints, the node shift floor(-kick)
+//   kickw    2n float4 (FP32 instances): per column x, [2x] the cubic weights
+//            of that shift times the pending scale, [2x+1].x the node shift
+//            floor(-kick) as int bits
 //   pring    ring of CSR powers, pring[t] = P(psi_t)
 //   qring    ring of charges before renormalisation, qring[t] = Q of step t
 //   st       DevState: pending scale, step count, ticket, parity, status
@@ -51,8 +52,7 @@ struct Desc {
     T* colsum;                         // n column sums (scratch)
     double* rho;
     T* kick;
-    float4* kickw;                     // FP32 path: per-column kick weights x pending scale
-    int* kicks;                        // FP32 path: per-column kick node shift
+    float4* kickw;                     // FP32 path: 2 per column, see layout above
     double* pring;
     double* qring;
     DevState* st;
@@ -432,8 +432,8 @@ __device__ void finalise(const Desc<T>& D, unsigned char* smem, int is_step)
             const float ks = -k, fk = floorf(ks);
             float w[4];
             lagrange_w<float, 4>(ks - fk, w);
-            D.kickw[x] = make_float4(s_new * w[0], s_new * w[1], s_new * w[2], s_new * w[3]);
-            D.kicks[x] = int(fk);
+            D.kickw[2 * x] = make_float4(s_new * w[0], s_new * w[1], s_new * w[2], s_new * w[3]);
+            D.kickw[2 * x + 1] = make_float4(__int_as_float(int(fk)), 0.f, 0.f, 0.f);
         }
     }
     if (tid == 0) {
