@@ -276,7 +276,7 @@ void fill_desc(Instance& I)
     d.psi[1] = (T*)I.psi[1];
     d.zhat = (const typename C2<T>::type*)I.zhat;
     d.tw = (const typename C2<T>::type*)I.tw;
-    d.colsum = reinterpret_cast<T*>(I.colsum);
+    d.colsum = I.colsum;
     d.rho = I.rho;
     d.kick = (T*)I.kick;
     d.kickw = (float4*)I.kickw;

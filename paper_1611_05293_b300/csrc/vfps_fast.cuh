@@ -357,7 +357,7 @@ step_kernel_f32(const Desc<float>* __restrict__ descs, const int2* __restrict__ 
     const int T = min(tps, (n - xs + W - 1) / W);
     const float cm1 = D.cm1, sn = D.sn, c = D.c;
     const float4* __restrict__ kickw = D.kickw;
-    float* __restrict__ colsum = D.colsum;
+    double* __restrict__ colsum = D.colsum;
 
     float* ring = reinterpret_cast<float*>(smem);
     float* colA = ring + R * P;
@@ -466,7 +466,7 @@ step_kernel_f32(const Desc<float>* __restrict__ descs, const int2* __restrict__ 
                     lsum += v;
                 }
             }
-            float csum = lsum;
+            double csum = double(lsum);  // FP32 lane partials, FP64 across lanes
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) csum += __shfl_down_sync(0xffffffffu, csum, o);
             if (lane == 0) colsum[x] = csum;

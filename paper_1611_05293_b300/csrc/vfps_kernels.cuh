@@ -11,7 +11,7 @@
 //            ping-pong buffers, device-side parity flips every step
 //   zhat     M/2+1 complex T, dimensionless impedance at kappa_k
 //   tw       M/2 complex T, exp(-2 pi i k/M)
-//   colsum   n values of T, sum_y psi_c[x][y] of the step just written (scratch)
+//   colsum   n doubles, sum_y psi_c[x][y] of the step just written (scratch)
 //   rho      n doubles, profile of the current (renormalised) state
 //   kick     n T, p-shift of column x in grid cells for the next step
 //   kickw    2n float4 (FP32 instances): per column x, [2x] the cubic weights
@@ -49,7 +49,7 @@ struct Desc {
     T* psi[2];
     const typename C2<T>::type* zhat;
     const typename C2<T>::type* tw;
-    T* colsum;                         // n column sums (scratch)
+    double* colsum;                    // n column sums (scratch)
     double* rho;
     T* kick;
     float4* kickw;                     // FP32 path: 2 per column, see layout above
@@ -210,14 +210,13 @@ template <typename T2> __device__ __forceinline__ T2 cmulc(T2 a, T2 b)  // a * c
 // is_step = 1 after a time step (ring slot t+1, t advances); 0 for the
 // prologue that only (re)computes the wake of the current state.
 // Shared memory (bytes) for FFT length M and n columns: two H-point complex
-// buffers, twiddles (H) and impedance (H+1) complex values, the column sums
-// zero-padded to M, H/2+1 power terms and a reduction area.
+// buffers, twiddles (H) and impedance (H+1) complex values, the n column
+// sums and H/2+1 power terms as doubles, and a reduction area.
 __host__ __device__ inline size_t finalise_smem(int M, int n, int nt, int complex_bytes)
 {
     (void)nt;
-    (void)n;
-    const size_t H = (size_t)M / 2, es = (size_t)complex_bytes / 2;
-    return (4 * H + 2) * complex_bytes + (size_t)M * es + (H / 2 + 4) * es + 64;
+    const size_t H = (size_t)M / 2;
+    return (4 * H + 2) * complex_bytes + (size_t)((n + 1) & ~1) * 8 + (H / 2 + 2) * 8 + 64;
 }
 
 template <typename T2, bool INV>
@@ -346,9 +345,9 @@ __device__ void finalise(const Desc<T>& D, unsigned char* smem, int is_step)
     T2* bufB = bufA + H;
     T2* tw = bufB + H;
     T2* zh = tw + H;
-    T* cs = reinterpret_cast<T*>(zh + H + 2);  // M values: column sums, then zeros
-    T* pterm = cs + M;                          // H/2+1 power terms
-    double* red = reinterpret_cast<double*>(pterm + H / 2 + 4);
+    double* cs = reinterpret_cast<double*>(zh + H + 2);  // n column sums
+    double* pterm = cs + ((n + 1) & ~1);                 // H/2+1 power terms
+    double* red = pterm + H / 2 + 2;
 
     // one round of asynchronous copies: twiddles, impedance, column sums
     // (written by the other CTAs of this step; .cg keeps L1 out of the way)
@@ -358,32 +357,36 @@ __device__ void finalise(const Desc<T>& D, unsigned char* smem, int is_step)
         const char* gzh = reinterpret_cast<const char*>(D.zhat);
         const char* gcs = reinterpret_cast<const char*>(D.colsum);
         const int ntw = H * CB / 16, zbytes = (H + 1) * CB, nzh = (zbytes + 15) / 16;
-        const int cbytes = n * (int)sizeof(T), ncs = M * (int)sizeof(T) / 16;
+        const int cbytes = n * 8, ncs = (cbytes + 15) / 16;
         for (int i = tid; i < ntw; i += nt) cp_async16(reinterpret_cast<char*>(tw) + 16 * i, gtw + 16 * i, 16);
         for (int i = tid; i < nzh; i += nt)
             cp_async16(reinterpret_cast<char*>(zh) + 16 * i, gzh + 16 * i, min(16, zbytes - 16 * i));
-        for (int i = tid; i < ncs; i += nt) {
-            const int b = max(0, min(16, cbytes - 16 * i));
-            cp_async16(reinterpret_cast<char*>(cs) + 16 * i, b ? gcs + 16 * i : gcs, b);
-        }
+        for (int i = tid; i < ncs; i += nt)
+            cp_async16(reinterpret_cast<char*>(cs) + 16 * i, gcs + 16 * i, min(16, cbytes - 16 * i));
         cp_async_commit();
         cp_async_wait_0();
         __syncthreads();
     }
+    // transform input z_j = cs_2j + i cs_2j+1 (zero-padded), in T
+    for (int j = tid; j < H; j += nt) {
+        const int x = 2 * j;
+        bufB[j] = T2{x < n ? T(cs[x]) : T(0), x + 1 < n ? T(cs[x + 1]) : T(0)};
+    }
+    __syncthreads();
 
-    // forward transform of z_j = cs_2j + i cs_2j+1; meanwhile warp 0 sums
-    // the charge Q = Delta^2 sum cs into red[0]
-    T2* Z = fft_h<T, false>(reinterpret_cast<const T2*>(cs), bufA, bufB, tw, H, [&] {
+    // forward transform; meanwhile warp 0 sums the charge Q = Delta^2 sum cs
+    // into red[0] in FP64
+    T2* Z = fft_h<T, false>(bufB, bufA, bufB, tw, H, [&] {
         if (tid < 32) {
-            const T s = warp_fixed_sum<T>(cs, n);
-            if (tid == 0) red[0] = double(s);
+            const double sum = warp_fixed_sum<double>(cs, n);
+            if (tid == 0) red[0] = sum;
         }
     });
-    const T Q = T(D.delta * D.delta) * T(red[0]);
-    const bool bad = !(Q > T(0)) || !isfinite(Q);
-    const T s_new = (D.renorm && !bad) ? T(1) / Q : T(1);
-    const T sd = s_new * T(D.delta);  // rho_x = sd * cs_x
-    const T sk = sd * T(D.delta);     // rho~_k = Delta * DFT(rho)_k = sk * X_k
+    const double Q = D.delta * D.delta * red[0];
+    const bool bad = !(Q > 0.0) || !isfinite(Q);
+    const double s_new = (D.renorm && !bad) ? 1.0 / Q : 1.0;
+    const double sd = s_new * D.delta;        // rho_x = sd * cs_x
+    const T sk = T(sd * D.delta);             // rho~_k = Delta * DFT(rho)_k = sk * X_k
 
     // per pair (k, H-k): split, multiply by the impedance, power, fold back
     for (int p = tid; p <= H / 2; p += nt) {
@@ -410,15 +413,16 @@ __device__ void finalise(const Desc<T>& D, unsigned char* smem, int is_step)
             Z[k] = cadd(S, iuD);
             if (kk != k) Z[kk] = T2{S.x - iuD.x, iuD.y - S.y};  // conj(S - i u Df)
         }
-        pterm[p] = term;
+        pterm[p] = double(term);
     }
     __syncthreads();
 
     // inverse transform; meanwhile warp 0 sums the power terms into red[1]
+    // in FP64
     T2* y = fft_h<T, true>(Z, Z == bufA ? bufB : bufA, Z, tw, H, [&] {
         if (tid < 32) {
-            const T s = warp_fixed_sum<T>(pterm, H / 2 + 1);
-            if (tid == 0) red[1] = double(s);
+            const double sum = warp_fixed_sum<double>(pterm, H / 2 + 1);
+            if (tid == 0) red[1] = sum;
         }
     });
     const T kpv = T(D.kick_per_v * D.dkappa);
@@ -426,13 +430,14 @@ __device__ void finalise(const Desc<T>& D, unsigned char* smem, int is_step)
         const T2 v = y[x >> 1];
         const T k = kpv * ((x & 1) ? v.y : v.x);
         D.kick[x] = k;
-        D.rho[x] = double(sd * cs[x]);
+        D.rho[x] = sd * cs[x];
         if constexpr (sizeof(T) == 4) {
             // psi_b(y) = sum_k w_k psi_a(y + s - 1 + k): source y - kick, s = floor(-kick)
             const float ks = -k, fk = floorf(ks);
             float w[4];
             lagrange_w<float, 4>(ks - fk, w);
-            D.kickw[2 * x] = make_float4(s_new * w[0], s_new * w[1], s_new * w[2], s_new * w[3]);
+            const float sf = float(s_new);
+            D.kickw[2 * x] = make_float4(sf * w[0], sf * w[1], sf * w[2], sf * w[3]);
             D.kickw[2 * x + 1] = make_float4(__int_as_float(int(fk)), 0.f, 0.f, 0.f);
         }
     }
@@ -441,15 +446,15 @@ __device__ void finalise(const Desc<T>& D, unsigned char* smem, int is_step)
         DevState* st = D.st;
         long long t = st->t;
         if (is_step) {
-            D.qring[t & D.ring_mask] = double(Q);
+            D.qring[t & D.ring_mask] = Q;
             D.pring[(t + 1) & D.ring_mask] = P;
             st->t = t + 1;
             st->parity ^= 1;
-            st->qlast = double(Q);
+            st->qlast = Q;
         } else {
             D.pring[t & D.ring_mask] = P;
         }
-        st->scale = double(s_new);
+        st->scale = s_new;
         if (bad || !isfinite(P)) st->status = -5;
         st->ticket = 0u;
     }
@@ -541,7 +546,7 @@ step_kernel(const Desc<T>* __restrict__ descs, const int2* __restrict__ tiles)
     __syncwarp();
 
     // Fokker-Planck -> psi_c, column sum
-    T csum = T(0);
+    double csum = 0.0;
     if (active) {
         const T* cb = colB + warp * n;
         T* dst = out + (size_t)x * ld;
@@ -560,7 +565,7 @@ step_kernel(const Desc<T>* __restrict__ descs, const int2* __restrict__ tiles)
             dst[y] = v;
             lsum += v;
         }
-        csum = lsum;
+        csum = double(lsum);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) csum += __shfl_down_sync(0xffffffffu, csum, o);
         if (lane == 0) {
@@ -598,8 +603,9 @@ project_kernel(const Desc<T>* __restrict__ descs, const int2* __restrict__ tiles
     pdl_wait();
     const T* in = D.psi[D.st->parity];
     if (x < n) {
-        T s = T(0);
-        for (int y = lane; y < n; y += 32) s += in[(size_t)x * ld + y];
+        T ls = T(0);
+        for (int y = lane; y < n; y += 32) ls += in[(size_t)x * ld + y];
+        double s = double(ls);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
         if (lane == 0) {
