@@ -69,6 +69,24 @@ def rotation_matrix(n, L, steps, ni=4):
     return A
 
 
+def manhattan_matrices(n, L, steps, ni=4):
+    """(drift, RF kick) matrices of the Manhattan rotation.  The step h is
+    taken from the composite linear map [[1, h], [-h, 1 - h^2]] turning by
+    2 pi/steps: trace 2 - h^2 = 2 cos(2 pi/steps)."""
+    d = 2 * L / (n - 1)
+    h = math.sqrt(2.0 - 2.0 * math.cos(2 * math.pi / steps))
+    Dm = np.zeros((n * n, n * n))
+    Km = np.zeros((n * n, n * n))
+    for x in range(n):
+        for y in range(n):
+            q, p = -L + x * d, -L + y * d
+            for ix, w in _interp_rows(n, ni, (q - h * p + L) / d):    # drift: q -> q + h p
+                Dm[n * x + y, n * ix + y] += w
+            for iy, w in _interp_rows(n, ni, (p + h * q + L) / d):    # RF kick: p -> p - h q
+                Km[n * x + y, n * x + iy] += w
+    return Dm, Km
+
+
 def kick_matrix(n, L, steps, V, s_csr, ni=4):
     d = 2 * L / (n - 1)
     phi = 2 * np.pi / steps
@@ -118,13 +136,17 @@ def wake(n, L, pad, zre, zim, rho):
     return Vc.real, P
 
 
-def step(n, L, steps, beta, s_csr, pad, zre, zim, psi, ni=4, kind=1, renorm=True):
-    """One step: returns (psi_next, V, P)."""
+def step(n, L, steps, beta, s_csr, pad, zre, zim, psi, ni=4, kind=1, renorm=True, rotation=0):
+    """One step: returns (psi_next, V, P).  rotation 1 = Manhattan."""
     d = 2 * L / (n - 1)
     f = np.asarray(psi, dtype=np.float64).reshape(n * n)
     rho = d * f.reshape(n, n).sum(axis=1)
     V, P = wake(n, L, pad, zre, zim, rho)
-    a = rotation_matrix(n, L, steps, ni) @ f
+    if rotation == 1:
+        Dm, Km = manhattan_matrices(n, L, steps, ni)
+        a = Km @ (Dm @ f)
+    else:
+        a = rotation_matrix(n, L, steps, ni) @ f
     b = kick_matrix(n, L, steps, V, s_csr, ni) @ a
     c = fokker_planck_matrix(n, L, steps, beta, kind) @ b
     if renorm:

@@ -41,7 +41,8 @@ class _CParams(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("steps_per_period", ctypes.c_int),
                 ("interp_points", ctypes.c_int), ("clamp", ctypes.c_int),
                 ("fp_derivative", ctypes.c_int), ("pad_factor", ctypes.c_int),
-                ("renormalize", ctypes.c_int), ("half_width", ctypes.c_double),
+                ("renormalize", ctypes.c_int), ("rotation", ctypes.c_int),
+                ("half_width", ctypes.c_double),
                 ("beta", ctypes.c_double), ("s_csr", ctypes.c_double)]
 
 
@@ -58,6 +59,7 @@ class Params:
     fp_derivative: int = 1
     pad_factor: int = 2
     renormalize: int = 1
+    rotation: int = 0      # 0: standard rotation, 1: Manhattan (drift, then RF kick)
 
     @property
     def delta(self) -> float:
@@ -70,7 +72,7 @@ class Params:
 
     def c(self) -> _CParams:
         return _CParams(self.n, self.steps_per_period, self.interp_points, self.clamp,
-                        self.fp_derivative, self.pad_factor, self.renormalize,
+                        self.fp_derivative, self.pad_factor, self.renormalize, self.rotation,
                         self.half_width, self.beta, self.s_csr)
 
 
@@ -90,6 +92,10 @@ def lib():
         L.or_interp_p.argtypes = [P, _D, ctypes.c_int, ctypes.c_double]
         L.or_interp_p.restype = ctypes.c_double
         L.or_rotate.argtypes = [P, _D, _D]
+        L.or_drift.argtypes = [P, _D, _D]
+        L.or_rfkick.argtypes = [P, _D, _D]
+        L.or_manhattan_h.argtypes = [P]
+        L.or_manhattan_h.restype = ctypes.c_double
         L.or_project.argtypes = [P, _D, _D]
         L.or_project.restype = ctypes.c_double
         L.or_wake.argtypes = [P, _D, _D, _D, _D, _D]
@@ -130,6 +136,24 @@ def rotate(pr: Params, psi) -> np.ndarray:
     psi = _grid(psi, pr.n)
     out = np.empty_like(psi)
     lib().or_rotate(ctypes.byref(pr.c()), _p(psi), _p(out))
+    return out
+
+
+def manhattan_h(pr: Params) -> float:
+    return lib().or_manhattan_h(ctypes.byref(pr.c()))
+
+
+def drift(pr: Params, psi) -> np.ndarray:
+    psi = _grid(psi, pr.n)
+    out = np.empty_like(psi)
+    lib().or_drift(ctypes.byref(pr.c()), _p(psi), _p(out))
+    return out
+
+
+def rfkick(pr: Params, psi) -> np.ndarray:
+    psi = _grid(psi, pr.n)
+    out = np.empty_like(psi)
+    lib().or_rfkick(ctypes.byref(pr.c()), _p(psi), _p(out))
     return out
 
 

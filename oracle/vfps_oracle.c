@@ -13,6 +13,8 @@
  *                                                      lagrange-basis-polynomials)
  *   - clamped interpolation                          (Sec. III.A, Eq. clamping)
  *   - time step = rotation, kick, damping/diffusion  (Sec. III.B, f = f_rot+f_kick+f_damp,diff)
+ *   - Manhattan rotation: energy-dependent drift, then location-dependent
+ *     RF kick, each a 1-D interpolation          (Sec. III.B, symplectic rotation)
  *   - wake potential from the impedance              (Sec. II.B, Eq. wakepotential)
  *   - cubic first derivative for the FP term         (Sec. III.B, Eq. cubic diff)
  *   - CSR power P ~ int Re(Z) |rho~|^2 dk            (Sec. IV.C)
@@ -39,6 +41,7 @@ typedef struct or_params {
     int fp_derivative;     /* 1: cubic derivative (Eq. cubic diff), 0: central   */
     int pad_factor;        /* FFT length M = pad_factor * n                      */
     int renormalize;       /* 1: rescale the charge to 1 after every step        */
+    int rotation;          /* 0: standard rotation, 1: Manhattan rotation        */
     double half_width;     /* L: q, p in [-L, L]                                 */
     double beta;           /* 1 / (f_s tau_d)                                    */
     double s_csr;          /* collective kick strength                           */
@@ -139,6 +142,64 @@ double or_interp_p(const or_params* pr, const double* psi, int x, double yr)
     for (int b = 0; b < ni; ++b) v += w[b] * node(psi, n, x, my + f0 + b);
     if (pr->clamp) v = clamp_to(v, node(psi, n, x, my), node(psi, n, x, my + 1));
     return v;
+}
+
+/* 1-D interpolation along q of row y at x_r (the drift of the Manhattan
+ * rotation); clamping restricts to the two nearest nodes (Eq. clamping). */
+double or_interp_q(const or_params* pr, const double* psi, double xr, int y)
+{
+    int n = pr->n, ni = pr->interp_points;
+    if (outside(xr, n)) return 0.0;
+    double mxf = floor(xr);
+    int mx = (int)mxf;
+    double w[4];
+    or_lagrange(ni, xr - mxf, w);
+    int f0 = or_first_node(ni);
+    double v = 0.0;
+    for (int a = 0; a < ni; ++a) v += w[a] * node(psi, n, mx + f0 + a, y);
+    if (pr->clamp) v = clamp_to(v, node(psi, n, mx, y), node(psi, n, mx + 1, y));
+    return v;
+}
+
+/* Step parameter h of the Manhattan rotation.  The drift-kick map
+ * (q, p) -> (q + h p, p - h (q + h p)) has determinant 1 and trace 2 - h^2,
+ * i.e. it turns phase space by mu with 2 cos(mu) = 2 - h^2.  The paper does
+ * not state h; h = 2 sin(pi/steps_per_period) makes mu = 2 pi/steps, so that
+ * one synchrotron period is again exactly one turn. */
+double or_manhattan_h(const or_params* pr) { return 2.0 * sin(M_PI / pr->steps_per_period); }
+
+/* Manhattan rotation, first half (Sec. III.B, symplectic integrator): the
+ * energy-dependent drift q -> q + h p moves every row p along q, so the new
+ * value at (q, p) is the old one at (q - h p, p). */
+void or_drift(const or_params* pr, const double* in, double* out)
+{
+    int n = pr->n;
+    double d = grid_delta(pr), L = pr->half_width, h = or_manhattan_h(pr);
+#pragma omp parallel for schedule(static)
+    for (int x = 0; x < n; ++x) {
+        double q = -L + x * d;
+        for (int y = 0; y < n; ++y) {
+            double p = -L + y * d;
+            out[(size_t)x * n + y] = or_interp_q(pr, in, (q - h * p + L) / d, y);
+        }
+    }
+}
+
+/* Manhattan rotation, second half: the location-dependent RF kick
+ * p -> p - h q moves every column q along p, so the new value at (q, p) is
+ * the old one at (q, p + h q). */
+void or_rfkick(const or_params* pr, const double* in, double* out)
+{
+    int n = pr->n;
+    double d = grid_delta(pr), L = pr->half_width, h = or_manhattan_h(pr);
+#pragma omp parallel for schedule(static)
+    for (int x = 0; x < n; ++x) {
+        double q = -L + x * d;
+        for (int y = 0; y < n; ++y) {
+            double p = -L + y * d;
+            out[(size_t)x * n + y] = or_interp_p(pr, in, x, (p + h * q + L) / d);
+        }
+    }
 }
 
 /* RotationMap ("standard rotation", Sec. III.B): the new value at (q, p) is
@@ -299,8 +360,9 @@ double or_normalize(const or_params* pr, double* psi)
 }
 
 /* One time step, in the order
- *   1. profile and charge of psi_t,  2. wake and CSR power,  3. rotation,
- *   4. kick,  5. damping and diffusion,  6. renormalisation to charge 1.
+ *   1. profile and charge of psi_t,  2. wake and CSR power,  3. rotation
+ *   (standard, or Manhattan: drift then RF kick),  4. kick,  5. damping and
+ *   diffusion,  6. renormalisation to charge 1.
  * The collective force is held fixed over the step (Sec. II.A).
  * work must hold 2*n*n doubles.  Outputs (any may be NULL): rho and V of
  * psi_t (n each), P of psi_t, and the charge before renormalisation. */
@@ -317,9 +379,16 @@ void or_step(const or_params* pr, const double* zre, const double* zim,
     double P = 0.0;
     or_project(pr, psi, rho);
     or_wake(pr, zre, zim, rho, V, &P);
-    or_rotate(pr, psi, a);
-    or_kick(pr, V, a, b);
-    or_fokker_planck(pr, b, psi);
+    if (pr->rotation == 1) {
+        or_drift(pr, psi, a);
+        or_rfkick(pr, a, b);
+        or_kick(pr, V, b, a);
+        or_fokker_planck(pr, a, psi);
+    } else {
+        or_rotate(pr, psi, a);
+        or_kick(pr, V, a, b);
+        or_fokker_planck(pr, b, psi);
+    }
     double q = or_charge(pr, psi);
     if (pr->renormalize)
         for (size_t i = 0; i < nn; ++i) psi[i] /= q;
