@@ -65,6 +65,10 @@ typedef struct vfps_params {
                                  >= pad_factor*n; 2..64, pad_factor*n <= 16384; default 2 */
     int32_t precision;        /* 0: FP32 psi with FP64 sums (default); 1: FP64 throughout */
     int32_t renormalize;      /* 1: rescale the charge to 1 after every step (default)    */
+    int32_t rotation;         /* 0: standard rotation (default); 1: Manhattan rotation of
+                                 Sec. III.B: drift q -> q + h p, then RF kick p -> p - h q,
+                                 each a 1-D interpolation, h = 2 sin(pi/steps_per_period)
+                                 so that one period is exactly one turn                   */
     double half_width;        /* L: q, p in [-L, L]; default 6                            */
     double beta;              /* 1/(f_s tau_d) >= 0 (Eq. VFP); default 0                  */
 } vfps_params;

@@ -76,6 +76,7 @@ int check_params(const vfps_params* p)
     if (p->fp_derivative != 0 && p->fp_derivative != 1) return VFPS_EINVAL;
     if (p->precision != 0 && p->precision != 1) return VFPS_EINVAL;
     if (p->renormalize != 0 && p->renormalize != 1) return VFPS_EINVAL;
+    if (p->rotation != 0 && p->rotation != 1) return VFPS_EINVAL;
     if (!(p->half_width > 0.0) || !std::isfinite(p->half_width)) return VFPS_EINVAL;
     if (!(p->beta >= 0.0) || !std::isfinite(p->beta)) return VFPS_EINVAL;
     if (p->pad_factor < 2 || p->pad_factor > 64) return VFPS_EINVAL;
@@ -99,6 +100,8 @@ int halo_for(const vfps_params* p)
     double c = 0.5 * (p->n - 1);
     double cm1 = std::fabs(-2.0 * std::sin(0.5 * phi) * std::sin(0.5 * phi));
     double dmax = c * (cm1 + std::fabs(std::sin(phi)));
+    // Manhattan drift: row y moves by h (y - c), h = 2 sin(phi/2)
+    dmax = std::max(dmax, c * 2.0 * std::fabs(std::sin(0.5 * phi)));
     return 3 + (int)std::ceil(dmax);
 }
 
@@ -127,11 +130,12 @@ int device_smem_limit()
     return g_max_smem;
 }
 
-// The FP32 register-blocked kernel (vfps_fast.cuh) covers cubic
-// interpolation without clamping on grids with n a multiple of 4.
+// The FP32 register-blocked kernel (vfps_fast.cuh) covers the standard
+// rotation with cubic interpolation and no clamping on grids with n a
+// multiple of 4.
 bool fast_eligible(const vfps_params* p)
 {
-    return p->precision == 0 && p->interp_points == 4 && p->clamp == 0 && (p->n % 4) == 0;
+    return p->precision == 0 && p->interp_points == 4 && p->clamp == 0 && p->rotation == 0 && (p->n % 4) == 0;
 }
 
 // Rows per lane of the FP32 kernel's kick/FP blocks: 8 where n allows.
@@ -292,6 +296,8 @@ void fill_desc(Instance& I)
     d.clamp = I.p.clamp;
     d.h = halo_for(&I.p);
     d.ntiles = I.ntiles;
+    d.rotation = I.p.rotation;
+    d.hm = T(2.0 * std::sin(kPi / I.p.steps_per_period));
     double phi = I.phi;
     double s2 = std::sin(0.5 * phi);
     d.cm1 = T(-2.0 * s2 * s2);
@@ -794,6 +800,7 @@ void vfps_params_default(vfps_params* p)
     p->pad_factor = 2;
     p->precision = 0;
     p->renormalize = 1;
+    p->rotation = 0;
     p->half_width = 6.0;
     p->beta = 0.0;
 }

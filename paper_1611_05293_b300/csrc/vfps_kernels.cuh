@@ -59,8 +59,9 @@ struct Desc {
     int n, ld, M, logM;
     int ring_mask, renorm, clamp, h;  // h: column halo of the staged slab
     int ntiles;                        // CTAs per step of this instance
-    int pad0;
+    int rotation;                      // 0 standard rotation, 1 Manhattan rotation
     T cm1, sn, c;                      // cos(phi)-1, sin(phi), grid centre (n-1)/2
+    T hm;                              // Manhattan step h = 2 sin(pi/steps)
     T ga[4], gb[4];                    // FP increment weights g_k(y) = ga[k] + gb[k]*y
     double delta, dkappa;              // Delta, 2 pi/(M Delta)
     double kick_per_v;                 // S_csr * phi / Delta: grid cells per unit wake
@@ -137,6 +138,63 @@ __device__ __forceinline__ T rotate_cell(const T* __restrict__ slab, int P, int 
         acc = acc < lo ? lo : (acc > hi ? hi : acc);
     }
     return acc;
+}
+
+// ----------------------------------------------------------------------------
+// Manhattan rotation (Sec. III.B, symplectic rotation), first half: the drift
+// q -> q + h p moves row y along q by h (y - c) cells, so the new value at
+// (x, y) is the old one at x - h (y - c), interpolated along q from the
+// staged slab.  As for the 2-D rotation, the displacement is formed first
+// (small, exact in FP32 to ~1e-7 cells) and the node index from it.
+template <typename T, int NI>
+__device__ __forceinline__ T drift_cell(const T* __restrict__ slab, int P, int cx0, int x, int y, int n, T hm, T c,
+                                        int clamp)
+{
+    const T dx = -hm * (T(y) - c);
+    const T fx = dfloor(dx);
+    const int mx = x + int(fx);
+    if (mx <= -2 || mx >= n) return T(0);
+    T w[NI];
+    lagrange_w<T, NI>(dx - fx, w);
+    constexpr int F = -((NI - 1) / 2);
+    const T* base = slab + (mx + F - cx0) * P + (y + 2);
+    T acc = T(0);
+#pragma unroll
+    for (int a = 0; a < NI; ++a) acc += w[a] * base[a * P];
+    if (clamp) acc = clamp2(acc, slab[(mx - cx0) * P + y + 2], slab[(mx + 1 - cx0) * P + y + 2]);
+    return acc;
+}
+
+// One column shifted along p: dst(y) = src interpolated at y + shift (the RF
+// kick of the Manhattan rotation, shift = h (x - c); the wake kick, shift =
+// -kick).  Nodes off the grid are 0; a source more than one cell outside the
+// grid gives 0; clamping restricts to the two nearest nodes.
+template <typename T, int NI>
+__device__ __forceinline__ void kick_column(const T* __restrict__ src, T* __restrict__ dst, T shift, int n, int clamp,
+                                            int lane)
+{
+    const T fk = dfloor(shift);
+    const int sI = int(fk);
+    T w[NI];
+    lagrange_w<T, NI>(shift - fk, w);
+    constexpr int F = -((NI - 1) / 2);
+    for (int y = lane; y < n; y += 32) {
+        const int m = y + sI;
+        T v = T(0);
+        if (m > -2 && m < n) {
+#pragma unroll
+            for (int k = 0; k < NI; ++k) {
+                const int r = m + F + k;
+                if (r >= 0 && r < n) v += w[k] * src[r];
+            }
+            if (clamp) {
+                const T a0 = (m >= 0) ? src[m] : T(0);
+                const T a1 = (m + 1 < n) ? src[m + 1] : T(0);
+                v = clamp2(v, a0, a1);
+            }
+        }
+        dst[y] = v;
+    }
 }
 
 // ----------------------------------------------------------------------------
@@ -505,50 +563,40 @@ step_kernel(const Desc<T>* __restrict__ descs, const int2* __restrict__ tiles)
     }
     __syncthreads();
 
-    // rotation -> psi_a
+    // rotation -> psi_a (standard: 2-D; Manhattan: drift along q, then RF
+    // kick along p), then the wake kick -> psi_b
     const int x = x0 + warp;
     const bool active = x < n;
-    if (active) {
-        T* ca = colA + warp * n;
-        for (int y = lane; y < n; y += 32)
-            ca[y] = rotate_cell<T, NI>(slab, P, x0 - h, x, y, n, D.cm1, D.sn, D.c, D.clamp);
-    }
-    __syncthreads();
-
-    // kick -> psi_b : psi_b(y) = psi_a(y_r), y_r = y - kick[x]
-    if (active) {
-        const T* ca = colA + warp * n;
-        T* cb = colB + warp * n;
-        T ks = -D.kick[x];
-        T fk = dfloor(ks);
-        int sI = int(fk);
-        T w[NI];
-        lagrange_w<T, NI>(ks - fk, w);
-        constexpr int F = -((NI - 1) / 2);
-        for (int y = lane; y < n; y += 32) {
-            int m = y + sI;
-            T v = T(0);
-            if (m > -2 && m < n) {
-#pragma unroll
-                for (int k = 0; k < NI; ++k) {
-                    int r = m + F + k;
-                    if (r >= 0 && r < n) v += w[k] * ca[r];
-                }
-                if (D.clamp) {
-                    T a0 = (m >= 0) ? ca[m] : T(0);
-                    T a1 = (m + 1 < n) ? ca[m + 1] : T(0);
-                    v = clamp2(v, a0, a1);
-                }
-            }
-            cb[y] = v;
+    const T* cb;  // psi_b column of this warp
+    if (D.rotation == 1) {
+        if (active) {
+            T* ca = colA + warp * n;
+            for (int y = lane; y < n; y += 32)
+                ca[y] = drift_cell<T, NI>(slab, P, x0 - h, x, y, n, D.hm, D.c, D.clamp);
         }
+        __syncthreads();  // the slab is free: RF kick into it, wake kick back
+        if (active) {
+            kick_column<T, NI>(colA + warp * n, colB + warp * n, D.hm * (T(x) - D.c), n, D.clamp, lane);
+            __syncwarp();
+            kick_column<T, NI>(colB + warp * n, colA + warp * n, -D.kick[x], n, D.clamp, lane);
+        }
+        cb = colA + warp * n;
+    } else {
+        if (active) {
+            T* ca = colA + warp * n;
+            for (int y = lane; y < n; y += 32)
+                ca[y] = rotate_cell<T, NI>(slab, P, x0 - h, x, y, n, D.cm1, D.sn, D.c, D.clamp);
+        }
+        __syncthreads();
+        // kick -> psi_b : psi_b(y) = psi_a(y_r), y_r = y - kick[x]
+        if (active) kick_column<T, NI>(colA + warp * n, colB + warp * n, -D.kick[x], n, D.clamp, lane);
+        cb = colB + warp * n;
     }
     __syncwarp();
 
     // Fokker-Planck -> psi_c, column sum
     double csum = 0.0;
     if (active) {
-        const T* cb = colB + warp * n;
         T* dst = out + (size_t)x * ld;
         T lsum = T(0);
         const T ga0 = D.ga[0], ga1 = D.ga[1], ga2 = D.ga[2], ga3 = D.ga[3];

@@ -47,6 +47,7 @@ class CParams(ctypes.Structure):
                 ("interp_points", ctypes.c_int32), ("clamp", ctypes.c_int32),
                 ("fp_derivative", ctypes.c_int32), ("pad_factor", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("renormalize", ctypes.c_int32),
+                ("rotation", ctypes.c_int32),
                 ("half_width", ctypes.c_double), ("beta", ctypes.c_double)]
 
 
@@ -63,11 +64,12 @@ class Params:
     pad_factor: int = 2
     precision: int = 0
     renormalize: int = 1
+    rotation: int = 0   # 0 standard rotation, 1 Manhattan rotation (drift, then RF kick)
 
     def c(self) -> CParams:
         return CParams(self.n, self.steps_per_period, self.interp_points, self.clamp,
                        self.fp_derivative, self.pad_factor, self.precision, self.renormalize,
-                       self.half_width, self.beta)
+                       self.rotation, self.half_width, self.beta)
 
 
 _lib = None

@@ -140,3 +140,25 @@ def test_large_batch_uses_strips_and_matches_solo_runs(V):
         assert np.array_equal(r["psi"], psi_a), i
         assert np.array_equal(r["power"], p_a), i
     b.close()
+
+
+def test_mixed_rotation_modes_in_one_batch(V):
+    """Standard and Manhattan simulations of the same grid size share a batch;
+    each slot equals its solo run bit for bit."""
+    n, spp, ns = 64, 500, 40
+    mix = [(0, 0.9, 2.0), (1, 0.9, 2.0), (1, 1.3, 1.0), (0, 0.5, 3.0)]
+    b = V.Batch(len(mix))
+    slots = []
+    for i, (rot, S, Pi) in enumerate(mix):
+        slots.append(b.add(V.Params(n=n, steps_per_period=spp, beta=1e-2, rotation=rot), W.blobs(n, 50 + i),
+                           V.IMPEDANCE_PARALLEL_PLATES, Pi, S, nsteps=ns))
+    b.run(ns)
+    for i, (rot, S, Pi) in enumerate(mix):
+        r = b.take(slots[i])
+        sim = V.Simulation(V.Params(n=n, steps_per_period=spp, beta=1e-2, rotation=rot), W.blobs(n, 50 + i))
+        sim.set_impedance(V.IMPEDANCE_PARALLEL_PLATES, Pi, S)
+        sim.step(ns)
+        assert np.array_equal(r["psi"], sim.get_state()), i
+        assert np.array_equal(r["power"], sim.csr_power()), i
+        sim.close()
+    b.close()

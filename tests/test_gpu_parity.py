@@ -48,6 +48,11 @@ CASES = [
     (48, "blobs", 1, 0.0, 0.8, {"fp_derivative": 0}),
     (64, "blobs", 2, 2.0, 0.9, {"pad_factor": 4}),
     (40, "blobs", 2, 2.0, 0.9, {"renormalize": 0}),
+    # Manhattan rotation (drift, then RF kick)
+    (64, "blobs", 2, 2.0, 0.9, {"rotation": 1}),
+    (33, "random", 2, 1.0, 1.3, {"rotation": 1, "interp_points": 3}),
+    (48, "blobs", 2, 3.0, 1.5, {"rotation": 1, "clamp": 1}),
+    (256, "blobs", 2, 2.0, 0.9, {"rotation": 1}),
 ]
 
 
@@ -195,3 +200,39 @@ def test_invalid_arguments_are_rejected(V):
     with pytest.raises(V.VfpsError):
         sim.step(-1)
     sim.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(1, 1e-10), (0, 1e-4)])
+def test_manhattan_run_matches_oracle(V, precision, tol):
+    """300 Manhattan-rotation steps below threshold (C1-like set-up)."""
+    n, spp = 64, 500
+    sim, op, zr, zi = make(V, n, precision, spp=spp, model=2, Pi=2.0, S=0.3, rotation=1)
+    ref0 = O.normalize(op, W.gaussian(n, 6.0, 1.0, 1.0))
+    ref, pref, _ = O.run(op, zr, zi, ref0, 300)
+    sim.step(300)
+    assert rel_linf(sim.get_state(), ref) < tol
+    P = sim.csr_power()
+    assert np.max(np.abs(P - pref) / pref) < (1e-10 if precision else 1e-2)
+    sim.close()
+
+
+@pytest.mark.parametrize("n", [9, 15])
+def test_manhattan_sixth_turn_permutation(V, n):
+    """steps_per_period = 6 (h = 1) on an odd grid: one Manhattan rotation is
+    the node permutation psi(2c - y, x + y - c); no wake, no FP."""
+    f = W.random_field(n, 21) + 0.5
+    for precision, tol in ((1, 1e-12), (0, 1e-6)):
+        sim = V.Simulation(V.Params(n=n, steps_per_period=6, beta=0.0, precision=precision,
+                                    renormalize=0, rotation=1), f)
+        f0 = sim.get_state()
+        sim.step(1)
+        out = sim.get_state()
+        c = (n - 1) // 2
+        ref = np.zeros_like(f0)
+        for x in range(n):
+            for y in range(n):
+                xs, ys = 2 * c - y, x + y - c
+                if 0 <= xs < n and 0 <= ys < n:
+                    ref[x, y] = f0[xs, ys]
+        assert rel_linf(out, ref) < tol
+        sim.close()
