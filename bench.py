@@ -115,14 +115,33 @@ def scan_points(count: int):
     return [base[i % len(base)] for i in range(count)]
 
 
-def build_batch(V, count, n, spp, beta, stream, seed=1612):
+def build_batch(V, count, n, spp, beta, stream, seed=1612, rotation=0):
     from paper_1611_05293_b300 import workloads as W
     b = V.Batch(count, 0, stream)
     psi0 = W.noisy_gaussian(n, seed, 1e-6)
     for S, Pi in scan_points(count):
-        b.add(V.Params(n=n, steps_per_period=spp, beta=beta), psi0, V.IMPEDANCE_PARALLEL_PLATES, Pi, S,
-              nsteps=1 << 40)
+        b.add(V.Params(n=n, steps_per_period=spp, beta=beta, rotation=rotation), psi0, V.IMPEDANCE_PARALLEL_PLATES,
+              Pi, S, nsteps=1 << 40)
     return b
+
+
+def manhattan_scan(V, torch, stream, warmup, count=512, steps=200):
+    """The headline scan with the Manhattan rotation (drift, then RF kick; two
+    1-D cubic interpolations instead of one 2-D) in place of the standard one."""
+    b = build_batch(V, count, 256, 1000, 1e-2, stream, rotation=1)
+    b.run(warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.run(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dt = e0.elapsed_time(e1) / 1e3
+    b.close()
+    value = count * 65536 * steps / dt
+    return {"value": value, "unit": "cell-updates/s", "ms_per_step": 1e3 * dt / steps,
+            "roofline_frac": 8.0 * value / 1e9 / measured_peaks()[0],
+            "workload": f"{count} x N=256 scan, Manhattan rotation"}
 
 
 def serving(V, stream, count=48, seed=1613):
@@ -364,6 +383,7 @@ def main():
         line["serving"] = serving(V, stream)
         line["c3_scan_64"] = c3_scan_64(V, torch, stream, args.warmup)
         line["c5_n1024"] = c5_single(V, torch, stream, args.warmup)
+        line["manhattan_scan"] = manhattan_scan(V, torch, stream, args.warmup)
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(n, spp, beta)
     print(json.dumps(line))

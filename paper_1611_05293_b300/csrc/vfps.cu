@@ -130,12 +130,15 @@ int device_smem_limit()
     return g_max_smem;
 }
 
-// The FP32 register-blocked kernel (vfps_fast.cuh) covers the standard
-// rotation with cubic interpolation and no clamping on grids with n a
-// multiple of 4.
+// The FP32 register-blocked kernel (vfps_fast.cuh) covers cubic
+// interpolation without clamping on grids with n a multiple of 4, for both
+// rotations.
 bool fast_eligible(const vfps_params* p)
 {
-    return p->precision == 0 && p->interp_points == 4 && p->clamp == 0 && p->rotation == 0 && (p->n % 4) == 0;
+    // the Manhattan drift's x-node may step by at most one per 4-row block:
+    // h = 2 sin(pi/steps) < 1/3
+    return p->precision == 0 && p->interp_points == 4 && p->clamp == 0 && (p->n % 4) == 0 &&
+           (p->rotation == 0 || p->steps_per_period >= 20);
 }
 
 // Rows per lane of the FP32 kernel's kick/FP blocks: 8 where n allows.
@@ -144,7 +147,7 @@ int fast_kr(int n) { return (n % 8 == 0) ? 8 : 4; }
 size_t fast_smem(const vfps_params* p, int W)
 {
     size_t fin = vfps::finalise_smem(fft_length(p), p->n, W * 32, 8);
-    return align_up(std::max(vfps::fast_ring_smem(p->n, halo_for(p), W), fin), 16);
+    return align_up(std::max(vfps::fast_ring_smem(p->n, halo_for(p), W, p->rotation == 1), fin), 16);
 }
 
 int g_num_sms = 0;
@@ -529,6 +532,7 @@ struct Group {
     int tps = 1;  // FP32 streaming kernel: consecutive tiles per CTA
     int kr = 4;   // FP32 streaming kernel: rows per lane of the kick/FP blocks
     int n = 0;    // grid size shared by the group's instances
+    int rot = 0;  // rotation shared by the group's instances (FP32 streaming kernel)
     size_t smem = 0;
     int ntiles = 0;
     void* ddescs = nullptr;  // array of Desc<T>
@@ -596,8 +600,12 @@ int launch_step_ni(const Group& g, cudaStream_t s)
 template <int W, int KR, int NC>
 int launch_fast_k(const Group& g, cudaStream_t s)
 {
-    CU(launch_pdl(step_kernel_f32<W, KR, NC>, g.ntiles / g.tps, W * 32, g.smem, s, (const Desc<float>*)g.ddescs,
-                  (const int2*)g.dtiles, g.tps));
+    if (g.rot)
+        CU(launch_pdl(step_kernel_f32<W, KR, NC, 1>, g.ntiles / g.tps, W * 32, g.smem, s,
+                      (const Desc<float>*)g.ddescs, (const int2*)g.dtiles, g.tps));
+    else
+        CU(launch_pdl(step_kernel_f32<W, KR, NC, 0>, g.ntiles / g.tps, W * 32, g.smem, s,
+                      (const Desc<float>*)g.ddescs, (const int2*)g.dtiles, g.tps));
     return VFPS_OK;
 }
 
@@ -690,18 +698,30 @@ int init_kernels()
     if (lim <= 0) return VFPS_ECUDA;
     CU(set_smem_attr_all<float>(lim));
     CU(set_smem_attr_all<double>(lim));
-    CU(set_smem_attr_one(step_kernel_f32<8, 8, 0>, lim));
-    CU(set_smem_attr_one(step_kernel_f32<4, 8, 0>, lim));
-    CU(set_smem_attr_one(step_kernel_f32<2, 8, 0>, lim));
-    CU(set_smem_attr_one(step_kernel_f32<8, 4, 0>, lim));
-    CU(set_smem_attr_one(step_kernel_f32<4, 4, 0>, lim));
-    CU(set_smem_attr_one(step_kernel_f32<2, 4, 0>, lim));
-    CU(set_smem_attr_one(step_kernel_f32<8, 8, 256>, lim));
-    CU(set_smem_attr_one(step_kernel_f32<4, 8, 256>, lim));
-    CU(set_smem_attr_one(step_kernel_f32<2, 8, 256>, lim));
-    CU(set_smem_attr_one(step_kernel_f32<8, 8, 1024>, lim));
-    CU(set_smem_attr_one(step_kernel_f32<4, 8, 1024>, lim));
-    CU(set_smem_attr_one(step_kernel_f32<2, 8, 1024>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<8, 8, 0, 0>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<4, 8, 0, 0>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<2, 8, 0, 0>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<8, 4, 0, 0>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<4, 4, 0, 0>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<2, 4, 0, 0>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<8, 8, 256, 0>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<4, 8, 256, 0>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<2, 8, 256, 0>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<8, 8, 1024, 0>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<4, 8, 1024, 0>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<2, 8, 1024, 0>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<8, 8, 0, 1>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<4, 8, 0, 1>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<2, 8, 0, 1>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<8, 4, 0, 1>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<4, 4, 0, 1>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<2, 4, 0, 1>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<8, 8, 256, 1>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<4, 8, 256, 1>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<2, 8, 256, 1>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<8, 8, 1024, 1>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<4, 8, 1024, 1>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<2, 8, 1024, 1>, lim));
     g_kernels_ready = 1;
     return VFPS_OK;
 }
@@ -716,6 +736,7 @@ Group single_group(const Instance& I)
     g.fast = I.fast;
     g.kr = fast_kr(I.p.n);
     g.n = I.p.n;
+    g.rot = I.p.rotation;
     g.smem = I.fast ? std::max(fast_smem(&I.p, I.W), step_smem(&I.p, I.W)) : step_smem(&I.p, I.W);
     g.ntiles = I.ntiles;
     g.ddescs = I.ddesc;
@@ -1049,13 +1070,14 @@ int rebuild_groups(vfps_batch* b)
     std::map<std::tuple<int, int, int, int, int>, std::vector<Instance*>> cls;
     std::map<std::tuple<int, int, int, int>, int> count;
     for (Instance* I : b->slots)
-        if (I && remaining(I) > 0) ++count[{I->p.precision, I->p.interp_points * 2 + I->fast, I->W, I->n}];
+        if (I && remaining(I) > 0)
+            ++count[{I->p.precision, (I->p.interp_points * 2 + I->fast) * 2 + I->p.rotation, I->W, I->n}];
     std::map<std::tuple<int, int, int, int>, int> seen;
     for (Instance* I : b->slots) {
         if (!I || remaining(I) <= 0) continue;
-        auto key = std::make_tuple(I->p.precision, I->p.interp_points * 2 + I->fast, I->W, I->n);
+        auto key = std::make_tuple(I->p.precision, (I->p.interp_points * 2 + I->fast) * 2 + I->p.rotation, I->W, I->n);
         int half = (count[key] >= 8 && seen[key]++ >= count[key] / 2) ? 1 : 0;
-        cls[{I->p.precision, I->p.interp_points * 2 + I->fast, I->W, I->n, half}].push_back(I);
+        cls[{I->p.precision, (I->p.interp_points * 2 + I->fast) * 2 + I->p.rotation, I->W, I->n, half}].push_back(I);
     }
     if (cls.empty()) {
         b->dirty = false;
@@ -1094,8 +1116,8 @@ int rebuild_groups(vfps_batch* b)
     for (auto& kv : cls) {
         Group g;
         g.prec = std::get<0>(kv.first);
-        g.ni = std::get<1>(kv.first) / 2;
-        g.fast = std::get<1>(kv.first) & 1;
+        g.ni = std::get<1>(kv.first) / 4;
+        g.fast = (std::get<1>(kv.first) >> 1) & 1;
         g.W = std::get<2>(kv.first);
         g.stream = b->pool[gi];
         g.ddescs = (unsigned char*)b->gmem + offs[gi].first;
@@ -1113,6 +1135,7 @@ int rebuild_groups(vfps_batch* b)
         g.ntiles = nt;
         g.kr = fast_kr(kv.second[0]->p.n);  // a group shares n
         g.n = kv.second[0]->p.n;
+        g.rot = kv.second[0]->p.rotation;
         if (g.fast) {
             // a strip of tps consecutive tiles per CTA: the largest divisor of
             // the tiles per instance that still leaves two CTAs per SM (long
@@ -1515,6 +1538,7 @@ extern "C" int vfps_step_static(const vfps_params* params, int model, double Pi,
     g.fast = fast;
     g.kr = fast_kr(params->n);
     g.n = params->n;
+    g.rot = params->rotation;
     g.ntiles = I.ntiles;
     g.smem = fast ? std::max(fast_smem(params, W), step_smem(params, W)) : step_smem(params, W);
     g.ddescs = d + kOffDesc;

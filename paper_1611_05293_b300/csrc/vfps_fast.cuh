@@ -132,7 +132,10 @@ __device__ __forceinline__ void rotate_block(const float* __restrict__ ring, int
 // the identity folded into the centre tap: psi_c(y) = sum_k g_k(y) psi_b(y-1+k).
 // SMALL: s is -1 or 0 (kicks under one cell), where the edge test reduces to
 // the rows just outside the grid.
-template <int O2, int PAR, int KR, bool SMALL>
+//
+// FP = false (the RF kick of the Manhattan rotation): only the shift, psi_b of
+// the lane's own rows goes to the psi_a-layout column dst (shared memory).
+template <int O2, int PAR, int KR, bool SMALL, bool FP = true>
 __device__ __forceinline__ float kick_fp_column(const float* __restrict__ colcol, int HC,
                                                 const float* __restrict__ g, float* __restrict__ dst, int n, int s,
                                                 int A2, float4 w, int lane)
@@ -189,6 +192,12 @@ __device__ __forceinline__ float kick_fp_column(const float* __restrict__ colcol
 #pragma unroll
             for (int j = 0; j < NB; ++j) b[j] = (j >= jlo && j <= jhi) ? b[j] : 0.f;
         }
+        if constexpr (!FP) {
+#pragma unroll
+            for (int q4 = 0; q4 < KR / 4; ++q4)
+                *reinterpret_cast<float4*>(dst + split_idx<KR>(kColPad + y0 + 4 * q4, HC)) =
+                    make_float4(b[4 * q4 + 1], b[4 * q4 + 2], b[4 * q4 + 3], b[4 * q4 + 4]);
+        } else {
 #pragma unroll
         for (int q4 = 0; q4 < KR / 4; ++q4) {
             const int y = y0 + 4 * q4;
@@ -207,6 +216,7 @@ __device__ __forceinline__ float kick_fp_column(const float* __restrict__ colcol
             }
             *reinterpret_cast<float4*>(dst + y) = make_float4(c[0], c[1], c[2], c[3]);
             lsum += (c[0] + c[1]) + (c[2] + c[3]);
+        }
         }
     }
     return lsum;
@@ -269,12 +279,13 @@ __host__ __device__ inline int ring_slots(int W, int h)
 }
 
 // Shared memory of the FP32 streaming kernel: ring, psi_a columns, FP
-// weights, and a 4-stage buffer of the tiles' kick-table entries.
-__host__ inline size_t fast_ring_smem(int n, int h, int W)
+// weights, a 4-stage buffer of the tiles' kick-table entries, and for the
+// Manhattan rotation a second set of columns (the RF-kicked psi).
+__host__ inline size_t fast_ring_smem(int n, int h, int W, bool manhattan)
 {
     const int RP = fast_row_pad(h);
-    return (size_t)ring_slots(W, h) * ring_pitch(n, RP) * 4 + (size_t)W * cola_pitch(n) * 4 + (size_t)n * 16 +
-           (size_t)4 * W * 32;
+    return (size_t)ring_slots(W, h) * ring_pitch(n, RP) * 4 + (size_t)W * cola_pitch(n) * 4 * (manhattan ? 2 : 1) +
+           (size_t)n * 16 + (size_t)4 * W * 32;
 }
 
 // Copy the kick-table entries (two float4) of column x into dst (lanes 0 and
@@ -327,6 +338,56 @@ __device__ __forceinline__ void rotate_column(const float* __restrict__ ring, in
     }
 }
 
+// Manhattan rotation, first half (Sec. III.B, symplectic rotation): the drift
+// q -> q + h p moves row y along q by h (y - c) cells, psi_a(x, y) = psi(x -
+// h (y - c), y), interpolated along q (cubic).  Four rows y0..y0+3 per lane
+// and pass; their x-node steps down by at most one inside the block (h <
+// 1/3), so one 5-column window of the ring (one LDS.128 per column) with a
+// 5-column weight vector covers the block, as in the 2-D rotation.
+template <int KR>
+__device__ __forceinline__ void drift_column(const float* __restrict__ ring, int R, int P, int RP,
+                                             float* __restrict__ colcol, int HC, int x, int n, int lane, float c,
+                                             float hm)
+{
+    for (int y0 = 4 * lane; y0 < n; y0 += 128) {
+        const float yc0 = float(y0) - c;
+        const float d0 = -hm * yc0, d1 = -hm * (yc0 + 1.f), d2 = -hm * (yc0 + 2.f), d3 = -hm * (yc0 + 3.f);
+        const float fx0 = floorf(d0), fx1 = floorf(d1), fx2 = floorf(d2), fx3 = floorf(d3);
+        float2 w01[4], w23[4];
+        lagrange2(f2(d0 - fx0, d1 - fx1), w01);
+        lagrange2(f2(d2 - fx2, d3 - fx3), w23);
+        const float wx[4][4] = {{w01[0].x, w01[1].x, w01[2].x, w01[3].x},
+                                {w01[0].y, w01[1].y, w01[2].y, w01[3].y},
+                                {w23[0].x, w23[1].x, w23[2].x, w23[3].x},
+                                {w23[0].y, w23[1].y, w23[2].y, w23[3].y}};
+        const bool e[4] = {false, fx1 < fx0, fx2 < fx0, fx3 < fx0};
+        const int mx0 = x + int(fx0);
+        const int slot0 = (mx0 - 2) & (R - 1);  // window columns mx0-2 .. mx0+2
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int a = 0; a < 5; ++a) {
+            const float4 q = *reinterpret_cast<const float4*>(ring + ((slot0 + a) & (R - 1)) * P + RP + y0);
+            const float v[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float wa = e[k] ? ((a <= 3) ? wx[k][a] : 0.f) : ((a >= 1) ? wx[k][a - 1] : 0.f);
+                acc[k] = fmaf(wa, v[k], acc[k]);
+            }
+        }
+        // sources more than one cell outside the grid give 0
+        if (!(mx0 >= 0 && mx0 <= n - 1)) {
+            const float fxk[4] = {fx0, fx1, fx2, fx3};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int mx = x + int(fxk[k]);
+                if (mx <= -2 || mx >= n) acc[k] = 0.f;
+            }
+        }
+        *reinterpret_cast<float4*>(colcol + split_idx<KR>(kColPad + y0, HC)) =
+            make_float4(acc[0], acc[1], acc[2], acc[3]);
+    }
+}
+
 // Streaming FP32 step.  CTA b takes the strip of tps consecutive W-column
 // tiles tiles[b*tps .. b*tps+tps-1] (one instance, consecutive columns) and
 // walks it tile by tile.  The slab columns live in a ring of R shared-memory
@@ -336,7 +397,7 @@ __device__ __forceinline__ void rotate_column(const float* __restrict__ ring, in
 // arithmetic.  psi_a stays unscaled; the pending renormalisation factor is
 // part of the kick weights.  The column sums of a strip are made visible
 // with one fence per thread before the CTA takes its ticket.
-template <int W, int KR, int NC>
+template <int W, int KR, int NC, int ROT>
 __global__ void __launch_bounds__(W * 32, 32 / W)
 step_kernel_f32(const Desc<float>* __restrict__ descs, const int2* __restrict__ tiles, int tps)
 {
@@ -364,6 +425,9 @@ step_kernel_f32(const Desc<float>* __restrict__ descs, const int2* __restrict__ 
     float* gtab = colA + W * PA;  // g_0(y) .. g_3(y), n each (split layout for KR = 8)
     float* colcol = colA + warp * PA;  // this warp's psi_a column, padded
     float4* kbuf = reinterpret_cast<float4*>(gtab + 4 * n) + 2 * warp;  // stage k: kbuf + 2 W k
+    constexpr int rot = ROT;            // 1: Manhattan rotation (every instance of the launch)
+    const float hm = D.hm;
+    float* colbcol = reinterpret_cast<float*>(reinterpret_cast<float4*>(gtab + 4 * n) + 8 * W) + warp * PA;
     pdl_trigger();
 
     // padding rows of every ring slot and of this warp's psi_a column: zero
@@ -374,6 +438,8 @@ step_kernel_f32(const Desc<float>* __restrict__ descs, const int2* __restrict__ 
             ring[slot * P + RP + n + r] = 0.f;
         }
     for (int r = lane; r < PA - n; r += 32) colcol[split_idx<KR>(r < kColPad ? r : n + r, HC)] = 0.f;
+    if (rot)
+        for (int r = lane; r < PA - n; r += 32) colbcol[split_idx<KR>(r < kColPad ? r : n + r, HC)] = 0.f;
     for (int y = threadIdx.x; y < n; y += blockDim.x) {
         const float yf = float(y);
         const int gi = split_idx<KR>(y, n >> 3);
@@ -400,7 +466,9 @@ step_kernel_f32(const Desc<float>* __restrict__ descs, const int2* __restrict__ 
         const bool active = x < n;
         cp_async_wait_1();
         __syncthreads();
-        if (active) {
+        if (active && rot) {
+            drift_column<KR>(ring, R, P, RP, colcol, HC, x, n, lane, c, hm);
+        } else if (active) {
             const float xc = float(x) - c;
             // dy is linear along the column: floor(dy) is the same on every row
             // iff it is at the first and the last row
@@ -421,6 +489,44 @@ step_kernel_f32(const Desc<float>* __restrict__ descs, const int2* __restrict__ 
             }
         }
         __syncwarp();
+        const float* kcol = colcol;  // the column the wake kick reads
+        if (active && rot) {
+            // Manhattan rotation, second half: RF kick p -> p - h q, i.e. this
+            // column moves along p by h (x - c) cells (source y + h (x - c))
+            const float ts = hm * (float(x) - c), fk = floorf(ts);
+            const int sr = int(fk);
+            float wr[4];
+            lagrange_w<float, 4>(ts - fk, wr);
+            const float4 w4 = make_float4(wr[0], wr[1], wr[2], wr[3]);
+            if (sr >= -4 && sr <= 4) {
+                const int A2 = sr - 2 + kColPad;
+                switch (KR == 8 ? (A2 & 7) : (A2 & 3)) {
+                case 0: kick_fp_column<0, 0, KR, false, false>(colcol, HC, gtab, colbcol, n, sr, A2, w4, lane); break;
+                case 1: kick_fp_column<1, 0, KR, false, false>(colcol, HC, gtab, colbcol, n, sr, A2, w4, lane); break;
+                case 2: kick_fp_column<2, 0, KR, false, false>(colcol, HC, gtab, colbcol, n, sr, A2, w4, lane); break;
+                case 3: kick_fp_column<3, 0, KR, false, false>(colcol, HC, gtab, colbcol, n, sr, A2, w4, lane); break;
+                case 4: kick_fp_column<0, 1, KR, false, false>(colcol, HC, gtab, colbcol, n, sr, A2, w4, lane); break;
+                case 5: kick_fp_column<1, 1, KR, KR == 8, false>(colcol, HC, gtab, colbcol, n, sr, A2, w4, lane); break;
+                case 6: kick_fp_column<2, 1, KR, KR == 8, false>(colcol, HC, gtab, colbcol, n, sr, A2, w4, lane); break;
+                default: kick_fp_column<3, 1, KR, false, false>(colcol, HC, gtab, colbcol, n, sr, A2, w4, lane); break;
+                }
+            } else {
+                for (int y = lane; y < n; y += 32) {
+                    const int m = y + sr;
+                    float v = 0.f;
+                    if (m > -2 && m < n) {
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const int rr = m - 1 + k;
+                            if (rr >= 0 && rr < n) v += wr[k] * colcol[split_idx<KR>(kColPad + rr, HC)];
+                        }
+                    }
+                    colbcol[split_idx<KR>(kColPad + y, HC)] = v;
+                }
+            }
+            __syncwarp();
+            kcol = colbcol;
+        }
         if (active) {
             const float4* kj = kbuf + 2 * W * (j & 3);
             const float4 kw = kj[0];
@@ -431,14 +537,14 @@ step_kernel_f32(const Desc<float>* __restrict__ descs, const int2* __restrict__ 
                 const int A2 = s - 2 + kColPad;  // column index of row y0+s-2, minus y0
                 // A2 = s + 14 with |s| <= 4: (A2 & 7) = 5 and 6 are s = -1 and 0 only
                 switch (KR == 8 ? (A2 & 7) : (A2 & 3)) {
-                case 0: lsum = kick_fp_column<0, 0, KR, false>(colcol, HC, gtab, dst, n, s, A2, kw, lane); break;
-                case 1: lsum = kick_fp_column<1, 0, KR, false>(colcol, HC, gtab, dst, n, s, A2, kw, lane); break;
-                case 2: lsum = kick_fp_column<2, 0, KR, false>(colcol, HC, gtab, dst, n, s, A2, kw, lane); break;
-                case 3: lsum = kick_fp_column<3, 0, KR, false>(colcol, HC, gtab, dst, n, s, A2, kw, lane); break;
-                case 4: lsum = kick_fp_column<0, 1, KR, false>(colcol, HC, gtab, dst, n, s, A2, kw, lane); break;
-                case 5: lsum = kick_fp_column<1, 1, KR, KR == 8>(colcol, HC, gtab, dst, n, s, A2, kw, lane); break;
-                case 6: lsum = kick_fp_column<2, 1, KR, KR == 8>(colcol, HC, gtab, dst, n, s, A2, kw, lane); break;
-                default: lsum = kick_fp_column<3, 1, KR, false>(colcol, HC, gtab, dst, n, s, A2, kw, lane); break;
+                case 0: lsum = kick_fp_column<0, 0, KR, false>(kcol, HC, gtab, dst, n, s, A2, kw, lane); break;
+                case 1: lsum = kick_fp_column<1, 0, KR, false>(kcol, HC, gtab, dst, n, s, A2, kw, lane); break;
+                case 2: lsum = kick_fp_column<2, 0, KR, false>(kcol, HC, gtab, dst, n, s, A2, kw, lane); break;
+                case 3: lsum = kick_fp_column<3, 0, KR, false>(kcol, HC, gtab, dst, n, s, A2, kw, lane); break;
+                case 4: lsum = kick_fp_column<0, 1, KR, false>(kcol, HC, gtab, dst, n, s, A2, kw, lane); break;
+                case 5: lsum = kick_fp_column<1, 1, KR, KR == 8>(kcol, HC, gtab, dst, n, s, A2, kw, lane); break;
+                case 6: lsum = kick_fp_column<2, 1, KR, KR == 8>(kcol, HC, gtab, dst, n, s, A2, kw, lane); break;
+                default: lsum = kick_fp_column<3, 1, KR, false>(kcol, HC, gtab, dst, n, s, A2, kw, lane); break;
                 }
             } else {
                 // large kick: plain per-row evaluation with bounds
@@ -454,7 +560,7 @@ step_kernel_f32(const Desc<float>* __restrict__ descs, const int2* __restrict__ 
 #pragma unroll
                             for (int k = 0; k < 4; ++k) {
                                 const int rr = mm - 1 + k;
-                                if (rr >= 0 && rr < n) v += w[k] * colcol[split_idx<KR>(kColPad + rr, HC)];
+                                if (rr >= 0 && rr < n) v += w[k] * kcol[split_idx<KR>(kColPad + rr, HC)];
                             }
                         }
                         b[d] = v;
