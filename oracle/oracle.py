@@ -101,6 +101,7 @@ def lib():
         L.or_wake.argtypes = [P, _D, _D, _D, _D, _D]
         L.or_kick.argtypes = [P, _D, _D, _D]
         L.or_fokker_planck.argtypes = [P, _D, _D]
+        L.or_moments.argtypes = [P, _D, _D]
         L.or_charge.argtypes = [P, _D]
         L.or_charge.restype = ctypes.c_double
         L.or_normalize.argtypes = [P, _D]
@@ -189,6 +190,14 @@ def fokker_planck(pr: Params, psi) -> np.ndarray:
     psi = _grid(psi, pr.n)
     out = np.empty_like(psi)
     lib().or_fokker_planck(ctypes.byref(pr.c()), _p(psi), _p(out))
+    return out
+
+
+def moments(pr: Params, psi) -> np.ndarray:
+    """(<q>, sigma_q, <p>, sigma_p) of psi."""
+    psi = _grid(psi, pr.n)
+    out = np.zeros(4)
+    lib().or_moments(ctypes.byref(pr.c()), _p(psi), _p(out))
     return out
 
 

@@ -341,6 +341,33 @@ void or_fokker_planck(const or_params* pr, const double* in, double* out)
     }
 }
 
+/* Bunch moments of psi (first and second moments of the distribution in q
+ * and p, the quantities behind the paper's bunch length and energy spread):
+ * out = {<q>, sigma_q, <p>, sigma_p} with <f> = sum f psi / sum psi over the
+ * nodes, sigma^2 = <f^2> - <f>^2. */
+void or_moments(const or_params* pr, const double* psi, double* out)
+{
+    int n = pr->n;
+    double d = grid_delta(pr), L = pr->half_width;
+    double s0 = 0.0, sq = 0.0, sqq = 0.0, sp = 0.0, spp = 0.0;
+    for (int x = 0; x < n; ++x) {
+        double q = -L + x * d;
+        for (int y = 0; y < n; ++y) {
+            double p = -L + y * d, v = psi[(size_t)x * n + y];
+            s0 += v;
+            sq += q * v;
+            sqq += q * q * v;
+            sp += p * v;
+            spp += p * p * v;
+        }
+    }
+    double mq = sq / s0, mp = sp / s0;
+    out[0] = mq;
+    out[1] = sqrt(sqq / s0 - mq * mq);
+    out[2] = mp;
+    out[3] = sqrt(spp / s0 - mp * mp);
+}
+
 /* Charge Q = Delta^2 sum psi. */
 double or_charge(const or_params* pr, const double* psi)
 {

@@ -103,3 +103,23 @@ def test_threshold_brackets_bcs_law():
     lo, hi = out[0.45], out[0.85]
     assert np.median(lo[-20:]) < 1e-3 and np.median(lo[-20:]) < np.median(lo[20:40])
     assert np.median(hi[-20:]) > 2e-3
+
+
+def test_moments_of_shifted_gaussians():
+    """Bunch moments (the bunch length and energy spread of the paper's
+    figures) of sampled Gaussians: a well-resolved Gaussian's discrete
+    moments equal its parameters (the sampling error of the rectangle rule
+    is exponentially small), an off-centre one has the centre as its mean."""
+    n = 255
+    pr = O.Params(n=n)
+    # (the grid edge is >= 6 sigma away, so truncation is below 1e-7)
+    for sq, sp, q0, p0 in ((0.6, 0.6, 0.0, 0.0), (0.5, 0.8, 0.5, -0.8), (0.8, 0.45, -1.0, 0.3)):
+        psi = W.gaussian(n, 6.0, sq, sp, q0, p0)
+        m = O.moments(pr, psi)
+        assert np.max(np.abs(m - np.array([q0, sq, p0, sp]))) < 1e-7, (m, sq, sp, q0, p0)
+    # a quarter period of dq/dtheta = p, dp/dtheta = -q carries a particle at
+    # (q0, p0) to (p0, -q0) (Sec. III.B): the mean moves there, the widths swap
+    pr4 = O.Params(n=n, steps_per_period=4)
+    psi = W.gaussian(n, 6.0, 0.5, 0.8, 0.5, -0.8)
+    m = O.moments(pr4, O.rotate(pr4, psi))
+    assert np.max(np.abs(m - np.array([-0.8, 0.8, -0.5, 0.5]))) < 1e-7, m
