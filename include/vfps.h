@@ -110,6 +110,13 @@ int vfps_step(vfps_handle* h, int64_t nsteps);
  * current state.  Synchronises.  Errors: EINVAL, ECUDA, ENAN. */
 int vfps_profile(vfps_handle* h, double* rho_out);
 
+/* out (host, 4 doubles): bunch moments of the current state, computed on the
+ * device -- {<q>, sigma_q, <p>, sigma_p} with <f> = sum f psi / sum psi over
+ * the nodes (the bunch length and energy spread the paper plots, in units of
+ * the natural sigma_z and sigma_delta).  One extra read of psi; FP32 (or FP64)
+ * partials, FP64 sums.  Synchronises.  Errors: EINVAL, ECUDA, ENAN. */
+int vfps_moments(vfps_handle* h, double* out);
+
 /* Drain the CSR-power series: out[k] = P(psi_t) for the steps t taken since
  * the last drain, oldest first (P of the state each step started from).
  * Writes min(cap, pending) values and *n_written; values beyond cap stay
@@ -211,6 +218,10 @@ int vfps_batch_poll(vfps_batch* b, int32_t* done_slots, int32_t cap, int32_t* n_
 int vfps_batch_take(vfps_batch* b, int32_t slot, double* psi_out, double* rho_out,
                     double* power_out, int64_t power_cap, int64_t* n_power,
                     int64_t* steps_done);
+
+/* out (host, 4 doubles): bunch moments of slot's current state, as
+ * vfps_moments.  Synchronises the batch.  Errors: EINVAL, ECUDA, ENAN. */
+int vfps_batch_moments(vfps_batch* b, int32_t slot, double* out);
 
 /* Free a slot (its memory returns to the budget). */
 int vfps_batch_remove(vfps_batch* b, int32_t slot);

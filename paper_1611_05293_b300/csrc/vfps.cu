@@ -232,6 +232,7 @@ struct Instance {
     double* rho = nullptr;
     void* kick = nullptr;
     void* kickw = nullptr;   // FP32: two float4 per column
+    double* mom = nullptr;   // moments scratch: 3n column sums, then the 4 results
     double* pring = nullptr;
     double* qring = nullptr;
     DevState* st = nullptr;
@@ -272,6 +273,7 @@ size_t instance_bytes(const vfps_params* p, int ring, size_t* offs)
     take(10, sizeof(Desc<double>));      // descriptor
     take(11, sizeof(int2) * (size_t)((n + 1) / 2 + 1));  // tiles (W >= 2)
     take(12, (size_t)n * 32);            // kick table (FP32 path)
+    take(13, (size_t)(3 * n + 4) * 8);   // moments scratch
     return align_up(o, kAlign);
 }
 
@@ -464,7 +466,7 @@ int create_instance(const vfps_params* p, const double* psi0, int ring, cudaStre
     I->ring = ring;
     I->delta = 2.0 * p->half_width / (p->n - 1);
     I->phi = 2.0 * kPi / p->steps_per_period;
-    size_t offs[13];
+    size_t offs[14];
     I->dbytes = instance_bytes(p, ring, offs);
     if (cudaMalloc(&I->dmem, I->dbytes) != cudaSuccess) {
         cudaGetLastError();
@@ -485,6 +487,7 @@ int create_instance(const vfps_params* p, const double* psi0, int ring, cudaStre
     I->ddesc = b + offs[10];
     I->dtiles = (int2*)(b + offs[11]);
     I->kickw = b + offs[12];
+    I->mom = (double*)(b + offs[13]);
     // twiddles exp(-2 pi i k/M), FP64 on the host
     {
         int K = I->M / 2;
@@ -797,6 +800,38 @@ int copy_state(Instance& I, cudaStream_t s, double* psi_out)
     return st.status;
 }
 
+// Bunch moments of the current state on the device (two small kernels on
+// the instance's descriptor and tile table), copied to out[4].  Synchronises.
+template <typename T, int W>
+int launch_moments_t(Instance& I, cudaStream_t s)
+{
+    moments_columns_kernel<T, W><<<I.ntiles, W * 32, 0, s>>>((const Desc<T>*)I.ddesc, I.dtiles, I.mom);
+    CU(cudaGetLastError());
+    moments_finish_kernel<T><<<1, 256, 0, s>>>((const Desc<T>*)I.ddesc, I.mom);
+    CU(cudaGetLastError());
+    return VFPS_OK;
+}
+
+template <typename T>
+int launch_moments_p(Instance& I, cudaStream_t s)
+{
+    switch (I.W) {
+    case 8: return launch_moments_t<T, 8>(I, s);
+    case 4: return launch_moments_t<T, 4>(I, s);
+    case 2: return launch_moments_t<T, 2>(I, s);
+    }
+    return VFPS_EINVAL;
+}
+
+int instance_moments(Instance& I, cudaStream_t s, double* out)
+{
+    if (!out) return VFPS_EINVAL;
+    int rc = I.p.precision ? launch_moments_p<double>(I, s) : launch_moments_p<float>(I, s);
+    if (rc) return rc;
+    CU(cudaMemcpyAsync(out, I.mom + 3 * I.n, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    return read_status(I, s);
+}
+
 }  // namespace
 
 // ============================================================================
@@ -932,6 +967,12 @@ int vfps_step(vfps_handle* h, int64_t nsteps)
         nsteps -= chunk;
     }
     return VFPS_OK;
+}
+
+int vfps_moments(vfps_handle* h, double* out)
+{
+    if (!h) return VFPS_EINVAL;
+    return instance_moments(*h->I, h->stream, out);
 }
 
 int vfps_profile(vfps_handle* h, double* rho_out)
@@ -1169,7 +1210,7 @@ extern "C" {
 int64_t vfps_batch_slot_bytes(const vfps_params* params)
 {
     if (check_params(params)) return -1;
-    size_t offs[13];
+    size_t offs[14];
     return (int64_t)instance_bytes(params, kRingDefault / 2, offs);
 }
 
@@ -1205,7 +1246,7 @@ int vfps_batch_add(vfps_batch* b, const vfps_params* params, const double* psi0,
             break;
         }
     if (free_slot < 0) return VFPS_EBUSY;
-    size_t offs[13];
+    size_t offs[14];
     long long need = (long long)instance_bytes(params, kRingDefault / 2, offs);
     if (b->budget > 0 && b->used + need > b->budget) return VFPS_EBUSY;
     size_t fr = 0, tot = 0;
@@ -1316,6 +1357,12 @@ int vfps_batch_take(vfps_batch* b, int32_t slot, double* psi_out, double* rho_ou
     }
     if (steps_done) *steps_done = I.steps_queued;
     return read_status(I, b->stream);
+}
+
+int vfps_batch_moments(vfps_batch* b, int32_t slot, double* out)
+{
+    if (!b || slot < 0 || slot >= b->max_slots || !b->slots[slot]) return VFPS_EINVAL;
+    return instance_moments(*b->slots[slot], b->stream, out);
 }
 
 int vfps_batch_remove(vfps_batch* b, int32_t slot)

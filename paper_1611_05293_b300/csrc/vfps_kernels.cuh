@@ -673,4 +673,74 @@ project_kernel(const Desc<T>* __restrict__ descs, const int2* __restrict__ tiles
     }
 }
 
+// ----------------------------------------------------------------------------
+// Bunch moments of the current state (the bunch length and energy spread of
+// the paper's figures): <f> = sum f psi / sum psi over the nodes.
+// Pass 1, one warp per column x: FP32 lane partials of psi, p psi, p^2 psi,
+// summed across lanes in FP64 into m[3x .. 3x+2].  Pass 2, one CTA: fixed-
+// order FP64 sums over the columns, out = {<q>, sigma_q, <p>, sigma_p}
+// (m + 3n .. m + 3n + 3).  The stored psi carries a pending scale, which
+// cancels in every ratio.
+template <typename T, int W>
+__global__ void __launch_bounds__(W * 32)
+moments_columns_kernel(const Desc<T>* __restrict__ descs, const int2* __restrict__ tiles, double* __restrict__ m)
+{
+    const int2 tile = tiles[blockIdx.x];
+    const Desc<T>& D = descs[tile.x];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int x = tile.y + warp, n = D.n;
+    if (x >= n) return;
+    const T* col = D.psi[D.st->parity] + (size_t)x * D.ld;
+    const T L = T(D.c * D.delta), d = T(D.delta);  // p_y = -L + y Delta, L = c Delta
+    T a0 = T(0), a1 = T(0), a2 = T(0);
+    for (int y = lane; y < n; y += 32) {
+        const T v = col[y], p = T(y) * d - L;
+        const T pv = p * v;
+        a0 += v;
+        a1 += pv;
+        a2 += p * pv;
+    }
+    double s0 = double(a0), s1 = double(a1), s2 = double(a2);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_down_sync(0xffffffffu, s0, o);
+        s1 += __shfl_down_sync(0xffffffffu, s1, o);
+        s2 += __shfl_down_sync(0xffffffffu, s2, o);
+    }
+    if (lane == 0) {
+        m[3 * x] = s0;
+        m[3 * x + 1] = s1;
+        m[3 * x + 2] = s2;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) moments_finish_kernel(const Desc<T>* __restrict__ desc, double* __restrict__ m)
+{
+    const Desc<T>& D = *desc;
+    const int n = D.n, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __shared__ double sums[5];
+    if (warp < 5) {
+        // warp 0: sum psi; 1: sum q psi; 2: sum q^2 psi; 3: sum p psi; 4: sum p^2 psi
+        double acc = 0.0;
+        for (int x = lane; x < n; x += 32) {
+            const double q = (x - D.c) * D.delta;
+            const double c0 = m[3 * x];
+            acc += warp == 0 ? c0 : warp == 1 ? q * c0 : warp == 2 ? q * q * c0 : m[3 * x + warp - 2];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (lane == 0) sums[warp] = acc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double mq = sums[1] / sums[0], mp = sums[3] / sums[0];
+        double* out = m + 3 * n;
+        out[0] = mq;
+        out[1] = sqrt(fmax(sums[2] / sums[0] - mq * mq, 0.0));
+        out[2] = mp;
+        out[3] = sqrt(fmax(sums[4] / sums[0] - mp * mp, 0.0));
+    }
+}
+
 }  // namespace vfps

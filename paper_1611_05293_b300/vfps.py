@@ -27,6 +27,7 @@ EXPORTS = [
     "vfps_batch_create", "vfps_batch_add", "vfps_batch_slot_bytes", "vfps_batch_run",
     "vfps_batch_poll", "vfps_batch_take", "vfps_batch_remove", "vfps_batch_usage",
     "vfps_batch_destroy", "vfps_step_static", "vfps_batch_launches_per_step",
+    "vfps_moments", "vfps_batch_moments",
 ]
 
 
@@ -94,6 +95,8 @@ def lib() -> ctypes.CDLL:
         "vfps_set_impedance": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_double, ctypes.c_double, _D]),
         "vfps_step": (ctypes.c_int, [_VP, _I64]),
         "vfps_profile": (ctypes.c_int, [_VP, _D]),
+        "vfps_moments": (ctypes.c_int, [_VP, _D]),
+        "vfps_batch_moments": (ctypes.c_int, [_VP, _I32, _D]),
         "vfps_csr_power": (ctypes.c_int, [_VP, _D, _I64, ctypes.POINTER(_I64)]),
         "vfps_charge_series": (ctypes.c_int, [_VP, _D, _I64, ctypes.POINTER(_I64)]),
         "vfps_get_state": (ctypes.c_int, [_VP, _D]),
@@ -198,6 +201,12 @@ class Simulation:
         _check(lib().vfps_profile(self._h, _dptr(out)), "vfps_profile")
         return out
 
+    def moments(self) -> np.ndarray:
+        """(<q>, sigma_q, <p>, sigma_p) of the current state, computed on the device."""
+        out = np.empty(4)
+        _check(lib().vfps_moments(self._h, _dptr(out)), "vfps_moments")
+        return out
+
     def _series(self, fn, cap):
         out = np.empty(max(cap, 1))
         k = _I64()
@@ -290,6 +299,12 @@ class Batch:
         k = _I32()
         _check(lib().vfps_batch_poll(self._b, out, cap, ctypes.byref(k)), "vfps_batch_poll")
         return [out[i] for i in range(k.value)]
+
+    def moments(self, slot: int) -> np.ndarray:
+        """(<q>, sigma_q, <p>, sigma_p) of a slot's current state, on the device."""
+        out = np.empty(4)
+        _check(lib().vfps_batch_moments(self._b, int(slot), _dptr(out)), "vfps_batch_moments")
+        return out
 
     def take(self, slot: int, psi=True, rho=True, power_cap: int = 1 << 22):
         n = self.params[slot].n

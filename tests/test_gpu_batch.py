@@ -162,3 +162,19 @@ def test_mixed_rotation_modes_in_one_batch(V):
         assert np.array_equal(r["power"], sim.csr_power()), i
         sim.close()
     b.close()
+
+
+def test_batch_moments_equal_solo(V):
+    """vfps_batch_moments of a slot equals vfps_moments of the same run alone."""
+    n, spp, ns = 128, 800, 30
+    b = V.Batch(3)
+    slots = [b.add(V.Params(n=n, steps_per_period=spp, beta=1e-2), W.blobs(n, 70 + i),
+                   V.IMPEDANCE_PARALLEL_PLATES, 2.0, 0.6 + 0.2 * i, nsteps=ns) for i in range(3)]
+    b.run(ns)
+    for i, sl in enumerate(slots):
+        sim = V.Simulation(V.Params(n=n, steps_per_period=spp, beta=1e-2), W.blobs(n, 70 + i))
+        sim.set_impedance(V.IMPEDANCE_PARALLEL_PLATES, 2.0, 0.6 + 0.2 * i)
+        sim.step(ns)
+        assert np.array_equal(b.moments(sl), sim.moments()), i
+        sim.close()
+    b.close()

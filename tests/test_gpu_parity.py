@@ -236,3 +236,18 @@ def test_manhattan_sixth_turn_permutation(V, n):
                     ref[x, y] = f0[xs, ys]
         assert rel_linf(out, ref) < tol
         sim.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(1, 1e-12), (0, 1e-6)])
+def test_moments_match_oracle(V, precision, tol):
+    """Bunch moments computed on the device against the oracle's moments of
+    the same state (an off-centre Gaussian after 50 steps with wake)."""
+    from paper_1611_05293_b300 import workloads as W
+    for n, rot in ((64, 0), (256, 0), (100, 1)):
+        psi0 = W.gaussian(n, 6.0, 0.8, 1.1, 0.4, -0.3)
+        sim, op, zr, zi = make(V, n, precision, model=2, Pi=2.0, S=0.8, psi=psi0, rotation=rot)
+        sim.step(50)
+        m = sim.moments()
+        ref = O.moments(op, sim.get_state())
+        assert np.max(np.abs(m - ref)) < tol * 10, (n, rot, m, ref)
+        sim.close()
