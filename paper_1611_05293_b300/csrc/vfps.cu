@@ -769,14 +769,21 @@ int drain(Instance& I, cudaStream_t s)
 {
     long long lo = I.drained, hi = I.steps_queued;
     if (hi <= lo) return VFPS_OK;
-    std::vector<double> pr(I.ring), qr(I.ring);
-    CU(cudaMemcpyAsync(pr.data(), I.pring, sizeof(double) * I.ring, cudaMemcpyDeviceToHost, s));
-    CU(cudaMemcpyAsync(qr.data(), I.qring, sizeof(double) * I.ring, cudaMemcpyDeviceToHost, s));
-    CU(cudaStreamSynchronize(s));
-    for (long long t = lo; t < hi; ++t) {
-        I.pw.push_back(pr[t & (I.ring - 1)]);
-        I.qw.push_back(qr[t & (I.ring - 1)]);
+    // only the new entries: [lo, hi) wraps around the ring at most once
+    const long long cnt = hi - lo, mask = I.ring - 1;
+    const size_t old = I.pw.size();
+    I.pw.resize(old + cnt);
+    I.qw.resize(old + cnt);
+    const long long a = lo & mask, first = std::min<long long>(cnt, I.ring - a);
+    CU(cudaMemcpyAsync(I.pw.data() + old, I.pring + a, sizeof(double) * first, cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(I.qw.data() + old, I.qring + a, sizeof(double) * first, cudaMemcpyDeviceToHost, s));
+    if (cnt > first) {
+        CU(cudaMemcpyAsync(I.pw.data() + old + first, I.pring, sizeof(double) * (cnt - first),
+                           cudaMemcpyDeviceToHost, s));
+        CU(cudaMemcpyAsync(I.qw.data() + old + first, I.qring, sizeof(double) * (cnt - first),
+                           cudaMemcpyDeviceToHost, s));
     }
+    CU(cudaStreamSynchronize(s));
     I.drained = hi;
     return VFPS_OK;
 }
@@ -1356,6 +1363,9 @@ int vfps_batch_take(vfps_batch* b, int32_t slot, double* psi_out, double* rho_ou
         *n_power = (int64_t)I.pw.size();
     }
     if (steps_done) *steps_done = I.steps_queued;
+    // copy_state has already synchronised and read the status word; rho (if
+    // asked for) still needs a synchronisation, read_status provides it
+    if (psi_out && !rho_out) return VFPS_OK;
     return read_status(I, b->stream);
 }
 
