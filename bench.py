@@ -202,6 +202,28 @@ def c5_single(V, torch, stream, warmup, steps=400):
             "roofline_frac": 8.0 * 1024 * 1024 / (dt / steps) / 1e9 / measured_peaks()[0]}
 
 
+def m6_rotation(V, torch, stream, warmup, steps=1000):
+    """The paper's rotation benchmark set-up (Fig. sm-performance): one N=512
+    grid, 1000 steps, no wake and no damping, for the standard and the
+    Manhattan rotation (the kick and Fokker-Planck passes still run, with
+    identity weights, inside the same fused kernel)."""
+    out = {}
+    for name, rot in (("standard", 0), ("manhattan", 1)):
+        sim = V.Simulation(V.Params(n=512, steps_per_period=1000, beta=0.0, rotation=rot), None, stream)
+        sim.step(warmup)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dt = e0.elapsed_time(e1) / 1e3
+        sim.close()
+        out[name] = {"value": 512 * 512 * steps / dt, "unit": "cell-updates/s", "ms_per_step": 1e3 * dt / steps}
+    out["workload"] = "single simulation N=512, 1000 steps, no wake, beta=0"
+    return out
+
+
 def cpu_baseline(n, spp, beta, budget_s=12.0):
     """FP64 oracle on the host cores: one N=n instance of the scan for as many
     steps as fit in budget_s (after one untimed step)."""
@@ -384,6 +406,7 @@ def main():
         line["c3_scan_64"] = c3_scan_64(V, torch, stream, args.warmup)
         line["c5_n1024"] = c5_single(V, torch, stream, args.warmup)
         line["manhattan_scan"] = manhattan_scan(V, torch, stream, args.warmup)
+        line["m6_rotation_n512"] = m6_rotation(V, torch, stream, args.warmup)
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(n, spp, beta)
     print(json.dumps(line))
