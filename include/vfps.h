@@ -223,6 +223,25 @@ int vfps_batch_take(vfps_batch* b, int32_t slot, double* psi_out, double* rho_ou
  * vfps_moments.  Synchronises the batch.  Errors: EINVAL, ECUDA, ENAN. */
 int vfps_batch_moments(vfps_batch* b, int32_t slot, double* out);
 
+/* Autotuner of the batch's FP32 launch groups (on = 1, the default; 0 keeps
+ * the built-in rules).  For a group of a configuration not seen before in the
+ * process -- key: n, precision, rotation, steps per period, group size
+ * rounded up to a power of two -- the first steps of vfps_batch_run time the
+ * candidate CTA widths W in {8, 4, 2} and strip lengths (4..32 tiles), four
+ * back-to-back steps each after four warm-up steps, and keep the fastest for
+ * the rest of the process (a run shorter than the tuning keeps tuning on its
+ * next call).  The timed steps are ordinary steps: every candidate gives the same
+ * bits.  Setting VFPS_AUTOTUNE=0 in the environment disables it everywhere.
+ * Errors: EINVAL. */
+int vfps_batch_autotune(vfps_batch* b, int32_t on);
+
+/* Current launch groups of the batch: for each group, five int32 in out --
+ * grid size n, instances, CTA width W, tiles per CTA strip, 1 if its shape is
+ * final (tuned or fixed) or 0 while the autotuner is still timing it.  At most
+ * cap groups; *n_groups gets the number written.  Errors: EINVAL, ENOMEM,
+ * ECUDA. */
+int vfps_batch_shapes(vfps_batch* b, int32_t* out, int32_t cap, int32_t* n_groups);
+
 /* Free a slot (its memory returns to the budget). */
 int vfps_batch_remove(vfps_batch* b, int32_t slot);
 

@@ -13,6 +13,7 @@
 #include <cmath>
 #include <complex>
 #include <cstdint>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <deque>
@@ -536,6 +537,15 @@ struct Group {
     int kr = 4;   // FP32 streaming kernel: rows per lane of the kick/FP blocks
     int n = 0;    // grid size shared by the group's instances
     int rot = 0;  // rotation shared by the group's instances (FP32 streaming kernel)
+    // batches: members, where their descriptors and tiles sit in the batch
+    // arrays, and the autotuner's state (candidates (W, tps) still to time)
+    std::vector<Instance*> members;
+    size_t off_d = 0, off_t = 0;
+    std::vector<std::pair<int, int>> cands;
+    std::vector<float> cand_ms;
+    int cand = -1;  // candidate of the step in flight; -1 = warm-up step
+    std::tuple<int, int, int, int, int, int> tune_key;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
     size_t smem = 0;
     int ntiles = 0;
     void* ddescs = nullptr;  // array of Desc<T>
@@ -1091,6 +1101,9 @@ struct vfps_batch {
     size_t gbytes = 0;
     std::vector<cudaStream_t> pool;   // one stream per group, forked from `stream`
     std::vector<cudaEvent_t> events;  // fork event + one join event per pool stream
+    std::vector<cudaEvent_t> timers;  // two timing events per pool stream (autotuner)
+    std::vector<unsigned char> hbuf;  // host copy of gmem
+    bool autotune = true;
 };
 
 namespace {
@@ -1103,6 +1116,84 @@ void free_groups(vfps_batch* b)
     b->gmem = nullptr;
     b->gbytes = 0;
     b->groups.clear();
+}
+
+// Lay out a batch group for CTA width W and strips of tps tiles: its
+// members' descriptors (ntiles patched to CTAs per step) and its tile table,
+// in the host copy of the group arrays; shared memory and tile count.
+void layout_group(vfps_batch* b, Group& g, int W, int tps)
+{
+    g.W = W;
+    g.tps = tps;
+    g.smem = 0;
+    const size_t dsz = g.prec ? sizeof(Desc<double>) : sizeof(Desc<float>);
+    int2* ht = (int2*)(b->hbuf.data() + g.off_t);
+    int nt = 0;
+    for (size_t k = 0; k < g.members.size(); ++k) {
+        Instance* I = g.members[k];
+        unsigned char* hd = b->hbuf.data() + g.off_d + k * dsz;
+        std::memcpy(hd, I->hdesc, dsz);
+        const int per_inst = (I->n + W - 1) / W;
+        for (int t = 0; t < per_inst; ++t) ht[nt++] = make_int2((int)k, t * W);
+        if (g.prec) ((Desc<double>*)hd)->ntiles = per_inst / tps;
+        else ((Desc<float>*)hd)->ntiles = per_inst / tps;
+        g.smem = std::max(g.smem, step_smem(&I->p, W));
+        if (g.fast) g.smem = std::max(g.smem, fast_smem(&I->p, W));
+    }
+    g.ntiles = nt;
+}
+
+int default_tps(const Group& g, int W)
+{
+    const int per_inst = (g.n + W - 1) / W;
+    int nt = 0;
+    for (const Instance* I : g.members) nt += (I->n + W - 1) / W;
+    const int target = 2 * num_sms();
+    for (int t = per_inst; t >= 1; --t)
+        if (per_inst % t == 0 && (t == 1 || nt / t >= target)) return t;
+    return 1;
+}
+
+// ---- autotuner: per (n, precision, rotation, steps/period, group size
+// rounded up to a power of two, default width) the fastest (W, tps) of the
+// FP32 streaming kernel, timed on the group's own first steps.  Every
+// candidate computes the same bits (results do not depend on the CTA width or
+// the strip length), so the timed steps are ordinary steps of the run.
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, int, int>, std::pair<int, int>> g_tuned;
+constexpr int kTuneSteps = 4;  // steps timed per candidate
+
+bool autotune_enabled()
+{
+    const char* e = std::getenv("VFPS_AUTOTUNE");
+    return !(e && e[0] == '0');
+}
+
+bool tuned_choice(const std::tuple<int, int, int, int, int, int>& key, std::pair<int, int>* out)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(key);
+    if (it == g_tuned.end()) return false;
+    *out = it->second;
+    return true;
+}
+
+std::vector<std::pair<int, int>> tune_candidates(const Group& g)
+{
+    std::vector<std::pair<int, int>> c;
+    const long long lim = device_smem_limit() - 1024;
+    for (int W : {8, 4, 2}) {
+        bool fits = true;
+        for (const Instance* I : g.members) fits = fits && (long long)fast_smem(&I->p, W) <= lim;
+        if (!fits) continue;
+        const int per_inst = (g.n + W - 1) / W;
+        int nt = 0;
+        for (const Instance* I : g.members) nt += (I->n + W - 1) / W;
+        for (int t : {4, 8, 16, 32})
+            if (per_inst % t == 0 && nt / t >= num_sms()) c.push_back({W, t});
+        if (c.empty() || c.back().first != W) c.push_back({W, default_tps(g, W)});
+    }
+    return c;
 }
 
 // Group the slots that still have steps to run by (precision, N_I, W, n):
@@ -1144,11 +1235,17 @@ int rebuild_groups(vfps_batch* b)
         CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
         b->events.push_back(ev);
     }
+    while (b->timers.size() < 2 * b->pool.size()) {
+        cudaEvent_t ev;
+        CU(cudaEventCreate(&ev));
+        b->timers.push_back(ev);
+    }
+    // descriptor and tile arrays, with room for the narrowest width (W = 2)
     size_t total = 0;
     std::vector<std::pair<size_t, size_t>> offs;
     for (auto& kv : cls) {
         size_t nt = 0;
-        for (Instance* I : kv.second) nt += I->ntiles;
+        for (Instance* I : kv.second) nt += (size_t)(I->n + 1) / 2;
         size_t od = align_up(total, kAlign);
         size_t ot = align_up(od + kv.second.size() * sizeof(Desc<double>), kAlign);
         total = ot + nt * sizeof(int2);
@@ -1159,54 +1256,82 @@ int rebuild_groups(vfps_batch* b)
         return VFPS_ENOMEM;
     }
     b->gbytes = total;
-    std::vector<unsigned char> host(total, 0);
+    b->hbuf.assign(total, 0);
     size_t gi = 0;
     for (auto& kv : cls) {
         Group g;
         g.prec = std::get<0>(kv.first);
         g.ni = std::get<1>(kv.first) / 4;
         g.fast = (std::get<1>(kv.first) >> 1) & 1;
-        g.W = std::get<2>(kv.first);
         g.stream = b->pool[gi];
-        g.ddescs = (unsigned char*)b->gmem + offs[gi].first;
-        g.dtiles = (int2*)((unsigned char*)b->gmem + offs[gi].second);
-        int2* ht = (int2*)(host.data() + offs[gi].second);
-        int nt = 0;
-        for (size_t k = 0; k < kv.second.size(); ++k) {
-            Instance* I = kv.second[k];
-            size_t dsz = g.prec ? sizeof(Desc<double>) : sizeof(Desc<float>);
-            std::memcpy(host.data() + offs[gi].first + k * dsz, I->hdesc, dsz);
-            for (int t = 0; t < I->ntiles; ++t) ht[nt++] = make_int2((int)k, t * I->W);
-            g.smem = std::max(g.smem, step_smem(&I->p, I->W));
-            if (g.fast) g.smem = std::max(g.smem, fast_smem(&I->p, I->W));
-        }
-        g.ntiles = nt;
+        g.t0 = b->timers[2 * gi];
+        g.t1 = b->timers[2 * gi + 1];
+        g.members = kv.second;
+        g.off_d = offs[gi].first;
+        g.off_t = offs[gi].second;
+        g.ddescs = (unsigned char*)b->gmem + g.off_d;
+        g.dtiles = (int2*)((unsigned char*)b->gmem + g.off_t);
         g.kr = fast_kr(kv.second[0]->p.n);  // a group shares n
         g.n = kv.second[0]->p.n;
         g.rot = kv.second[0]->p.rotation;
+        int W = std::get<2>(kv.first), tps = 1;
         if (g.fast) {
             // a strip of tps consecutive tiles per CTA: the largest divisor of
             // the tiles per instance that still leaves two CTAs per SM (long
             // strips spread the CTA prologue and the halo columns over more
-            // cells; measured on 512 x N=256: 4 tiles 161 us, 8 152, 16 148)
-            const int per_inst = kv.second[0]->ntiles;
-            const int target = 2 * num_sms();
-            for (int t = per_inst; t >= 1; --t)
-                if (per_inst % t == 0 && (t == 1 || nt / t >= target)) {
-                    g.tps = t;
-                    break;
-                }
-            for (size_t k = 0; k < kv.second.size(); ++k) {
-                Desc<float>* dd = (Desc<float>*)(host.data() + offs[gi].first + k * sizeof(Desc<float>));
-                dd->ntiles = per_inst / g.tps;
+            // cells; measured on 512 x N=256: 4 tiles 161 us, 8 152, 16 148);
+            // the autotuner replaces this choice once it has timed the group
+            tps = default_tps(g, W);
+            const Instance* I0 = kv.second[0];
+            const int cnt = (int)kv.second.size();
+            int bucket = 1;
+            while (bucket < cnt) bucket <<= 1;
+            g.tune_key = std::make_tuple(I0->n, g.prec, g.rot, I0->p.steps_per_period, bucket, I0->W);
+            std::pair<int, int> best;
+            if (tuned_choice(g.tune_key, &best)) {
+                W = best.first;
+                tps = best.second;
+            } else if (b->autotune && autotune_enabled()) {
+                g.cands = tune_candidates(g);
+                g.cand = -1;
             }
         }
+        layout_group(b, g, W, tps);
         b->groups.push_back(g);
         ++gi;
     }
-    CU(cudaMemcpyAsync(b->gmem, host.data(), total, cudaMemcpyHostToDevice, b->stream));
+    CU(cudaMemcpyAsync(b->gmem, b->hbuf.data(), total, cudaMemcpyHostToDevice, b->stream));
     CU(cudaStreamSynchronize(b->stream));
     b->dirty = false;
+    return VFPS_OK;
+}
+
+// After a tuning step: record each tuning group's time, move on to its next
+// candidate, and once all are timed keep the fastest (cached per key).
+int tune_step_done(vfps_batch* b)
+{
+    CU(cudaStreamSynchronize(b->stream));
+    for (Group& g : b->groups) {
+        if (g.cands.empty()) continue;
+        float ms = 0.f;
+        CU(cudaEventElapsedTime(&ms, g.t0, g.t1));
+        if (g.cand >= 0) g.cand_ms.push_back(ms);  // the warm-up steps (-1) are not kept
+        if (++g.cand < (int)g.cands.size()) continue;
+        size_t best = 0;
+        for (size_t i = 1; i < g.cand_ms.size(); ++i)
+            if (g.cand_ms[i] < g.cand_ms[best]) best = i;
+        const std::pair<int, int> choice = g.cands[best];
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tuned[g.tune_key] = choice;
+        }
+        g.cands.clear();
+        g.cand_ms.clear();
+        layout_group(b, g, choice.first, choice.second);
+        const size_t bytes = g.off_t + sizeof(int2) * g.ntiles - g.off_d;
+        CU(cudaMemcpyAsync((unsigned char*)b->gmem + g.off_d, b->hbuf.data() + g.off_d, bytes,
+                           cudaMemcpyHostToDevice, b->stream));
+    }
     return VFPS_OK;
 }
 
@@ -1303,19 +1428,40 @@ int vfps_batch_run(vfps_batch* b, int64_t chunk_steps)
             k = std::min(k, room);
         }
         if (!any) break;
+        // while a group is being tuned, kTuneSteps steps at a time (back to
+        // back, as in steady state), timed on the group's own stream with the
+        // candidate under test
+        bool tuning = false;
+        for (const Group& g : b->groups) tuning = tuning || !g.cands.empty();
+        if (tuning) k = std::min<long long>(k, kTuneSteps);
         // fork: every group stream waits for the batch stream, runs its k
         // steps, and the batch stream waits for all of them again
         cudaEvent_t fork = b->events.back();
         CU(cudaEventRecord(fork, b->stream));
         for (const Group& g : b->groups) CU(cudaStreamWaitEvent(g.stream, fork, 0));
+        for (Group& g : b->groups) {
+            if (g.cands.empty()) continue;
+            if (g.cand >= 0) {  // upload the layout of the candidate under test
+                layout_group(b, g, g.cands[g.cand].first, g.cands[g.cand].second);
+                const size_t bytes = g.off_t + sizeof(int2) * g.ntiles - g.off_d;
+                CU(cudaMemcpyAsync((unsigned char*)b->gmem + g.off_d, b->hbuf.data() + g.off_d, bytes,
+                                   cudaMemcpyHostToDevice, g.stream));
+            }
+            CU(cudaEventRecord(g.t0, g.stream));
+        }
         for (long long s = 0; s < k; ++s)
             for (const Group& g : b->groups) {
                 rc = launch_step(g, g.stream);
                 if (rc) return rc;
             }
         for (size_t i = 0; i < b->groups.size(); ++i) {
+            if (!b->groups[i].cands.empty()) CU(cudaEventRecord(b->groups[i].t1, b->groups[i].stream));
             CU(cudaEventRecord(b->events[i], b->groups[i].stream));
             CU(cudaStreamWaitEvent(b->stream, b->events[i], 0));
+        }
+        if (tuning) {
+            rc = tune_step_done(b);
+            if (rc) return rc;
         }
         for (Instance* I : b->slots) {
             if (!I || remaining(I) <= 0) continue;
@@ -1367,6 +1513,35 @@ int vfps_batch_take(vfps_batch* b, int32_t slot, double* psi_out, double* rho_ou
     // asked for) still needs a synchronisation, read_status provides it
     if (psi_out && !rho_out) return VFPS_OK;
     return read_status(I, b->stream);
+}
+
+int vfps_batch_shapes(vfps_batch* b, int32_t* out, int32_t cap, int32_t* n_groups)
+{
+    if (!b || !n_groups || cap < 0 || (cap > 0 && !out)) return VFPS_EINVAL;
+    if (b->dirty) {
+        int rc = rebuild_groups(b);
+        if (rc) return rc;
+    }
+    int k = 0;
+    for (const Group& g : b->groups) {
+        if (k < cap) {
+            out[5 * k] = g.n;
+            out[5 * k + 1] = (int32_t)g.members.size();
+            out[5 * k + 2] = g.W;
+            out[5 * k + 3] = g.tps;
+            out[5 * k + 4] = g.cands.empty() ? 1 : 0;
+        }
+        ++k;
+    }
+    *n_groups = std::min(k, cap);
+    return VFPS_OK;
+}
+
+int vfps_batch_autotune(vfps_batch* b, int32_t on)
+{
+    if (!b || (on != 0 && on != 1)) return VFPS_EINVAL;
+    b->autotune = on == 1;
+    return VFPS_OK;
 }
 
 int vfps_batch_moments(vfps_batch* b, int32_t slot, double* out)

@@ -27,7 +27,7 @@ EXPORTS = [
     "vfps_batch_create", "vfps_batch_add", "vfps_batch_slot_bytes", "vfps_batch_run",
     "vfps_batch_poll", "vfps_batch_take", "vfps_batch_remove", "vfps_batch_usage",
     "vfps_batch_destroy", "vfps_step_static", "vfps_batch_launches_per_step",
-    "vfps_moments", "vfps_batch_moments",
+    "vfps_moments", "vfps_batch_moments", "vfps_batch_autotune", "vfps_batch_shapes",
 ]
 
 
@@ -97,6 +97,8 @@ def lib() -> ctypes.CDLL:
         "vfps_profile": (ctypes.c_int, [_VP, _D]),
         "vfps_moments": (ctypes.c_int, [_VP, _D]),
         "vfps_batch_moments": (ctypes.c_int, [_VP, _I32, _D]),
+        "vfps_batch_autotune": (ctypes.c_int, [_VP, _I32]),
+        "vfps_batch_shapes": (ctypes.c_int, [_VP, ctypes.POINTER(_I32), _I32, ctypes.POINTER(_I32)]),
         "vfps_csr_power": (ctypes.c_int, [_VP, _D, _I64, ctypes.POINTER(_I64)]),
         "vfps_charge_series": (ctypes.c_int, [_VP, _D, _I64, ctypes.POINTER(_I64)]),
         "vfps_get_state": (ctypes.c_int, [_VP, _D]),
@@ -299,6 +301,19 @@ class Batch:
         k = _I32()
         _check(lib().vfps_batch_poll(self._b, out, cap, ctypes.byref(k)), "vfps_batch_poll")
         return [out[i] for i in range(k.value)]
+
+    def shapes(self) -> list:
+        """Launch groups: dicts with n, instances, W, tiles per strip, final."""
+        cap = 64
+        out = (_I32 * (5 * cap))()
+        k = _I32()
+        _check(lib().vfps_batch_shapes(self._b, out, cap, ctypes.byref(k)), "vfps_batch_shapes")
+        return [dict(n=out[5 * i], instances=out[5 * i + 1], W=out[5 * i + 2], tps=out[5 * i + 3],
+                     final=bool(out[5 * i + 4])) for i in range(k.value)]
+
+    def autotune(self, on: bool = True):
+        """Enable or disable the per-configuration autotuner (on by default)."""
+        _check(lib().vfps_batch_autotune(self._b, 1 if on else 0), "vfps_batch_autotune")
 
     def moments(self, slot: int) -> np.ndarray:
         """(<q>, sigma_q, <p>, sigma_p) of a slot's current state, on the device."""

@@ -178,3 +178,25 @@ def test_batch_moments_equal_solo(V):
         assert np.array_equal(b.moments(sl), sim.moments()), i
         sim.close()
     b.close()
+
+
+def test_autotuner_times_candidates_and_keeps_bits(V):
+    """The autotuner times candidate launch shapes on the batch's first steps;
+    the shapes become final, and results equal the same run with the
+    autotuner off (and the solo runs) bit for bit."""
+    n, spp, ns, count = 128, 700, 80, 12
+    pts = [(0.5 + 0.1 * i, 1.0 + (i % 3)) for i in range(count)]
+    out = {}
+    for on in (True, False):
+        b = V.Batch(count)
+        b.autotune(on)
+        slots = [b.add(V.Params(n=n, steps_per_period=spp, beta=1e-2), W.blobs(n, 90 + i),
+                       V.IMPEDANCE_PARALLEL_PLATES, Pi, S, nsteps=ns) for i, (S, Pi) in enumerate(pts)]
+        b.run(ns // 2)
+        sh = b.shapes()
+        assert sh and all(g["n"] == n for g in sh)
+        b.run(ns - ns // 2)
+        out[on] = [b.take(s) for s in slots]
+        b.close()
+    for a, c in zip(out[True], out[False]):
+        assert np.array_equal(a["psi"], c["psi"]) and np.array_equal(a["power"], c["power"])
