@@ -40,10 +40,11 @@ HBM_FALLBACK_GBS = 6400.0
 
 # DRAM bytes (read + write) of one launch of step_kernel_f32 on a 256-instance
 # N=256 group, from the ncu capture summarised in
-# profiles/step_kernel_f32_batched_n256.md; a step of the 512-instance
-# benchmark is two such launches.  Set to None whenever the kernel changes
-# until a new capture is taken.
-MEASURED_TRAFFIC_PER_LAUNCH = None
+# profiles/step_kernel_f32_batched_n256.md (launch shape W=4, 8-tile strips, the
+# autotuner's choice; W=8 with 16-tile strips measured 96.1 MB); a step of the
+# 512-instance benchmark is two such launches.  Set to None whenever the kernel
+# changes until a new capture is taken.
+MEASURED_TRAFFIC_PER_LAUNCH = 96.2e6
 
 
 def measured_peaks():
@@ -115,9 +116,14 @@ def scan_points(count: int):
     return [base[i % len(base)] for i in range(count)]
 
 
+PIN_SHAPE = None  # (W, tiles per strip) from --shape: fixed launch shape instead of the autotuner's
+
+
 def build_batch(V, count, n, spp, beta, stream, seed=1612, rotation=0):
     from paper_1611_05293_b300 import workloads as W
     b = V.Batch(count, 0, stream)
+    if PIN_SHAPE:
+        b.pin_shape(*PIN_SHAPE)
     psi0 = W.noisy_gaussian(n, seed, 1e-6)
     for S, Pi in scan_points(count):
         b.add(V.Params(n=n, steps_per_period=spp, beta=beta, rotation=rotation), psi0, V.IMPEDANCE_PARALLEL_PLATES,
@@ -305,7 +311,11 @@ def main():
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the serving / C3 / C5 side measurements")
+    ap.add_argument("--shape", default="", help="W,tps: fixed batch launch shape (profiling runs)")
     args = ap.parse_args()
+    global PIN_SHAPE
+    if args.shape:
+        PIN_SHAPE = tuple(int(v) for v in args.shape.split(","))
     if args.impl == "reference":
         run_reference(args)
         return
@@ -326,7 +336,8 @@ def main():
     hbm, peak_kind = measured_peaks()
 
     # ---- batched scan (the headline)
-    calibrate(V, torch, stream, args.instances, n, spp, beta)
+    if not PIN_SHAPE:
+        calibrate(V, torch, stream, args.instances, n, spp, beta)
     b = build_batch(V, args.instances, n, spp, beta, stream)
     b.run(args.warmup)
     launches = b.launches_per_step()

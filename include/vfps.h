@@ -242,6 +242,13 @@ int vfps_batch_autotune(vfps_batch* b, int32_t on);
  * ECUDA. */
 int vfps_batch_shapes(vfps_batch* b, int32_t* out, int32_t cap, int32_t* n_groups);
 
+/* Fix the launch shape of the batch's FP32 groups: CTA width W (2, 4 or 8)
+ * and tps tiles per CTA strip, instead of the autotuner's or the built-in
+ * choice, for groups where it fits (shared memory, tps dividing the tiles per
+ * instance); W = tps = 0 releases it.  Results do not depend on the shape.
+ * Errors: EINVAL. */
+int vfps_batch_pin_shape(vfps_batch* b, int32_t W, int32_t tps);
+
 /* Free a slot (its memory returns to the budget). */
 int vfps_batch_remove(vfps_batch* b, int32_t slot);
 

@@ -1104,6 +1104,7 @@ struct vfps_batch {
     std::vector<cudaEvent_t> timers;  // two timing events per pool stream (autotuner)
     std::vector<unsigned char> hbuf;  // host copy of gmem
     bool autotune = true;
+    int pin_W = 0, pin_tps = 0;       // vfps_batch_pin_shape: fixed shape of FP32 groups
 };
 
 namespace {
@@ -1176,6 +1177,16 @@ bool tuned_choice(const std::tuple<int, int, int, int, int, int>& key, std::pair
     if (it == g_tuned.end()) return false;
     *out = it->second;
     return true;
+}
+
+// A pinned shape applies to a group if its shared memory fits and the strip
+// length divides the tiles per instance.
+bool pin_fits(const Group& g, int W, int tps)
+{
+    const long long lim = device_smem_limit() - 1024;
+    for (const Instance* I : g.members)
+        if ((long long)fast_smem(&I->p, W) > lim) return false;
+    return tps >= 1 && ((g.n + W - 1) / W) % tps == 0;
 }
 
 std::vector<std::pair<int, int>> tune_candidates(const Group& g)
@@ -1288,7 +1299,10 @@ int rebuild_groups(vfps_batch* b)
             while (bucket < cnt) bucket <<= 1;
             g.tune_key = std::make_tuple(I0->n, g.prec, g.rot, I0->p.steps_per_period, bucket, I0->W);
             std::pair<int, int> best;
-            if (tuned_choice(g.tune_key, &best)) {
+            if (b->pin_W && pin_fits(g, b->pin_W, b->pin_tps)) {
+                W = b->pin_W;
+                tps = b->pin_tps;
+            } else if (tuned_choice(g.tune_key, &best)) {
                 W = best.first;
                 tps = best.second;
             } else if (b->autotune && autotune_enabled()) {
@@ -1534,6 +1548,16 @@ int vfps_batch_shapes(vfps_batch* b, int32_t* out, int32_t cap, int32_t* n_group
         ++k;
     }
     *n_groups = std::min(k, cap);
+    return VFPS_OK;
+}
+
+int vfps_batch_pin_shape(vfps_batch* b, int32_t W, int32_t tps)
+{
+    if (!b || !((W == 0 && tps == 0) || ((W == 2 || W == 4 || W == 8) && tps >= 1 && tps <= 256)))
+        return VFPS_EINVAL;
+    b->pin_W = W;
+    b->pin_tps = tps;
+    b->dirty = true;
     return VFPS_OK;
 }
 

@@ -28,6 +28,7 @@ EXPORTS = [
     "vfps_batch_poll", "vfps_batch_take", "vfps_batch_remove", "vfps_batch_usage",
     "vfps_batch_destroy", "vfps_step_static", "vfps_batch_launches_per_step",
     "vfps_moments", "vfps_batch_moments", "vfps_batch_autotune", "vfps_batch_shapes",
+    "vfps_batch_pin_shape",
 ]
 
 
@@ -98,6 +99,7 @@ def lib() -> ctypes.CDLL:
         "vfps_moments": (ctypes.c_int, [_VP, _D]),
         "vfps_batch_moments": (ctypes.c_int, [_VP, _I32, _D]),
         "vfps_batch_autotune": (ctypes.c_int, [_VP, _I32]),
+        "vfps_batch_pin_shape": (ctypes.c_int, [_VP, _I32, _I32]),
         "vfps_batch_shapes": (ctypes.c_int, [_VP, ctypes.POINTER(_I32), _I32, ctypes.POINTER(_I32)]),
         "vfps_csr_power": (ctypes.c_int, [_VP, _D, _I64, ctypes.POINTER(_I64)]),
         "vfps_charge_series": (ctypes.c_int, [_VP, _D, _I64, ctypes.POINTER(_I64)]),
@@ -310,6 +312,10 @@ class Batch:
         _check(lib().vfps_batch_shapes(self._b, out, cap, ctypes.byref(k)), "vfps_batch_shapes")
         return [dict(n=out[5 * i], instances=out[5 * i + 1], W=out[5 * i + 2], tps=out[5 * i + 3],
                      final=bool(out[5 * i + 4])) for i in range(k.value)]
+
+    def pin_shape(self, W: int = 0, tps: int = 0):
+        """Fix the CTA width and strip length of the FP32 groups (0, 0 releases)."""
+        _check(lib().vfps_batch_pin_shape(self._b, int(W), int(tps)), "vfps_batch_pin_shape")
 
     def autotune(self, on: bool = True):
         """Enable or disable the per-configuration autotuner (on by default)."""
