@@ -407,6 +407,8 @@ __device__ void finalise(const Desc<T>& D, unsigned char* smem, int is_step)
     double* pterm = cs + ((n + 1) & ~1);                 // H/2+1 power terms
     double* red = pterm + H / 2 + 2;
 
+    // the step counter, read early (its latency overlaps the transforms)
+    const long long t_now = tid == 0 ? D.st->t : 0;
     // one round of asynchronous copies: twiddles, impedance, column sums
     // (written by the other CTAs of this step; .cg keeps L1 out of the way)
     {
@@ -432,12 +434,14 @@ __device__ void finalise(const Desc<T>& D, unsigned char* smem, int is_step)
     }
     __syncthreads();
 
-    // forward transform; meanwhile warp 0 sums the charge Q = Delta^2 sum cs
+    // forward transform; meanwhile one warp sums the charge Q = Delta^2 sum cs
     // into red[0] in FP64
+    // (the last warp: with H/8 <= 32 butterflies per pass it has no FFT work)
+    const int sum_warp = (nt >> 5) - 1;
     T2* Z = fft_h<T, false>(bufB, bufA, bufB, tw, H, [&] {
-        if (tid < 32) {
+        if ((tid >> 5) == sum_warp) {
             const double sum = warp_fixed_sum<double>(cs, n);
-            if (tid == 0) red[0] = sum;
+            if ((tid & 31) == 0) red[0] = sum;
         }
     });
     const double Q = D.delta * D.delta * red[0];
@@ -475,12 +479,12 @@ __device__ void finalise(const Desc<T>& D, unsigned char* smem, int is_step)
     }
     __syncthreads();
 
-    // inverse transform; meanwhile warp 0 sums the power terms into red[1]
+    // inverse transform; meanwhile one warp sums the power terms into red[1]
     // in FP64
     T2* y = fft_h<T, true>(Z, Z == bufA ? bufB : bufA, Z, tw, H, [&] {
-        if (tid < 32) {
+        if ((tid >> 5) == sum_warp) {
             const double sum = warp_fixed_sum<double>(pterm, H / 2 + 1);
-            if (tid == 0) red[1] = sum;
+            if ((tid & 31) == 0) red[1] = sum;
         }
     });
     const T kpv = T(D.kick_per_v * D.dkappa);
@@ -502,7 +506,7 @@ __device__ void finalise(const Desc<T>& D, unsigned char* smem, int is_step)
     if (tid == 0) {
         const double P = D.dkappa * red[1];
         DevState* st = D.st;
-        long long t = st->t;
+        const long long t = t_now;
         if (is_step) {
             D.qring[t & D.ring_mask] = Q;
             D.pring[(t + 1) & D.ring_mask] = P;
