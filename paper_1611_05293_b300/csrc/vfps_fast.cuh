@@ -103,24 +103,28 @@ __device__ __forceinline__ void rotate_block(const float* __restrict__ ring, int
                             {wx23[0].x, wx23[1].x, wx23[2].x, wx23[3].x},
                             {wx23[0].y, wx23[1].y, wx23[2].y, wx23[3].y}};
     const bool e[4] = {false, e1, e2, e3};
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    float2 acc01 = f2(0.f, 0.f), acc23 = f2(0.f, 0.f);
 #pragma unroll
     for (int a = 0; a < 5; ++a) {
         const float4* cp = reinterpret_cast<const float4*>(ring + ((slot0 + a) & (R - 1)) * P + rowoff);
         const float4 q0 = cp[0], q1 = cp[1], q2 = cp[2];
         const float win[12] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, q2.x, q2.y, q2.z, q2.w};
+        float r[4], wa[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            float r = wy[k][0] * win[O + k];
-            r = fmaf(wy[k][1], win[O + k + 1], r);
-            r = fmaf(wy[k][2], win[O + k + 2], r);
-            r = fmaf(wy[k][3], win[O + k + 3], r);
-            const float wa = e[k] ? ((a <= 3) ? wx[k][a] : 0.f) : ((a >= 1) ? wx[k][a - 1] : 0.f);
-            acc[k] = fmaf(wa, r, acc[k]);
+            float v = wy[k][0] * win[O + k];
+            v = fmaf(wy[k][1], win[O + k + 1], v);
+            v = fmaf(wy[k][2], win[O + k + 2], v);
+            r[k] = fmaf(wy[k][3], win[O + k + 3], v);
+            wa[k] = e[k] ? ((a <= 3) ? wx[k][a] : 0.f) : ((a >= 1) ? wx[k][a - 1] : 0.f);
         }
+        acc01 = __ffma2_rn(f2(wa[0], wa[1]), f2(r[0], r[1]), acc01);
+        acc23 = __ffma2_rn(f2(wa[2], wa[3]), f2(r[2], r[3]), acc23);
     }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) out[k] = acc[k];
+    out[0] = acc01.x;
+    out[1] = acc01.y;
+    out[2] = acc23.x;
+    out[3] = acc23.y;
 }
 
 // Kick + Fokker-Planck for the lane's blocks of KR rows of one column.  The
