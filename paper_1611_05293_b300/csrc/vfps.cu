@@ -8,6 +8,7 @@
 // and the batch/slot bookkeeping.  The per-step work runs in the kernels of
 // vfps_kernels.cuh; nothing of the step is computed on the host.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -119,6 +120,28 @@ size_t step_smem(const vfps_params* p, int W)
 }
 
 int g_max_smem = -1;
+
+// Device allocations of the library go through here.  VFPS_FAULT_ALLOC=k in
+// the environment makes the k-th allocation of the process (1-based) fail
+// with ENOMEM without touching the device -- the host-side fault injection
+// the error-path tests use; the allocations after it succeed again.
+long long g_alloc_count = 0;
+
+cudaError_t dev_alloc(void** ptr, size_t bytes)
+{
+    static const long long fail_at = [] {
+        const char* e = std::getenv("VFPS_FAULT_ALLOC");
+        return e ? std::atoll(e) : 0LL;
+    }();
+    if (fail_at > 0 && ++g_alloc_count == fail_at) return cudaErrorMemoryAllocation;
+    return cudaMalloc(ptr, bytes);
+}
+
+// NVTX range for the duration of a scope (host-side trace of the API calls).
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
 
 int device_smem_limit()
 {
@@ -469,7 +492,7 @@ int create_instance(const vfps_params* p, const double* psi0, int ring, cudaStre
     I->phi = 2.0 * kPi / p->steps_per_period;
     size_t offs[14];
     I->dbytes = instance_bytes(p, ring, offs);
-    if (cudaMalloc(&I->dmem, I->dbytes) != cudaSuccess) {
+    if (dev_alloc(&I->dmem, I->dbytes) != cudaSuccess) {
         cudaGetLastError();
         return VFPS_ENOMEM;
     }
@@ -956,6 +979,7 @@ static int ensure_graph(vfps_handle* h)
 int vfps_step(vfps_handle* h, int64_t nsteps)
 {
     if (!h || nsteps < 0) return VFPS_EINVAL;
+    Range r("vfps_step");
     Instance& I = *h->I;
     Group g = single_group(I);
     int rc;
@@ -1262,7 +1286,7 @@ int rebuild_groups(vfps_batch* b)
         total = ot + nt * sizeof(int2);
         offs.push_back({od, ot});
     }
-    if (cudaMalloc(&b->gmem, total) != cudaSuccess) {
+    if (dev_alloc(&b->gmem, total) != cudaSuccess) {
         cudaGetLastError();
         return VFPS_ENOMEM;
     }
@@ -1420,6 +1444,7 @@ int vfps_batch_add(vfps_batch* b, const vfps_params* params, const double* psi0,
 int vfps_batch_run(vfps_batch* b, int64_t chunk_steps)
 {
     if (!b || chunk_steps < 0) return VFPS_EINVAL;
+    Range r("vfps_batch_run");
     int rc;
     while (chunk_steps > 0) {
         if (b->dirty) {
