@@ -48,6 +48,9 @@ extern "C" {
 #define VFPS_ETIMEOUT (-4) /* a bounded device wait ran out                  */
 #define VFPS_ENAN (-5)     /* non-finite or non-positive charge detected     */
 #define VFPS_EBUSY (-6)    /* capacity exhausted (batch slots, HBM budget)   */
+#define VFPS_EBOUNDS (-7)  /* debug build (VFPS_DEBUG) only: a shared-memory
+                              index check failed; the site is named in
+                              vfps_last_cuda_error()                         */
 
 #define VFPS_IMPEDANCE_NONE 0            /* no collective effect                      */
 #define VFPS_IMPEDANCE_FREE_SPACE 1      /* CSR in free space (Sec. II.B)             */

@@ -14,6 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libvfps.so")
+LIB_DEBUG = os.path.join(HERE, "libvfps_debug.so")  # -DVFPS_DEBUG: shared-memory index checks
 SOURCES = [os.path.join(CSRC, f) for f in ("vfps.cu", "impedance_host.cpp")]
 DEPS = SOURCES + [os.path.join(CSRC, "vfps_kernels.cuh"), os.path.join(CSRC, "vfps_fast.cuh"),
                   os.path.join(ROOT, "include", "vfps.h")]
@@ -25,23 +26,28 @@ def nvcc() -> str:
     return cand if os.path.exists(cand) else "nvcc"
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(f) <= t for f in DEPS)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and up_to_date():
-        return LIB
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    """Build libvfps.so (or, with debug, libvfps_debug.so: the same code with
+    the shared-memory index checks of VFPS_DEBUG compiled in)."""
+    lib = LIB_DEBUG if debug else LIB
+    if not force and up_to_date(lib):
+        return lib
     cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
-           "-I", os.path.join(ROOT, "include"), "-o", LIB + ".tmp", *SOURCES, "-lcudart"]
+           "-I", os.path.join(ROOT, "include"), "-o", lib + ".tmp", *SOURCES, "-lcudart"]
+    if debug:
+        cmd.insert(1, "-DVFPS_DEBUG")
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     subprocess.check_call(cmd)
-    os.replace(LIB + ".tmp", LIB)
-    return LIB
+    os.replace(lib + ".tmp", lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -789,12 +789,22 @@ int prologue(Instance& I, cudaStream_t s)
     return launch_project(g, s);
 }
 
+// Status word -> API code.  -100 - k: the debug build's index check k failed.
+int status_code(int status)
+{
+    if (status <= -100) {
+        std::snprintf(g_last_error, sizeof(g_last_error), "debug build: index check %d failed", -100 - status);
+        return VFPS_EBOUNDS;
+    }
+    return status;
+}
+
 int read_status(Instance& I, cudaStream_t s)
 {
     DevState st;
     CU(cudaMemcpyAsync(&st, I.st, sizeof(st), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
-    return st.status;
+    return status_code(st.status);
 }
 
 // Move ring entries [drained, steps_queued) to the host series (synchronises).
@@ -837,7 +847,7 @@ int copy_state(Instance& I, cudaStream_t s, double* psi_out)
                                : (double)reinterpret_cast<float*>(buf.data())[(size_t)i * I.ld + j];
             psi_out[(size_t)i * n + j] = v * st.scale;
         }
-    return st.status;
+    return status_code(st.status);
 }
 
 // Bunch moments of the current state on the device (two small kernels on
@@ -913,6 +923,7 @@ const char* vfps_strerror(int code)
     case VFPS_ETIMEOUT: return "bounded device wait timed out";
     case VFPS_ENAN: return "non-finite or non-positive charge";
     case VFPS_EBUSY: return "capacity exhausted";
+    case VFPS_EBOUNDS: return "index check failed (debug build)";
     }
     return "unknown error";
 }

@@ -107,7 +107,9 @@ __device__ __forceinline__ void rotate_block(const float* __restrict__ ring, int
 #pragma unroll
     for (int a = 0; a < 5; ++a) {
         const float4* cp = reinterpret_cast<const float4*>(ring + ((slot0 + a) & (R - 1)) * P + rowoff);
-        const float4 q0 = cp[0], q1 = cp[1], q2 = cp[2];
+        const bool ok = VFPS_GUARD(rowoff >= 0 && rowoff + 12 <= P && slot0 >= 0 && slot0 < R, 2);
+        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 q0 = ok ? cp[0] : z4, q1 = ok ? cp[1] : z4, q2 = ok ? cp[2] : z4;
         const float win[12] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, q2.x, q2.y, q2.z, q2.w};
         float r[4], wa[4];
 #pragma unroll
@@ -151,7 +153,12 @@ __device__ __forceinline__ float kick_fp_column(const float* __restrict__ colcol
     float lsum = 0.f;
     for (int y0 = KR * lane; y0 < n; y0 += 32 * KR) {
         float win[4 * NV];
-        if constexpr (KR == 8) {
+        // window rows y0 + A2 - O2 .. + 4 NV - 1 of the padded column (8 HC rows)
+        const bool wok = VFPS_GUARD(y0 + A2 - O2 >= 0 && y0 + A2 - O2 + 4 * NV <= 8 * HC, 4);
+        if (!wok) {
+#pragma unroll
+            for (int v = 0; v < 4 * NV; ++v) win[v] = 0.f;
+        } else if constexpr (KR == 8) {
             // chunk of window row 4v: (y0 + A2 - O2)/4 + v = 2*(y0/8 + m) + PAR + v
             const float* b0 = colcol + 4 * ((y0 >> 3) + ((A2 >> 2) >> 1));
             const float* b1 = b0 + 4 * HC;
@@ -199,8 +206,9 @@ __device__ __forceinline__ float kick_fp_column(const float* __restrict__ colcol
         if constexpr (!FP) {
 #pragma unroll
             for (int q4 = 0; q4 < KR / 4; ++q4)
-                *reinterpret_cast<float4*>(dst + split_idx<KR>(kColPad + y0 + 4 * q4, HC)) =
-                    make_float4(b[4 * q4 + 1], b[4 * q4 + 2], b[4 * q4 + 3], b[4 * q4 + 4]);
+                if (VFPS_GUARD(kColPad + y0 + 4 * q4 + 4 <= 8 * HC, 5))
+                    *reinterpret_cast<float4*>(dst + split_idx<KR>(kColPad + y0 + 4 * q4, HC)) =
+                        make_float4(b[4 * q4 + 1], b[4 * q4 + 2], b[4 * q4 + 3], b[4 * q4 + 4]);
         } else {
 #pragma unroll
         for (int q4 = 0; q4 < KR / 4; ++q4) {
@@ -265,6 +273,7 @@ __device__ __forceinline__ void load_columns(float* ring, int R, int P, int RP, 
     for (int k = warp; k < ncols; k += W) {
         const int gx = col0 + k;
         float* dst = ring + (size_t)(gx & (R - 1)) * P + RP + 4 * lane;
+        if (!VFPS_GUARD(RP + n <= P, 1)) continue;
         if (gx >= 0 && gx < n) {
             const float* src = in + (size_t)gx * ld + 4 * lane;
             for (int r4 = lane; r4 < n4; r4 += 32, dst += 128, src += 128) cp_async16(dst, src, 16);
@@ -338,7 +347,8 @@ __device__ __forceinline__ void rotate_column(const float* __restrict__ ring, in
                 if (mx <= -2 || mx >= n || my <= -2 || my >= n) r[k] = 0.f;
             }
         }
-        *reinterpret_cast<float4*>(colcol + split_idx<KR>(kColPad + y0, HC)) = make_float4(r[0], r[1], r[2], r[3]);
+        if (VFPS_GUARD(kColPad + y0 + 4 <= 8 * HC, 5))
+            *reinterpret_cast<float4*>(colcol + split_idx<KR>(kColPad + y0, HC)) = make_float4(r[0], r[1], r[2], r[3]);
     }
 }
 
@@ -370,7 +380,9 @@ __device__ __forceinline__ void drift_column(const float* __restrict__ ring, int
         float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int a = 0; a < 5; ++a) {
-            const float4 q = *reinterpret_cast<const float4*>(ring + ((slot0 + a) & (R - 1)) * P + RP + y0);
+            const float4 q = VFPS_GUARD(RP + y0 + 4 <= P && slot0 >= 0 && slot0 < R, 3)
+                                 ? *reinterpret_cast<const float4*>(ring + ((slot0 + a) & (R - 1)) * P + RP + y0)
+                                 : make_float4(0.f, 0.f, 0.f, 0.f);
             const float v[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -387,8 +399,9 @@ __device__ __forceinline__ void drift_column(const float* __restrict__ ring, int
                 if (mx <= -2 || mx >= n) acc[k] = 0.f;
             }
         }
-        *reinterpret_cast<float4*>(colcol + split_idx<KR>(kColPad + y0, HC)) =
-            make_float4(acc[0], acc[1], acc[2], acc[3]);
+        if (VFPS_GUARD(kColPad + y0 + 4 <= 8 * HC, 5))
+            *reinterpret_cast<float4*>(colcol + split_idx<KR>(kColPad + y0, HC)) =
+                make_float4(acc[0], acc[1], acc[2], acc[3]);
     }
 }
 
@@ -427,6 +440,10 @@ step_kernel_f32(const Desc<float>* __restrict__ descs, const int2* __restrict__ 
     float* ring = reinterpret_cast<float*>(smem);
     float* colA = ring + R * P;
     float* gtab = colA + W * PA;  // g_0(y) .. g_3(y), n each (split layout for KR = 8)
+#ifdef VFPS_DEBUG
+    if (threadIdx.x == 0) s_dbg_site = 0;
+    __syncthreads();
+#endif
     float* colcol = colA + warp * PA;  // this warp's psi_a column, padded
     float4* kbuf = reinterpret_cast<float4*>(gtab + 4 * n) + 2 * warp;  // stage k: kbuf + 2 W k
     constexpr int rot = ROT;            // 1: Manhattan rotation (every instance of the launch)
@@ -591,6 +608,9 @@ step_kernel_f32(const Desc<float>* __restrict__ descs, const int2* __restrict__ 
     cp_async_wait_0();
     __threadfence();  // this thread's column sums, before the ticket
     __syncthreads();
+#ifdef VFPS_DEBUG
+    if (threadIdx.x == 0 && s_dbg_site) D.st->status = -100 - s_dbg_site;
+#endif
     if (threadIdx.x == 0) {
         const unsigned prev = atomicAdd(&D.st->ticket, 1u);
         s_last = (prev == (unsigned)(D.ntiles - 1));

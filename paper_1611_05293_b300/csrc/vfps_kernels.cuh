@@ -30,6 +30,19 @@
 
 namespace vfps {
 
+// Index checks of the debug build (-DVFPS_DEBUG; the release build compiles
+// them away): VFPS_GUARD(cond, site) is true when cond holds; otherwise it
+// records the site in the CTA's s_dbg_site (first failure wins) and is false,
+// and the caller skips the access.  The step kernel copies a recorded site to
+// the instance's status word as -100 - site, which the host reports as
+// VFPS_EBOUNDS.  A substitute for the memory checker, with no device fault.
+#ifdef VFPS_DEBUG
+__shared__ int s_dbg_site;
+#define VFPS_GUARD(cond, site) ((cond) ? true : (atomicCAS(&::vfps::s_dbg_site, 0, (site)), false))
+#else
+#define VFPS_GUARD(cond, site) true
+#endif
+
 template <typename T> struct C2;
 template <> struct C2<float> { using type = float2; };
 template <> struct C2<double> { using type = double2; };

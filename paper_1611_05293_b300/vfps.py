@@ -16,7 +16,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libvfps.so")
 
-OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENAN, EBUSY = 0, -1, -2, -3, -4, -5, -6
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENAN, EBUSY, EBOUNDS = 0, -1, -2, -3, -4, -5, -6, -7
 IMPEDANCE_NONE, IMPEDANCE_FREE_SPACE, IMPEDANCE_PARALLEL_PLATES, IMPEDANCE_TABLE = 0, 1, 2, 3
 
 # every symbol include/vfps.h declares
