@@ -108,6 +108,7 @@ def lib():
         L.or_normalize.restype = ctypes.c_double
         L.or_step.argtypes = [P, _D, _D, _D, _D, _D, _D, _D, _D]
         L.or_run.argtypes = [P, _D, _D, _D, ctypes.c_longlong, _D, _D]
+        L.or_power_spectrum.argtypes = [_D, ctypes.c_int, _D]
         _lib = L
     return _lib
 
@@ -241,3 +242,12 @@ def run(pr: Params, zre, zim, psi, nsteps: int):
 def impedance(pr: Params, model: int, Pi: float = 0.0):
     """The oracle's impedance table on pr's FFT grid (see oracle.impedance)."""
     return _imp.impedance_table(model, pr.n, pr.half_width, pr.pad_factor, Pi)
+
+
+def power_spectrum(x, L: int) -> np.ndarray:
+    """|DFT|^2 (k = 0..L/2) of the last L values of x, mean removed, Hann window."""
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float64)[-L:])
+    assert x.size == L
+    out = np.zeros(L // 2 + 1)
+    lib().or_power_spectrum(_p(x), int(L), _p(out))
+    return out

@@ -441,3 +441,27 @@ void or_run(const or_params* pr, const double* zre, const double* zim,
     }
     free(work);
 }
+
+/* Power spectrum of a CSR-power series (the rows of the paper's bursting
+ * spectrogram, Sec. IV.C): the last L values x_j of the series, their mean
+ * removed, times the Hann window h_j = (1 - cos(2 pi j/L))/2, and
+ * out[k] = |sum_j h_j (x_j - mean) exp(-2 pi i j k/L)|^2 for k = 0..L/2,
+ * written as the direct sum.  Frequency k is k steps_per_period/L cycles per
+ * synchrotron period. */
+void or_power_spectrum(const double* x, int L, double* out)
+{
+    double mean = 0.0;
+    for (int j = 0; j < L; ++j) mean += x[j];
+    mean /= L;
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k <= L / 2; ++k) {
+        double re = 0.0, im = 0.0;
+        for (int j = 0; j < L; ++j) {
+            double h = 0.5 * (1.0 - cos(2.0 * M_PI * j / L));
+            double a = -2.0 * M_PI * (double)j * (double)k / L;
+            re += h * (x[j] - mean) * cos(a);
+            im += h * (x[j] - mean) * sin(a);
+        }
+        out[k] = re * re + im * im;
+    }
+}

@@ -123,3 +123,20 @@ def test_moments_of_shifted_gaussians():
     psi = W.gaussian(n, 6.0, 0.5, 0.8, 0.5, -0.8)
     m = O.moments(pr4, O.rotate(pr4, psi))
     assert np.max(np.abs(m - np.array([-0.8, 0.8, -0.5, 0.5]))) < 1e-7, m
+
+
+def test_power_spectrum_of_known_signals():
+    """Power spectrum of a P(t) window: a constant has none (mean removed); a
+    cosine on bin m puts (A L/4)^2 on bin m and (A L/8)^2 on each neighbour
+    (the Hann window's three-bin response) and nothing else; two cosines add."""
+    L = 256
+    j = np.arange(L)
+    assert np.max(O.power_spectrum(np.full(L, 3.7), L)) < 1e-20
+    for m, A in ((10, 1.0), (37, 0.25)):
+        s = O.power_spectrum(5.0 + A * np.cos(2 * np.pi * m * j / L), L)
+        ref = np.zeros(L // 2 + 1)
+        ref[m] = (A * L / 4) ** 2
+        ref[m - 1] = ref[m + 1] = (A * L / 8) ** 2
+        assert np.max(np.abs(s - ref)) < 1e-9 * ref.max(), m
+    both = O.power_spectrum(np.cos(2 * np.pi * 10 * j / L) + np.cos(2 * np.pi * 40 * j / L), L)
+    assert abs(both[10] - (L / 4) ** 2) < 1e-9 * (L / 4) ** 2 and abs(both[40] - (L / 4) ** 2) < 1e-9 * (L / 4) ** 2
