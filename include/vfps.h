@@ -120,6 +120,17 @@ int vfps_profile(vfps_handle* h, double* rho_out);
  * partials, FP64 sums.  Synchronises.  Errors: EINVAL, ECUDA, ENAN. */
 int vfps_moments(vfps_handle* h, double* out);
 
+/* out (host, length/2 + 1 doubles): power spectrum of the last `length` values
+ * of the CSR-power series (one row of the paper's bursting spectrogram,
+ * Sec. IV.C), computed on the device: mean removed, Hann window
+ * (1 - cos(2 pi j/length))/2, out[k] = |sum_j ... exp(-2 pi i j k/length)|^2;
+ * bin k is k steps_per_period/length cycles per synchrotron period.  length:
+ * power of two, 16..8192, at most the steps done and at most the ring size
+ * minus one (the series is read from the device ring, so it need not have been
+ * drained).  FP32 transform of FP64-centred values.  Synchronises.  Errors:
+ * EINVAL, ECUDA, ENAN. */
+int vfps_power_spectrum(vfps_handle* h, int32_t length, double* out);
+
 /* Drain the CSR-power series: out[k] = P(psi_t) for the steps t taken since
  * the last drain, oldest first (P of the state each step started from).
  * Writes min(cap, pending) values and *n_written; values beyond cap stay
@@ -225,6 +236,10 @@ int vfps_batch_take(vfps_batch* b, int32_t slot, double* psi_out, double* rho_ou
 /* out (host, 4 doubles): bunch moments of slot's current state, as
  * vfps_moments.  Synchronises the batch.  Errors: EINVAL, ECUDA, ENAN. */
 int vfps_batch_moments(vfps_batch* b, int32_t slot, double* out);
+
+/* out (host, length/2 + 1 doubles): vfps_power_spectrum of a slot.  Errors:
+ * EINVAL, ECUDA, ENAN. */
+int vfps_batch_power_spectrum(vfps_batch* b, int32_t slot, int32_t length, double* out);
 
 /* Autotuner of the batch's FP32 launch groups (on = 1, the default; 0 keeps
  * the built-in rules).  For a group of a configuration not seen before in the

@@ -758,6 +758,8 @@ int init_kernels()
     CU(set_smem_attr_one(step_kernel_f32<8, 8, 1024, 1>, lim));
     CU(set_smem_attr_one(step_kernel_f32<4, 8, 1024, 1>, lim));
     CU(set_smem_attr_one(step_kernel_f32<2, 8, 1024, 1>, lim));
+    CU(cudaFuncSetAttribute(power_spectrum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)(3 * 8192 * sizeof(float2))));
     g_kernels_ready = 1;
     return VFPS_OK;
 }
@@ -871,6 +873,25 @@ int launch_moments_p(Instance& I, cudaStream_t s)
     case 2: return launch_moments_t<T, 2>(I, s);
     }
     return VFPS_EINVAL;
+}
+
+// Power spectrum of the last L CSR-power values of an instance, computed on
+// the device, copied to out (L/2 + 1 doubles).  Synchronises.
+int instance_power_spectrum(Instance& I, cudaStream_t s, int L, double* out)
+{
+    if (!out || L < 16 || L > 8192 || (L & (L - 1)) || L > I.ring - 1 || L > I.steps_queued) return VFPS_EINVAL;
+    double* d = nullptr;
+    CU(cudaMallocAsync((void**)&d, sizeof(double) * (L / 2 + 1), s));
+    const size_t sm = (size_t)3 * L * sizeof(float2);
+    power_spectrum_kernel<<<1, 256, sm, s>>>(I.pring, I.ring - 1, I.steps_queued - L, L, d);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, d, sizeof(double) * (L / 2 + 1), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(d, s);
+    if (e != cudaSuccess) {
+        std::snprintf(g_last_error, sizeof(g_last_error), "power spectrum: %s", cudaGetErrorString(e));
+        return VFPS_ECUDA;
+    }
+    return read_status(I, s);
 }
 
 int instance_moments(Instance& I, cudaStream_t s, double* out)
@@ -1019,6 +1040,12 @@ int vfps_step(vfps_handle* h, int64_t nsteps)
         nsteps -= chunk;
     }
     return VFPS_OK;
+}
+
+int vfps_power_spectrum(vfps_handle* h, int32_t length, double* out)
+{
+    if (!h) return VFPS_EINVAL;
+    return instance_power_spectrum(*h->I, h->stream, length, out);
 }
 
 int vfps_moments(vfps_handle* h, double* out)
@@ -1602,6 +1629,12 @@ int vfps_batch_autotune(vfps_batch* b, int32_t on)
     if (!b || (on != 0 && on != 1)) return VFPS_EINVAL;
     b->autotune = on == 1;
     return VFPS_OK;
+}
+
+int vfps_batch_power_spectrum(vfps_batch* b, int32_t slot, int32_t length, double* out)
+{
+    if (!b || slot < 0 || slot >= b->max_slots || !b->slots[slot]) return VFPS_EINVAL;
+    return instance_power_spectrum(*b->slots[slot], b->stream, length, out);
 }
 
 int vfps_batch_moments(vfps_batch* b, int32_t slot, double* out)

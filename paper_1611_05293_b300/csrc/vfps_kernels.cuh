@@ -760,4 +760,47 @@ __global__ void __launch_bounds__(256) moments_finish_kernel(const Desc<T>* __re
     }
 }
 
+// ----------------------------------------------------------------------------
+// Power spectrum of the last L values of an instance's CSR-power series (a
+// row of the paper's bursting spectrogram, Sec. IV.C): mean removed (FP64),
+// Hann window, L-point complex FFT in FP32 (the Stockham passes of the
+// finaliser), out[k] = |X_k|^2 for k = 0..L/2.  One CTA of 256 threads;
+// shared memory 3 L float2 (two transform buffers and the twiddles
+// exp(-pi i m/L), m < L).  P(psi_t) for t = t0 .. t0+L-1 sits in
+// ring[t & mask].
+__global__ void __launch_bounds__(256)
+power_spectrum_kernel(const double* __restrict__ ring, int mask, long long t0, int L, double* __restrict__ out)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double part[256];
+    float2* A = reinterpret_cast<float2*>(smem);
+    float2* B = A + L;
+    float2* tw = B + L;
+    const int tid = threadIdx.x;
+    double acc = 0.0;
+    for (int j = tid; j < L; j += 256) acc += ring[(t0 + j) & mask];
+    part[tid] = acc;
+    for (int m = tid; m < L; m += 256) {
+        double sn, cs;
+        sincospi(-(double)m / L, &sn, &cs);
+        tw[m] = make_float2((float)cs, (float)sn);
+    }
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (tid < h) part[tid] += part[tid + h];
+        __syncthreads();
+    }
+    const double mean = part[0] / L;
+    for (int j = tid; j < L; j += 256) {
+        const double hann = 0.5 * (1.0 - cospi(2.0 * j / L));
+        A[j] = make_float2((float)(hann * (ring[(t0 + j) & mask] - mean)), 0.f);
+    }
+    __syncthreads();
+    float2* X = fft_h<float, false>(A, B, A, tw, L, [] {});
+    for (int k = tid; k <= L / 2; k += 256) {
+        const float2 v = X[k];
+        out[k] = (double)v.x * v.x + (double)v.y * v.y;
+    }
+}
+
 }  // namespace vfps

@@ -28,7 +28,7 @@ EXPORTS = [
     "vfps_batch_poll", "vfps_batch_take", "vfps_batch_remove", "vfps_batch_usage",
     "vfps_batch_destroy", "vfps_step_static", "vfps_batch_launches_per_step",
     "vfps_moments", "vfps_batch_moments", "vfps_batch_autotune", "vfps_batch_shapes",
-    "vfps_batch_pin_shape",
+    "vfps_batch_pin_shape", "vfps_power_spectrum", "vfps_batch_power_spectrum",
 ]
 
 
@@ -97,6 +97,8 @@ def lib() -> ctypes.CDLL:
         "vfps_step": (ctypes.c_int, [_VP, _I64]),
         "vfps_profile": (ctypes.c_int, [_VP, _D]),
         "vfps_moments": (ctypes.c_int, [_VP, _D]),
+        "vfps_power_spectrum": (ctypes.c_int, [_VP, _I32, _D]),
+        "vfps_batch_power_spectrum": (ctypes.c_int, [_VP, _I32, _I32, _D]),
         "vfps_batch_moments": (ctypes.c_int, [_VP, _I32, _D]),
         "vfps_batch_autotune": (ctypes.c_int, [_VP, _I32]),
         "vfps_batch_pin_shape": (ctypes.c_int, [_VP, _I32, _I32]),
@@ -203,6 +205,12 @@ class Simulation:
     def profile(self) -> np.ndarray:
         out = np.empty(self.params.n)
         _check(lib().vfps_profile(self._h, _dptr(out)), "vfps_profile")
+        return out
+
+    def power_spectrum(self, length: int) -> np.ndarray:
+        """|DFT|^2 of the last `length` CSR-power values (mean removed, Hann), on the device."""
+        out = np.empty(length // 2 + 1)
+        _check(lib().vfps_power_spectrum(self._h, int(length), _dptr(out)), "vfps_power_spectrum")
         return out
 
     def moments(self) -> np.ndarray:
@@ -320,6 +328,13 @@ class Batch:
     def autotune(self, on: bool = True):
         """Enable or disable the per-configuration autotuner (on by default)."""
         _check(lib().vfps_batch_autotune(self._b, 1 if on else 0), "vfps_batch_autotune")
+
+    def power_spectrum(self, slot: int, length: int) -> np.ndarray:
+        """|DFT|^2 of the slot's last `length` CSR-power values, on the device."""
+        out = np.empty(length // 2 + 1)
+        _check(lib().vfps_batch_power_spectrum(self._b, int(slot), int(length), _dptr(out)),
+               "vfps_batch_power_spectrum")
+        return out
 
     def moments(self, slot: int) -> np.ndarray:
         """(<q>, sigma_q, <p>, sigma_p) of a slot's current state, on the device."""

@@ -97,3 +97,27 @@ def test_bursting_statistics_match_oracle(V):
     assert abs(m - m_ref) <= 0.02 * m_ref, (m, m_ref)
     T_ref, T = A.bursting_period(P_ref, spp), A.bursting_period(P, spp)
     assert abs(T - T_ref) <= 0.02 * T_ref, (T, T_ref)
+
+
+def test_power_spectrum_on_device_matches_oracle(V):
+    """The device spectrum of the last L CSR-power values against the
+    oracle's direct DFT of the same series (bursting run, so the spectrum has
+    lines): relative to its peak within 1e-5; the strongest line sits in the
+    same bin; a batch slot gives the same spectrum as its solo run."""
+    n, spp, S, Pi = 64, 500, 1.3, 2.0
+    sim = V.Simulation(V.Params(n=n, steps_per_period=spp, beta=1e-2), None)
+    sim.set_impedance(V.IMPEDANCE_PARALLEL_PLATES, Pi, S)
+    sim.step(6000)
+    P = sim.csr_power()
+    for L in (256, 4096):
+        s = sim.power_spectrum(L)
+        ref = O.power_spectrum(P, L)
+        assert np.max(np.abs(s - ref)) <= 1e-5 * ref.max(), L
+        assert int(np.argmax(s[1:])) == int(np.argmax(ref[1:])), L
+    sim.close()
+    b = V.Batch(1)
+    sl = b.add(V.Params(n=n, steps_per_period=spp, beta=1e-2), None, V.IMPEDANCE_PARALLEL_PLATES, Pi, S, nsteps=6000)
+    b.run(6000)
+    sb = b.power_spectrum(sl, 4096)
+    b.close()
+    assert np.array_equal(sb, s)
