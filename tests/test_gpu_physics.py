@@ -121,3 +121,33 @@ def test_power_spectrum_on_device_matches_oracle(V):
     sb = b.power_spectrum(sl, 4096)
     b.close()
     assert np.array_equal(sb, s)
+
+
+def test_threshold_current_of_iso_anka_near_measured_fingertip(V):
+    """The paper's isomagnetic ANKA-like set (Pi = 1.32, beta = 1/94.3 through
+    the physical-unit front end): a batched scan locates the strong-bursting
+    threshold, whose bunch current is compared with the instability threshold
+    the paper's measured spectrogram shows (fingertip at 0.21 mA, Sec. IV.D):
+    within 25 %.  Measured: S_th = 0.8, 0.20 mA."""
+    from paper_1611_05293_b300 import units as U
+    m = U.iso_anka()
+    d = U.derived(m)
+    n, spp, periods = 128, 500, 120
+    S_grid = np.round(np.arange(0.5, 1.11, 0.1), 2)
+    b = V.Batch(len(S_grid))
+    slots = []
+    for i, S in enumerate(S_grid):
+        op = O.Params(n=n, steps_per_period=spp, beta=d["beta"], s_csr=S)
+        zr, zi = O.impedance(op, 2, d["Pi"])
+        slots.append(b.add(V.Params(n=n, steps_per_period=spp, beta=d["beta"]), start(op, zr, zi, 77 + i),
+                           V.IMPEDANCE_PARALLEL_PLATES, d["Pi"], S, nsteps=spp * periods))
+    b.run(spp * periods)
+    burst = []
+    for sl in slots:
+        P = b.take(sl, psi=False, rho=False)["power"]
+        burst.append(float(np.median(A.fluctuation(P, spp)[-20:])) > 3e-2)
+    b.close()
+    th = A.threshold(S_grid, burst)
+    assert th is not None, burst
+    I_th = U.bunch_current(m, th) * 1e3
+    assert abs(I_th - 0.21) <= 0.25 * 0.21, (th, I_th, burst)
