@@ -261,7 +261,46 @@ def cpu_baseline(n, spp, beta, budget_s=12.0):
     dt = time.perf_counter() - t0
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": n * n * steps / dt, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
-            "sample": f"1 instance N={n} (S={S:.3f}, Pi={Pi:g}), {steps} steps, {dt:.1f} s"}
+            "sample": f"1 instance N={n} (S={S:.3f}, Pi={Pi:g}), {steps} steps, {dt:.1f} s",
+            "cpu_model": cpu_model(), "single_thread": cpu_single_thread(n, spp, beta)}
+
+
+def cpu_model() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def cpu_single_thread(n, spp, beta, budget_s=4.0):
+    """The same oracle sample on one thread (a subprocess with OMP_NUM_THREADS=1)."""
+    import subprocess
+    code = (f"import sys, time; sys.path.insert(0, {ROOT!r}); import bench; "
+            f"print(bench.cpu_baseline_value({n}, {spp}, {beta}, {budget_s}))")
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=120)
+        return {"value": float(out.stdout.strip().splitlines()[-1]), "unit": "cell-updates/s", "cores": 1}
+    except Exception as e:  # the single-thread figure is context only
+        return {"value": None, "error": str(e)[:200]}
+
+
+def cpu_baseline_value(n, spp, beta, budget_s):
+    from oracle import oracle as O
+    from paper_1611_05293_b300 import workloads as W
+    S, Pi = scan_points(1)[0]
+    pr = O.Params(n=n, steps_per_period=spp, beta=beta, s_csr=S)
+    zr, zi = O.impedance(pr, 2, Pi)
+    psi = O.normalize(pr, W.noisy_gaussian(n, 1612, 1e-6))
+    psi, _, _ = O.run(pr, zr, zi, psi, 1)
+    steps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        psi, _, _ = O.run(pr, zr, zi, psi, 2)
+        steps += 2
+    return n * n * steps / (time.perf_counter() - t0)
 
 
 def run_reference(args):
