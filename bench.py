@@ -110,22 +110,35 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-def scan_points(count: int):
+def scan_points(count: int, rank: int = 0, world: int = 1):
+    """(S, Pi) of this rank's `count` instances: ranks take consecutive,
+    disjoint slices of one scan of count * world points (replicas, weak
+    scaling: every rank runs its own simulations, no collective)."""
     from paper_1611_05293_b300 import workloads as W
     base = W.scan_grid()
-    return [base[i % len(base)] for i in range(count)]
+    return [base[i % len(base)] for i in range(rank * count, (rank + 1) * count)]
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """The job's time is the slowest rank's (all_reduce MAX; no-op alone)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 PIN_SHAPE = None  # (W, tiles per strip) from --shape: fixed launch shape instead of the autotuner's
 
 
-def build_batch(V, count, n, spp, beta, stream, seed=1612, rotation=0):
+def build_batch(V, count, n, spp, beta, stream, seed=1612, rotation=0, rank=0, world=1):
     from paper_1611_05293_b300 import workloads as W
     b = V.Batch(count, 0, stream)
     if PIN_SHAPE:
         b.pin_shape(*PIN_SHAPE)
     psi0 = W.noisy_gaussian(n, seed, 1e-6)
-    for S, Pi in scan_points(count):
+    for S, Pi in scan_points(count, rank, world):
         b.add(V.Params(n=n, steps_per_period=spp, beta=beta, rotation=rotation), psi0, V.IMPEDANCE_PARALLEL_PLATES,
               Pi, S, nsteps=1 << 40)
     return b
@@ -377,7 +390,7 @@ def main():
     # ---- batched scan (the headline)
     if not PIN_SHAPE:
         calibrate(V, torch, stream, args.instances, n, spp, beta)
-    b = build_batch(V, args.instances, n, spp, beta, stream)
+    b = build_batch(V, args.instances, n, spp, beta, stream, rank=rank, world=world)
     b.run(args.warmup)
     launches = b.launches_per_step()
     shapes = b.shapes()
@@ -393,11 +406,8 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
-    dt = e0.elapsed_time(e1) / 1e3
+    dt = max_over_ranks(e0.elapsed_time(e1) / 1e3, dist if world > 1 else None, "cuda")
     if world > 1:
-        t = torch.tensor([dt], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dt = float(t.item())
         dist.barrier()
     cells_step = args.instances * n * n
     value = world * cells_step * args.steps / dt
