@@ -200,3 +200,36 @@ def test_autotuner_times_candidates_and_keeps_bits(V):
         b.close()
     for a, c in zip(out[True], out[False]):
         assert np.array_equal(a["psi"], c["psi"]) and np.array_equal(a["power"], c["power"])
+
+
+def test_bench_configuration_sampled_slots_match_oracle(V):
+    """The benchmark's own launch configuration -- 512 instances of N=256 of
+    the parallel-plates scan in one batch, launch shape W=4 with 8-tile strips
+    (the autotuner's choice in the timed run), plus the autotuned shape --
+    against the FP64 oracle, element by element on sampled slots after two
+    steps: relative L-inf <= 1e-5 per step."""
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    n, spp, beta, steps = 256, 1000, 1e-2, 2
+    pts = bench.scan_points(512)
+    psi0 = W.noisy_gaussian(n, 1612, 1e-6)
+    for pin in ((4, 8), None):
+        b = V.Batch(512)
+        if pin:
+            b.pin_shape(*pin)
+        slots = [b.add(V.Params(n=n, steps_per_period=spp, beta=beta), psi0, V.IMPEDANCE_PARALLEL_PLATES, Pi, S,
+                       nsteps=steps) for S, Pi in pts]
+        b.run(steps)
+        if pin:
+            assert all(g["W"] == pin[0] and g["tps"] == pin[1] for g in b.shapes() if g["n"] == n)
+        for i in (0, 137, 511):
+            S, Pi = pts[i]
+            op = O.Params(n=n, steps_per_period=spp, beta=beta, s_csr=S)
+            zr, zi = O.impedance(op, 2, Pi)
+            ref, pref, _ = O.run(op, zr, zi, O.normalize(op, psi0), steps)
+            r = b.take(slots[i])
+            assert np.max(np.abs(r["psi"] - ref)) / ref.max() < 1e-5 * steps, i
+            assert np.max(np.abs(r["power"] - pref) / pref) < 1e-5 * steps, i
+        b.close()
