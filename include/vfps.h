@@ -245,7 +245,7 @@ int vfps_batch_power_spectrum(vfps_batch* b, int32_t slot, int32_t length, doubl
  * the built-in rules).  For a group of a configuration not seen before in the
  * process -- key: n, precision, rotation, steps per period, group size
  * rounded up to a power of two -- the first steps of vfps_batch_run time the
- * candidate CTA widths W in {8, 4, 2} and strip lengths (4..32 tiles), four
+ * candidate CTA widths W in {8, 4, 2} and strip lengths (1..32 tiles), four
  * back-to-back steps each after four warm-up steps, and keep the fastest for
  * the rest of the process (a run shorter than the tuning keeps tuning on its
  * next call).  The timed steps are ordinary steps: every candidate gives the same

@@ -1262,7 +1262,7 @@ std::vector<std::pair<int, int>> tune_candidates(const Group& g)
         const int per_inst = (g.n + W - 1) / W;
         int nt = 0;
         for (const Instance* I : g.members) nt += (I->n + W - 1) / W;
-        for (int t : {4, 8, 16, 32})
+        for (int t : {1, 2, 4, 8, 16, 32})
             if (per_inst % t == 0 && nt / t >= num_sms()) c.push_back({W, t});
         if (c.empty() || c.back().first != W) c.push_back({W, default_tps(g, W)});
     }
