@@ -130,6 +130,7 @@ def max_over_ranks(x: float, dist, device) -> float:
 
 
 PIN_SHAPE = None  # (W, tiles per strip) from --shape: fixed launch shape instead of the autotuner's
+PAIRING = True    # --no-pairing: every simulation in the single-simulation kernel
 
 
 def build_batch(V, count, n, spp, beta, stream, seed=1612, rotation=0, rank=0, world=1):
@@ -137,6 +138,8 @@ def build_batch(V, count, n, spp, beta, stream, seed=1612, rotation=0, rank=0, w
     b = V.Batch(count, 0, stream)
     if PIN_SHAPE:
         b.pin_shape(*PIN_SHAPE)
+    if not PAIRING:
+        b.pairing(False)
     psi0 = W.noisy_gaussian(n, seed, 1e-6)
     for S, Pi in scan_points(count, rank, world):
         b.add(V.Params(n=n, steps_per_period=spp, beta=beta, rotation=rotation), psi0, V.IMPEDANCE_PARALLEL_PLATES,
@@ -364,8 +367,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the serving / C3 / C5 side measurements")
     ap.add_argument("--shape", default="", help="W,tps: fixed batch launch shape (profiling runs)")
+    ap.add_argument("--no-pairing", action="store_true", help="no pair kernel (comparison runs)")
     args = ap.parse_args()
-    global PIN_SHAPE
+    global PIN_SHAPE, PAIRING
+    PAIRING = not args.no_pairing
     if args.shape:
         PIN_SHAPE = tuple(int(v) for v in args.shape.split(","))
     if args.impl == "reference":

@@ -28,6 +28,7 @@
 #include "../../include/vfps.h"
 #include "vfps_kernels.cuh"
 #include "vfps_fast.cuh"
+#include "vfps_pair.cuh"
 
 namespace vfps {
 void impedance_table(int model, int M, double delta, double Pi, std::vector<std::complex<double>>& z);
@@ -172,6 +173,21 @@ size_t fast_smem(const vfps_params* p, int W)
 {
     size_t fin = vfps::finalise_smem(fft_length(p), p->n, W * 32, 8);
     return align_up(std::max(vfps::fast_ring_smem(p->n, halo_for(p), W, p->rotation == 1), fin), 16);
+}
+
+// The pair kernel (vfps_pair.cuh) covers what the FP32 register-blocked
+// kernel covers for the standard rotation, on grids with n a multiple of 32
+// (rows per lane of its copies) and a column halo of at most 12 (its windows
+// then stay inside the kPairRP padding pair-rows of a ring column).
+bool pair_eligible(const vfps_params* p)
+{
+    return fast_eligible(p) && p->rotation == 0 && (p->n % 32) == 0 && halo_for(p) <= 12;
+}
+
+size_t pair_smem(const vfps_params* p, int W)
+{
+    size_t fin = vfps::finalise_smem(fft_length(p), p->n, W * 32, 8);
+    return align_up(std::max(vfps::pair_ring_smem(p->n, halo_for(p), W), fin), 16);
 }
 
 int g_num_sms = 0;
@@ -560,6 +576,7 @@ struct Group {
     int kr = 4;   // FP32 streaming kernel: rows per lane of the kick/FP blocks
     int n = 0;    // grid size shared by the group's instances
     int rot = 0;  // rotation shared by the group's instances (FP32 streaming kernel)
+    int pair = 0; // 1: members 2k, 2k+1 advance together in the pair kernel
     // batches: members, where their descriptors and tiles sit in the batch
     // arrays, and the autotuner's state (candidates (W, tps) still to time)
     std::vector<Instance*> members;
@@ -645,6 +662,22 @@ int launch_fast_k(const Group& g, cudaStream_t s)
     return VFPS_OK;
 }
 
+template <int W, int NC>
+int launch_pair_k(const Group& g, cudaStream_t s)
+{
+    CU(launch_pdl(step_kernel_f32x2<W, NC>, g.ntiles / g.tps, W * 32, g.smem, s, (const Desc<float>*)g.ddescs,
+                  (const int2*)g.dtiles, g.tps));
+    return VFPS_OK;
+}
+
+template <int W>
+int launch_pair_t(const Group& g, cudaStream_t s)
+{
+    if (g.n == 256) return launch_pair_k<W, 256>(g, s);
+    if (g.n == 1024) return launch_pair_k<W, 1024>(g, s);
+    return launch_pair_k<W, 0>(g, s);
+}
+
 // The hot grid sizes (N = 256 scans, N = 1024 single runs) have their own
 // compiled instances with n fixed at compile time.
 template <int W>
@@ -661,6 +694,14 @@ int launch_fast_t(const Group& g, cudaStream_t s)
 int launch_step(const Group& g, cudaStream_t s)
 {
     if (g.ntiles == 0) return VFPS_OK;
+    if (g.pair) {
+        switch (g.W) {
+        case 8: return launch_pair_t<8>(g, s);
+        case 4: return launch_pair_t<4>(g, s);
+        case 2: return launch_pair_t<2>(g, s);
+        }
+        return VFPS_EINVAL;
+    }
     if (g.fast) {
         switch (g.W) {
         case 8: return launch_fast_t<8>(g, s);
@@ -758,6 +799,15 @@ int init_kernels()
     CU(set_smem_attr_one(step_kernel_f32<8, 8, 1024, 1>, lim));
     CU(set_smem_attr_one(step_kernel_f32<4, 8, 1024, 1>, lim));
     CU(set_smem_attr_one(step_kernel_f32<2, 8, 1024, 1>, lim));
+    CU(set_smem_attr_one(step_kernel_f32x2<8, 0>, lim));
+    CU(set_smem_attr_one(step_kernel_f32x2<4, 0>, lim));
+    CU(set_smem_attr_one(step_kernel_f32x2<2, 0>, lim));
+    CU(set_smem_attr_one(step_kernel_f32x2<8, 256>, lim));
+    CU(set_smem_attr_one(step_kernel_f32x2<4, 256>, lim));
+    CU(set_smem_attr_one(step_kernel_f32x2<2, 256>, lim));
+    CU(set_smem_attr_one(step_kernel_f32x2<8, 1024>, lim));
+    CU(set_smem_attr_one(step_kernel_f32x2<4, 1024>, lim));
+    CU(set_smem_attr_one(step_kernel_f32x2<2, 1024>, lim));
     CU(cudaFuncSetAttribute(power_spectrum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)(3 * 8192 * sizeof(float2))));
     g_kernels_ready = 1;
@@ -1166,6 +1216,7 @@ struct vfps_batch {
     std::vector<cudaEvent_t> timers;  // two timing events per pool stream (autotuner)
     std::vector<unsigned char> hbuf;  // host copy of gmem
     bool autotune = true;
+    bool pairing = false;             // vfps_batch_pairing: pair kernel for equal geometries
     int pin_W = 0, pin_tps = 0;       // vfps_batch_pin_shape: fixed shape of FP32 groups
 };
 
@@ -1179,6 +1230,21 @@ void free_groups(vfps_batch* b)
     b->gmem = nullptr;
     b->gbytes = 0;
     b->groups.clear();
+}
+
+// Shared memory of a group member's kernel at CTA width W.
+size_t member_smem(const Group& g, const Instance* I, int W)
+{
+    return g.pair ? pair_smem(&I->p, W) : fast_smem(&I->p, W);
+}
+
+// Tiles (CTA column blocks) of one step of a group at width W: a pair
+// group's tiles cover both simulations of a pair.
+int group_tiles(const Group& g, int W)
+{
+    int nt = 0;
+    for (const Instance* I : g.members) nt += (I->n + W - 1) / W;
+    return g.pair ? nt / 2 : nt;
 }
 
 // Lay out a batch group for CTA width W and strips of tps tiles: its
@@ -1197,11 +1263,13 @@ void layout_group(vfps_batch* b, Group& g, int W, int tps)
         unsigned char* hd = b->hbuf.data() + g.off_d + k * dsz;
         std::memcpy(hd, I->hdesc, dsz);
         const int per_inst = (I->n + W - 1) / W;
-        for (int t = 0; t < per_inst; ++t) ht[nt++] = make_int2((int)k, t * W);
+        // a pair's tiles are listed once, by pair index
+        if (!g.pair || k % 2 == 0)
+            for (int t = 0; t < per_inst; ++t) ht[nt++] = make_int2(g.pair ? (int)k / 2 : (int)k, t * W);
         if (g.prec) ((Desc<double>*)hd)->ntiles = per_inst / tps;
         else ((Desc<float>*)hd)->ntiles = per_inst / tps;
         g.smem = std::max(g.smem, step_smem(&I->p, W));
-        if (g.fast) g.smem = std::max(g.smem, fast_smem(&I->p, W));
+        if (g.fast) g.smem = std::max(g.smem, member_smem(g, I, W));
     }
     g.ntiles = nt;
 }
@@ -1209,8 +1277,7 @@ void layout_group(vfps_batch* b, Group& g, int W, int tps)
 int default_tps(const Group& g, int W)
 {
     const int per_inst = (g.n + W - 1) / W;
-    int nt = 0;
-    for (const Instance* I : g.members) nt += (I->n + W - 1) / W;
+    const int nt = group_tiles(g, W);
     const int target = 2 * num_sms();
     for (int t = per_inst; t >= 1; --t)
         if (per_inst % t == 0 && (t == 1 || nt / t >= target)) return t;
@@ -1247,7 +1314,7 @@ bool pin_fits(const Group& g, int W, int tps)
 {
     const long long lim = device_smem_limit() - 1024;
     for (const Instance* I : g.members)
-        if ((long long)fast_smem(&I->p, W) > lim) return false;
+        if ((long long)member_smem(g, I, W) > lim) return false;
     return tps >= 1 && ((g.n + W - 1) / W) % tps == 0;
 }
 
@@ -1257,11 +1324,10 @@ std::vector<std::pair<int, int>> tune_candidates(const Group& g)
     const long long lim = device_smem_limit() - 1024;
     for (int W : {8, 4, 2}) {
         bool fits = true;
-        for (const Instance* I : g.members) fits = fits && (long long)fast_smem(&I->p, W) <= lim;
+        for (const Instance* I : g.members) fits = fits && (long long)member_smem(g, I, W) <= lim;
         if (!fits) continue;
         const int per_inst = (g.n + W - 1) / W;
-        int nt = 0;
-        for (const Instance* I : g.members) nt += (I->n + W - 1) / W;
+        const int nt = group_tiles(g, W);
         for (int t : {1, 2, 4, 8, 16, 32})
             if (per_inst % t == 0 && nt / t >= num_sms()) c.push_back({W, t});
         if (c.empty() || c.back().first != W) c.push_back({W, default_tps(g, W)});
@@ -1269,27 +1335,77 @@ std::vector<std::pair<int, int>> tune_candidates(const Group& g)
     return c;
 }
 
+// Whether two FP32 simulations advance by the same rotation map and
+// Fokker-Planck weights (grid, halo, angle, damping): they may then share the
+// pair kernel.
+bool same_geometry(const Instance& a, const Instance& b)
+{
+    const Desc<float>& x = *reinterpret_cast<const Desc<float>*>(a.hdesc);
+    const Desc<float>& y = *reinterpret_cast<const Desc<float>*>(b.hdesc);
+    return x.n == y.n && x.ld == y.ld && x.h == y.h && x.rotation == y.rotation &&
+           std::memcmp(&x.cm1, &y.cm1, sizeof(float)) == 0 && std::memcmp(&x.sn, &y.sn, sizeof(float)) == 0 &&
+           std::memcmp(&x.c, &y.c, sizeof(float)) == 0 && std::memcmp(x.ga, y.ga, sizeof(x.ga)) == 0 &&
+           std::memcmp(x.gb, y.gb, sizeof(x.gb)) == 0;
+}
+
+// One launch group to be: its members and kind.
+struct GroupPlan {
+    std::tuple<int, int, int, int> key;  // precision, (N_I, fast, rotation), W, n
+    int pair = 0;
+    std::vector<Instance*> members;
+};
+
 // Group the slots that still have steps to run by (precision, N_I, W, n):
 // one launch per group and step, each group on its own stream so that the
 // groups -- and the two halves of a large group -- overlap, and one group's
 // tail (its last CTAs and their finalisers) hides behind another's work.
 // Grouping by n keeps small grids from running at the occupancy that the
-// largest grid's shared memory would impose.
+// largest grid's shared memory would impose.  Simulations of equal geometry
+// that the pair kernel covers go, two by two, into pair groups; an odd one
+// out joins the single-simulation group of its key.
 int rebuild_groups(vfps_batch* b)
 {
     CU(cudaStreamSynchronize(b->stream));
     free_groups(b);
-    std::map<std::tuple<int, int, int, int, int>, std::vector<Instance*>> cls;
-    std::map<std::tuple<int, int, int, int>, int> count;
+    std::map<std::tuple<int, int, int, int>, std::vector<Instance*>> by_key;
     for (Instance* I : b->slots)
         if (I && remaining(I) > 0)
-            ++count[{I->p.precision, (I->p.interp_points * 2 + I->fast) * 2 + I->p.rotation, I->W, I->n}];
-    std::map<std::tuple<int, int, int, int>, int> seen;
-    for (Instance* I : b->slots) {
-        if (!I || remaining(I) <= 0) continue;
-        auto key = std::make_tuple(I->p.precision, (I->p.interp_points * 2 + I->fast) * 2 + I->p.rotation, I->W, I->n);
-        int half = (count[key] >= 8 && seen[key]++ >= count[key] / 2) ? 1 : 0;
-        cls[{I->p.precision, (I->p.interp_points * 2 + I->fast) * 2 + I->p.rotation, I->W, I->n, half}].push_back(I);
+            by_key[{I->p.precision, (I->p.interp_points * 2 + I->fast) * 2 + I->p.rotation, I->W, I->n}].push_back(I);
+    std::vector<GroupPlan> cls;
+    auto add_halves = [&](const std::tuple<int, int, int, int>& key, int pair, const std::vector<Instance*>& m) {
+        // large groups in two halves (a pair group splits between pairs)
+        const size_t unit = pair ? 2 : 1, units = m.size() / unit;
+        const size_t cut = units >= 8 / unit ? unit * ((units + 1) / 2) : m.size();
+        GroupPlan a{key, pair, std::vector<Instance*>(m.begin(), m.begin() + cut)};
+        cls.push_back(a);
+        if (cut < m.size()) cls.push_back(GroupPlan{key, pair, std::vector<Instance*>(m.begin() + cut, m.end())});
+    };
+    for (auto& kv : by_key) {
+        std::vector<Instance*> single;
+        std::vector<std::vector<Instance*>> sigs;
+        for (Instance* I : kv.second) {
+            if (!(b->pairing && I->fast && pair_eligible(&I->p) &&
+                  (long long)pair_smem(&I->p, 2) <= device_smem_limit() - 1024)) {
+                single.push_back(I);
+                continue;
+            }
+            bool placed = false;
+            for (auto& sg : sigs)
+                if (same_geometry(*sg[0], *I)) {
+                    sg.push_back(I);
+                    placed = true;
+                    break;
+                }
+            if (!placed) sigs.push_back({I});
+        }
+        for (auto& sg : sigs) {
+            if (sg.size() % 2) {
+                single.push_back(sg.back());
+                sg.pop_back();
+            }
+            if (!sg.empty()) add_halves(kv.first, 1, sg);
+        }
+        if (!single.empty()) add_halves(kv.first, 0, single);
     }
     if (cls.empty()) {
         b->dirty = false;
@@ -1318,9 +1434,9 @@ int rebuild_groups(vfps_batch* b)
     std::vector<std::pair<size_t, size_t>> offs;
     for (auto& kv : cls) {
         size_t nt = 0;
-        for (Instance* I : kv.second) nt += (size_t)(I->n + 1) / 2;
+        for (Instance* I : kv.members) nt += (size_t)(I->n + 1) / 2;
         size_t od = align_up(total, kAlign);
-        size_t ot = align_up(od + kv.second.size() * sizeof(Desc<double>), kAlign);
+        size_t ot = align_up(od + kv.members.size() * sizeof(Desc<double>), kAlign);
         total = ot + nt * sizeof(int2);
         offs.push_back({od, ot});
     }
@@ -1333,21 +1449,34 @@ int rebuild_groups(vfps_batch* b)
     size_t gi = 0;
     for (auto& kv : cls) {
         Group g;
-        g.prec = std::get<0>(kv.first);
-        g.ni = std::get<1>(kv.first) / 4;
-        g.fast = (std::get<1>(kv.first) >> 1) & 1;
+        g.prec = std::get<0>(kv.key);
+        g.ni = std::get<1>(kv.key) / 4;
+        g.fast = (std::get<1>(kv.key) >> 1) & 1;
+        g.pair = kv.pair;
         g.stream = b->pool[gi];
         g.t0 = b->timers[2 * gi];
         g.t1 = b->timers[2 * gi + 1];
-        g.members = kv.second;
+        g.members = kv.members;
         g.off_d = offs[gi].first;
         g.off_t = offs[gi].second;
         g.ddescs = (unsigned char*)b->gmem + g.off_d;
         g.dtiles = (int2*)((unsigned char*)b->gmem + g.off_t);
-        g.kr = fast_kr(kv.second[0]->p.n);  // a group shares n
-        g.n = kv.second[0]->p.n;
-        g.rot = kv.second[0]->p.rotation;
-        int W = std::get<2>(kv.first), tps = 1;
+        g.kr = fast_kr(kv.members[0]->p.n);  // a group shares n
+        g.n = kv.members[0]->p.n;
+        g.rot = kv.members[0]->p.rotation;
+        int W = std::get<2>(kv.key), tps = 1;
+        if (g.pair) {
+            // the widest width whose pair-kernel shared memory fits
+            const long long lim = device_smem_limit() - 1024;
+            for (int w : {8, 4, 2}) {
+                bool fits = true;
+                for (const Instance* I : g.members) fits = fits && (long long)pair_smem(&I->p, w) <= lim;
+                if (fits) {
+                    W = w;
+                    break;
+                }
+            }
+        }
         if (g.fast) {
             // a strip of tps consecutive tiles per CTA: the largest divisor of
             // the tiles per instance that still leaves two CTAs per SM (long
@@ -1355,11 +1484,11 @@ int rebuild_groups(vfps_batch* b)
             // cells; measured on 512 x N=256: 4 tiles 161 us, 8 152, 16 148);
             // the autotuner replaces this choice once it has timed the group
             tps = default_tps(g, W);
-            const Instance* I0 = kv.second[0];
-            const int cnt = (int)kv.second.size();
+            const Instance* I0 = kv.members[0];
+            const int cnt = (int)kv.members.size();
             int bucket = 1;
             while (bucket < cnt) bucket <<= 1;
-            g.tune_key = std::make_tuple(I0->n, g.prec, g.rot, I0->p.steps_per_period, bucket, I0->W);
+            g.tune_key = std::make_tuple(I0->n, g.prec, g.rot + 2 * g.pair, I0->p.steps_per_period, bucket, I0->W);
             std::pair<int, int> best;
             if (b->pin_W && pin_fits(g, b->pin_W, b->pin_tps)) {
                 W = b->pin_W;
@@ -1602,15 +1731,24 @@ int vfps_batch_shapes(vfps_batch* b, int32_t* out, int32_t cap, int32_t* n_group
     int k = 0;
     for (const Group& g : b->groups) {
         if (k < cap) {
-            out[5 * k] = g.n;
-            out[5 * k + 1] = (int32_t)g.members.size();
-            out[5 * k + 2] = g.W;
-            out[5 * k + 3] = g.tps;
-            out[5 * k + 4] = g.cands.empty() ? 1 : 0;
+            out[6 * k] = g.n;
+            out[6 * k + 1] = (int32_t)g.members.size();
+            out[6 * k + 2] = g.W;
+            out[6 * k + 3] = g.tps;
+            out[6 * k + 4] = g.cands.empty() ? 1 : 0;
+            out[6 * k + 5] = g.pair;
         }
         ++k;
     }
     *n_groups = std::min(k, cap);
+    return VFPS_OK;
+}
+
+int vfps_batch_pairing(vfps_batch* b, int32_t on)
+{
+    if (!b || (on != 0 && on != 1)) return VFPS_EINVAL;
+    b->pairing = on != 0;
+    b->dirty = true;
     return VFPS_OK;
 }
 

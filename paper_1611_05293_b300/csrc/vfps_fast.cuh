@@ -63,19 +63,37 @@ __device__ __forceinline__ int split_idx(int e, int half_chunks)
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
-// Cubic Lagrange weights (nodes -1, 0, 1, 2) for two fractions at once,
-// each weight as a product of two factors that are one FMA from t:
-//   w0 = t(t-1) (2-t)/6,  w1 = (t^2-1) (t-2)/2,  w2 = t(t+1) (2-t)/2,
-//   w3 = t(t-1) (t+1)/6.
+// Cubic Lagrange weights (nodes -1, 0, 1, 2) for two fractions at once.
+// With m = t(1 - t) and k = 1 + m/2 the four cardinal polynomials are
+//   w2 = t k,  w1 = (1 - t) k = k - w2,  w0 = m (t - 2)/6,  w3 = -m/2 - w0
+// (w0 + w3 = -m/2 and w1 + w2 = k, so they sum to 1): seven operations.
+// Each half of a pair is computed exactly as the scalar expression would be,
+// so a broadcast pair (t, t) gives the weights of t in both halves.
 __device__ __forceinline__ void lagrange2(float2 t, float2 w[4])
 {
-    const float2 p = __ffma2_rn(t, t, f2(-t.x, -t.y));                    // t(t-1)
-    const float2 r = __ffma2_rn(t, t, f2(-1.f, -1.f));                    // t^2-1
-    const float2 q = __ffma2_rn(t, t, t);                                  // t(t+1)
-    w[0] = __fmul2_rn(p, __ffma2_rn(t, f2(-1.f / 6.f, -1.f / 6.f), f2(1.f / 3.f, 1.f / 3.f)));
-    w[1] = __fmul2_rn(r, __ffma2_rn(t, f2(0.5f, 0.5f), f2(-1.f, -1.f)));
-    w[2] = __fmul2_rn(q, __ffma2_rn(t, f2(-0.5f, -0.5f), f2(1.f, 1.f)));
-    w[3] = __fmul2_rn(p, __ffma2_rn(t, f2(1.f / 6.f, 1.f / 6.f), f2(1.f / 6.f, 1.f / 6.f)));
+    const float2 m = __ffma2_rn(f2(-t.x, -t.y), t, t);                           // t - t^2
+    const float2 k = __ffma2_rn(m, f2(0.5f, 0.5f), f2(1.f, 1.f));                // 1 + m/2
+    w[2] = __fmul2_rn(t, k);
+    w[1] = __fadd2_rn(k, f2(-w[2].x, -w[2].y));
+    w[0] = __fmul2_rn(m, __ffma2_rn(t, f2(1.f / 6.f, 1.f / 6.f), f2(-1.f / 3.f, -1.f / 3.f)));
+    w[3] = __ffma2_rn(m, f2(-0.5f, -0.5f), f2(-w[0].x, -w[0].y));
+}
+
+// Fokker-Planck weight g_k(y) of tap k (rows y-1 .. y+2) with the identity
+// folded into the centre tap, in one fixed order of operations (the FP32
+// kernels all build their tables with it).
+__device__ __forceinline__ float fp_weight(const Desc<float>& D, int k, int y)
+{
+    return (k == 1 ? 1.f : 0.f) + fmaf(D.gb[k], float(y), D.ga[k]);
+}
+
+// psi_c(y) = sum_k g_k(y) psi_b(y - 1 + k), in one fixed order.
+__device__ __forceinline__ float fp_apply(float g0, float g1, float g2, float g3, const float* b)
+{
+    float v = g0 * b[0];
+    v = fmaf(g1, b[1], v);
+    v = fmaf(g2, b[2], v);
+    return fmaf(g3, b[3], v);
 }
 
 // Rotation of four rows from a 5 x 12 register window: 5 consecutive slab
@@ -222,10 +240,7 @@ __device__ __forceinline__ float kick_fp_column(const float* __restrict__ colcol
             const float gc[4] = {g2.x, g2.y, g2.z, g2.w}, gd[4] = {g3.x, g3.y, g3.z, g3.w};
             float c[4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const float* bb = b + 4 * q4 + k;
-                c[k] = ga[k] * bb[0] + gb[k] * bb[1] + gc[k] * bb[2] + gd[k] * bb[3];
-            }
+            for (int k = 0; k < 4; ++k) c[k] = fp_apply(ga[k], gb[k], gc[k], gd[k], b + 4 * q4 + k);
             *reinterpret_cast<float4*>(dst + y) = make_float4(c[0], c[1], c[2], c[3]);
             lsum += (c[0] + c[1]) + (c[2] + c[3]);
         }
@@ -234,28 +249,40 @@ __device__ __forceinline__ float kick_fp_column(const float* __restrict__ colcol
     return lsum;
 }
 
-// Rotation of one cell from the column ring (general path; same arithmetic
-// as rotate_cell, with slab column col stored in ring slot col & (R-1)).
+// Source node (mx, my) and cubic weights of cell (x, y) of the rotation, in
+// one fixed order of operations; false when the source lies more than one
+// cell outside the grid (the cell is then 0).
+__device__ __forceinline__ bool cell_weights(int x, int y, int n, float cm1, float sn, float c, int* mx, int* my,
+                                             float wx[4], float wy[4])
+{
+    const float xc = float(x) - c, yc = float(y) - c;
+    const float dx = fmaf(-sn, yc, cm1 * xc);
+    const float dy = fmaf(cm1, yc, sn * xc);
+    const float fx = floorf(dx), fy = floorf(dy);
+    *mx = x + int(fx);
+    *my = y + int(fy);
+    if (*mx <= -2 || *mx >= n || *my <= -2 || *my >= n) return false;
+    lagrange_w<float, 4>(dx - fx, wx);
+    lagrange_w<float, 4>(dy - fy, wy);
+    return true;
+}
+
+// Rotation of one cell from the column ring (general path), with slab
+// column col stored in ring slot col & (R-1).
 __device__ __forceinline__ float rotate_cell_ring(const float* __restrict__ ring, int R, int P, int RP, int x, int y,
                                                   int n, float cm1, float sn, float c)
 {
-    const float xc = float(x) - c, yc = float(y) - c;
-    const float dx = cm1 * xc - sn * yc;
-    const float dy = sn * xc + cm1 * yc;
-    const float fx = floorf(dx), fy = floorf(dy);
-    const int mx = x + int(fx), my = y + int(fy);
-    if (mx <= -2 || mx >= n || my <= -2 || my >= n) return 0.f;
+    int mx, my;
     float wx[4], wy[4];
-    lagrange_w<float, 4>(dx - fx, wx);
-    lagrange_w<float, 4>(dy - fy, wy);
+    if (!cell_weights(x, y, n, cm1, sn, c, &mx, &my, wx, wy)) return 0.f;
     float acc = 0.f;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
         const float* col = ring + ((mx - 1 + a) & (R - 1)) * P + (my - 1 + RP);
         float r = 0.f;
 #pragma unroll
-        for (int b = 0; b < 4; ++b) r += wy[b] * col[b];
-        acc += wx[a] * r;
+        for (int b = 0; b < 4; ++b) r = fmaf(wy[b], col[b], r);
+        acc = fmaf(wx[a], r, acc);
     }
     return acc;
 }
@@ -462,10 +489,9 @@ step_kernel_f32(const Desc<float>* __restrict__ descs, const int2* __restrict__ 
     if (rot)
         for (int r = lane; r < PA - n; r += 32) colbcol[split_idx<KR>(r < kColPad ? r : n + r, HC)] = 0.f;
     for (int y = threadIdx.x; y < n; y += blockDim.x) {
-        const float yf = float(y);
         const int gi = split_idx<KR>(y, n >> 3);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) gtab[k * n + gi] = (k == 1 ? 1.f : 0.f) + (D.ga[k] + D.gb[k] * yf);
+        for (int k = 0; k < 4; ++k) gtab[k * n + gi] = fp_weight(D, k, y);
     }
     // what the previous step wrote (state word, psi, kick table) is read from here on
     pdl_wait();
@@ -493,8 +519,8 @@ step_kernel_f32(const Desc<float>* __restrict__ descs, const int2* __restrict__ 
             const float xc = float(x) - c;
             // dy is linear along the column: floor(dy) is the same on every row
             // iff it is at the first and the last row
-            const float fy_top = floorf(sn * xc + cm1 * (0.f - c));
-            const float fy_bot = floorf(sn * xc + cm1 * (float(n - 1) - c));
+            const float fy_top = floorf(fmaf(cm1, 0.f - c, sn * xc));
+            const float fy_bot = floorf(fmaf(cm1, float(n - 1) - c, sn * xc));
             if (fy_top == fy_bot && sn < 0.3f) {
                 const int FY = int(fy_top);
                 const int A = FY - 1 + RP;
@@ -581,14 +607,13 @@ step_kernel_f32(const Desc<float>* __restrict__ descs, const int2* __restrict__ 
 #pragma unroll
                             for (int k = 0; k < 4; ++k) {
                                 const int rr = mm - 1 + k;
-                                if (rr >= 0 && rr < n) v += w[k] * kcol[split_idx<KR>(kColPad + rr, HC)];
+                                if (rr >= 0 && rr < n) v = fmaf(w[k], kcol[split_idx<KR>(kColPad + rr, HC)], v);
                             }
                         }
                         b[d] = v;
                     }
                     const int gi = split_idx<KR>(y, n >> 3);
-                    const float v = gtab[gi] * b[0] + gtab[n + gi] * b[1] + gtab[2 * n + gi] * b[2] +
-                                    gtab[3 * n + gi] * b[3];
+                    const float v = fp_apply(gtab[gi], gtab[n + gi], gtab[2 * n + gi], gtab[3 * n + gi], b);
                     dst[y] = v;
                     lsum += v;
                 }

@@ -28,7 +28,7 @@ EXPORTS = [
     "vfps_batch_poll", "vfps_batch_take", "vfps_batch_remove", "vfps_batch_usage",
     "vfps_batch_destroy", "vfps_step_static", "vfps_batch_launches_per_step",
     "vfps_moments", "vfps_batch_moments", "vfps_batch_autotune", "vfps_batch_shapes",
-    "vfps_batch_pin_shape", "vfps_power_spectrum", "vfps_batch_power_spectrum",
+    "vfps_batch_pin_shape", "vfps_power_spectrum", "vfps_batch_power_spectrum", "vfps_batch_pairing",
 ]
 
 
@@ -102,6 +102,7 @@ def lib() -> ctypes.CDLL:
         "vfps_batch_moments": (ctypes.c_int, [_VP, _I32, _D]),
         "vfps_batch_autotune": (ctypes.c_int, [_VP, _I32]),
         "vfps_batch_pin_shape": (ctypes.c_int, [_VP, _I32, _I32]),
+        "vfps_batch_pairing": (ctypes.c_int, [_VP, _I32]),
         "vfps_batch_shapes": (ctypes.c_int, [_VP, ctypes.POINTER(_I32), _I32, ctypes.POINTER(_I32)]),
         "vfps_csr_power": (ctypes.c_int, [_VP, _D, _I64, ctypes.POINTER(_I64)]),
         "vfps_charge_series": (ctypes.c_int, [_VP, _D, _I64, ctypes.POINTER(_I64)]),
@@ -313,13 +314,17 @@ class Batch:
         return [out[i] for i in range(k.value)]
 
     def shapes(self) -> list:
-        """Launch groups: dicts with n, instances, W, tiles per strip, final."""
+        """Launch groups: dicts with n, instances, W, tiles per strip, final, paired."""
         cap = 64
-        out = (_I32 * (5 * cap))()
+        out = (_I32 * (6 * cap))()
         k = _I32()
         _check(lib().vfps_batch_shapes(self._b, out, cap, ctypes.byref(k)), "vfps_batch_shapes")
-        return [dict(n=out[5 * i], instances=out[5 * i + 1], W=out[5 * i + 2], tps=out[5 * i + 3],
-                     final=bool(out[5 * i + 4])) for i in range(k.value)]
+        return [dict(n=out[6 * i], instances=out[6 * i + 1], W=out[6 * i + 2], tps=out[6 * i + 3],
+                     final=bool(out[6 * i + 4]), paired=bool(out[6 * i + 5])) for i in range(k.value)]
+
+    def pairing(self, on: bool = True):
+        """Run FP32 simulations of equal geometry two at a time (off by default)."""
+        _check(lib().vfps_batch_pairing(self._b, 1 if on else 0), "vfps_batch_pairing")
 
     def pin_shape(self, W: int = 0, tps: int = 0):
         """Fix the CTA width and strip length of the FP32 groups (0, 0 releases)."""

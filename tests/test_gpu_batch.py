@@ -233,3 +233,32 @@ def test_bench_configuration_sampled_slots_match_oracle(V):
             assert np.max(np.abs(r["psi"] - ref)) / ref.max() < 1e-5 * steps, i
             assert np.max(np.abs(r["power"] - pref) / pref) < 1e-5 * steps, i
         b.close()
+
+
+def test_pairing_keeps_bits(V):
+    """Simulations of equal geometry run two at a time in the pair kernel
+    (packed FP32x2); every slot gives the same bits with pairing on and off.
+    The mix has an odd one out, two geometries, strong kicks (shifts beyond 4
+    cells and shifts that differ by more than one between partners) and
+    columns whose y-node is not uniform (per-cell rotation path)."""
+    mix = [(64, 100, 12.0, 1.0), (64, 100, 0.9, 2.0), (64, 100, 30.0, 0.5), (64, 100, 0.3, 3.0),
+           (64, 100, 2.0, 1.0), (96, 500, 0.9, 2.0), (96, 500, 1.4, 1.0), (256, 1000, 0.8, 2.0),
+           (256, 1000, 1.2, 3.0)]
+    ns = 6
+    out = {}
+    for on in (True, False):
+        b = V.Batch(len(mix))
+        b.pairing(on)
+        slots = [b.add(V.Params(n=n, steps_per_period=spp, beta=1e-2), W.blobs(n, 300 + i),
+                       V.IMPEDANCE_PARALLEL_PLATES, Pi, S, nsteps=ns) for i, (n, spp, S, Pi) in enumerate(mix)]
+        b.run(1)
+        sh = b.shapes()
+        paired = sum(g["instances"] for g in sh if g["paired"])
+        assert paired == (8 if on else 0), sh
+        b.run(ns - 1)
+        out[on] = [b.take(s) for s in slots]
+        b.close()
+    for i, (a, c) in enumerate(zip(out[True], out[False])):
+        assert np.all(np.isfinite(a["psi"])), i
+        assert np.array_equal(a["psi"], c["psi"]), i
+        assert np.array_equal(a["power"], c["power"]), i

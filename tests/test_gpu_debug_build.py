@@ -1,8 +1,9 @@
 """The debug build (VFPS_DEBUG: shared-memory index checks that record the
 failing site and skip the access, reported as EBOUNDS; no device fault)
 against the release build: over grid sizes (ragged, fast and general
-kernels, the compiled-in sizes 256 and 1024), both rotations and pinned
-launch shapes, no check fires and both builds give the same bits."""
+kernels, the compiled-in sizes 256 and 1024), both rotations, pinned
+launch shapes and the pair kernel, no check fires and both builds give the
+same bits."""
 import os
 import subprocess
 import sys
@@ -26,12 +27,13 @@ SCRIPT = textwrap.dedent("""
             sim = V.Simulation(p, W.blobs(n, n + rot)); sim.set_impedance(2, 2.0, 0.9); sim.step(3)
             out[f"solo_{n}_{rot}"] = sim.get_state(); sim.close()
             for Wd, tps in ((2, 1), (4, 4), (8, 1), (8, 4)):
-                b = V.Batch(2); b.autotune(False); b.pin_shape(Wd, tps)
-                s = [b.add(p, W.blobs(n, 7 * i + n), 2, 2.0, 0.7 + 0.2 * i, nsteps=3) for i in range(2)]
-                b.run(3)
-                for i, sl in enumerate(s):
-                    out[f"b_{n}_{rot}_{Wd}_{tps}_{i}"] = b.take(sl)["psi"]
-                b.close()
+                for pair in (False, True):
+                    b = V.Batch(2); b.autotune(False); b.pin_shape(Wd, tps); b.pairing(pair)
+                    s = [b.add(p, W.blobs(n, 7 * i + n), 2, 2.0, 0.7 + 0.2 * i, nsteps=3) for i in range(2)]
+                    b.run(3)
+                    for i, sl in enumerate(s):
+                        out[f"b_{n}_{rot}_{Wd}_{tps}_{int(pair)}_{i}"] = b.take(sl)["psi"]
+                    b.close()
     np.savez(%(path)r, **out)
     print("OK")
 """)
