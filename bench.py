@@ -44,7 +44,7 @@ HBM_FALLBACK_GBS = 6400.0
 # autotuner's choice; W=8 with 16-tile strips measured 96.1 MB); a step of the
 # 512-instance benchmark is two such launches.  Set to None whenever the kernel
 # changes until a new capture is taken.
-MEASURED_TRAFFIC_PER_LAUNCH = 95.9e6
+MEASURED_TRAFFIC_PER_LAUNCH = 96.3e6
 
 
 def measured_peaks():
@@ -130,7 +130,7 @@ def max_over_ranks(x: float, dist, device) -> float:
 
 
 PIN_SHAPE = None  # (W, tiles per strip) from --shape: fixed launch shape instead of the autotuner's
-PAIRING = True    # --no-pairing: every simulation in the single-simulation kernel
+PAIRING = False   # --pairing: simulations of one geometry two at a time (pair kernel)
 
 
 def build_batch(V, count, n, spp, beta, stream, seed=1612, rotation=0, rank=0, world=1):
@@ -138,8 +138,7 @@ def build_batch(V, count, n, spp, beta, stream, seed=1612, rotation=0, rank=0, w
     b = V.Batch(count, 0, stream)
     if PIN_SHAPE:
         b.pin_shape(*PIN_SHAPE)
-    if not PAIRING:
-        b.pairing(False)
+    b.pairing(PAIRING)
     psi0 = W.noisy_gaussian(n, seed, 1e-6)
     for S, Pi in scan_points(count, rank, world):
         b.add(V.Params(n=n, steps_per_period=spp, beta=beta, rotation=rotation), psi0, V.IMPEDANCE_PARALLEL_PLATES,
@@ -367,10 +366,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the serving / C3 / C5 side measurements")
     ap.add_argument("--shape", default="", help="W,tps: fixed batch launch shape (profiling runs)")
-    ap.add_argument("--no-pairing", action="store_true", help="no pair kernel (comparison runs)")
+    ap.add_argument("--pairing", action="store_true", help="pair kernel for simulations of one geometry")
     args = ap.parse_args()
     global PIN_SHAPE, PAIRING
-    PAIRING = not args.no_pairing
+    PAIRING = args.pairing
     if args.shape:
         PIN_SHAPE = tuple(int(v) for v in args.shape.split(","))
     if args.impl == "reference":

@@ -243,18 +243,21 @@ int vfps_batch_power_spectrum(vfps_batch* b, int32_t slot, int32_t length, doubl
 
 /* Autotuner of the batch's FP32 launch groups (on = 1, the default; 0 keeps
  * the built-in rules).  For a group of a configuration not seen before in the
- * process -- key: n, precision, rotation, steps per period, group size
- * rounded up to a power of two -- the first steps of vfps_batch_run time the
- * candidate CTA widths W in {8, 4, 2} and strip lengths (1..32 tiles), four
- * back-to-back steps each after four warm-up steps, and keep the fastest for
- * the rest of the process (a run shorter than the tuning keeps tuning on its
- * next call).  The timed steps are ordinary steps: every candidate gives the same
- * bits.  Setting VFPS_AUTOTUNE=0 in the environment disables it everywhere.
+ * process -- key: n, precision, rotation, pairing, steps per period, group
+ * size rounded up to a power of two -- the first steps of vfps_batch_run time
+ * the candidate CTA widths W in {8, 4, 2} with strip lengths (1..32 tiles per
+ * CTA) and with the balanced grid (one resident wave of CTAs, each taking an
+ * equal run of the group's tiles), four back-to-back steps each after four
+ * warm-up steps, and keep the fastest for the rest of the process (a run
+ * shorter than the tuning keeps tuning on its next call).  The timed steps
+ * are ordinary steps: every candidate gives the same bits.  Setting
+ * VFPS_AUTOTUNE=0 in the environment disables it everywhere.
  * Errors: EINVAL. */
 int vfps_batch_autotune(vfps_batch* b, int32_t on);
 
 /* Current launch groups of the batch: for each group, six int32 in out --
- * grid size n, instances, CTA width W, tiles per CTA strip, 1 if its shape is
+ * grid size n, instances, CTA width W, tiles per CTA strip (-1: balanced
+ * grid), 1 if its shape is
  * final (tuned or fixed) or 0 while the autotuner is still timing it, 1 if
  * its CTAs advance pairs of simulations (see vfps_batch_pairing).  At most
  * cap groups; *n_groups gets the number written.  Errors: EINVAL, ENOMEM,
@@ -274,10 +277,10 @@ int vfps_batch_shapes(vfps_batch* b, int32_t* out, int32_t cap, int32_t* n_group
 int vfps_batch_pairing(vfps_batch* b, int32_t on);
 
 /* Fix the launch shape of the batch's FP32 groups: CTA width W (2, 4 or 8)
- * and tps tiles per CTA strip, instead of the autotuner's or the built-in
- * choice, for groups where it fits (shared memory, tps dividing the tiles per
- * instance); W = tps = 0 releases it.  Results do not depend on the shape.
- * Errors: EINVAL. */
+ * and tps tiles per CTA strip (1..256), or tps = -1 for the balanced grid,
+ * instead of the autotuner's or the built-in choice, for groups where it fits
+ * (shared memory, tps dividing the tiles per instance); W = tps = 0 releases
+ * it.  Results do not depend on the shape.  Errors: EINVAL. */
 int vfps_batch_pin_shape(vfps_batch* b, int32_t W, int32_t tps);
 
 /* Free a slot (its memory returns to the budget). */

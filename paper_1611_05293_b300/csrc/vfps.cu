@@ -279,6 +279,7 @@ struct Instance {
     unsigned char hdesc[sizeof(Desc<double>)];  // host copy of the descriptor
     void* ddesc = nullptr;                       // device copy
     int2* dtiles = nullptr;                      // this instance alone: its tiles
+    int4* dsegs = nullptr;                       // ... and one FP32-kernel segment per tile
     // host bookkeeping
     long long steps_queued = 0;   // steps launched so far
     long long drained = 0;        // ring entries already moved to the host
@@ -314,6 +315,7 @@ size_t instance_bytes(const vfps_params* p, int ring, size_t* offs)
     take(11, sizeof(int2) * (size_t)((n + 1) / 2 + 1));  // tiles (W >= 2)
     take(12, (size_t)n * 32);            // kick table (FP32 path)
     take(13, (size_t)(3 * n + 4) * 8);   // moments scratch
+    take(14, sizeof(int4) * (size_t)((n + 1) / 2 + 1));  // FP32-kernel segments (W >= 2)
     return align_up(o, kAlign);
 }
 
@@ -506,7 +508,7 @@ int create_instance(const vfps_params* p, const double* psi0, int ring, cudaStre
     I->ring = ring;
     I->delta = 2.0 * p->half_width / (p->n - 1);
     I->phi = 2.0 * kPi / p->steps_per_period;
-    size_t offs[14];
+    size_t offs[15];
     I->dbytes = instance_bytes(p, ring, offs);
     if (dev_alloc(&I->dmem, I->dbytes) != cudaSuccess) {
         cudaGetLastError();
@@ -528,6 +530,7 @@ int create_instance(const vfps_params* p, const double* psi0, int ring, cudaStre
     I->dtiles = (int2*)(b + offs[11]);
     I->kickw = b + offs[12];
     I->mom = (double*)(b + offs[13]);
+    I->dsegs = (int4*)(b + offs[14]);
     // twiddles exp(-2 pi i k/M), FP64 on the host
     {
         int K = I->M / 2;
@@ -550,9 +553,15 @@ int create_instance(const vfps_params* p, const double* psi0, int ring, cudaStre
     }
     {
         std::vector<int2> t(I->ntiles);
-        for (int i = 0; i < I->ntiles; ++i) t[i] = make_int2(0, i * W);
+        std::vector<int4> sg(I->ntiles);
+        for (int i = 0; i < I->ntiles; ++i) {
+            t[i] = make_int2(0, i * W);
+            sg[i] = make_int4(0, i * W, 1, 0);
+        }
         if (cudaMemcpyAsync(I->dtiles, t.data(), sizeof(int2) * t.size(), cudaMemcpyHostToDevice, s) !=
-            cudaSuccess)
+                cudaSuccess ||
+            cudaMemcpyAsync(I->dsegs, sg.data(), sizeof(int4) * sg.size(), cudaMemcpyHostToDevice, s) !=
+                cudaSuccess)
             return VFPS_ECUDA;
         DevState st{};
         st.scale = 1.0;
@@ -590,6 +599,11 @@ struct Group {
     int ntiles = 0;
     void* ddescs = nullptr;  // array of Desc<T>
     int2* dtiles = nullptr;
+    int4* dsegs = nullptr;   // FP32 kernels: spc segments per CTA, grid CTAs
+    int spc = 1, grid = 0;
+    size_t seg_cap = 0;      // batch groups: room for segments (entries)
+    size_t tab_bytes = 0;    // batch groups: bytes of descriptors + tile/segment table
+    double share = 1.0;      // batch groups: fraction of the batch's FP32 cells in this group
     cudaStream_t stream = nullptr;  // batch groups: their own (forked) stream
 };
 
@@ -654,19 +668,19 @@ template <int W, int KR, int NC>
 int launch_fast_k(const Group& g, cudaStream_t s)
 {
     if (g.rot)
-        CU(launch_pdl(step_kernel_f32<W, KR, NC, 1>, g.ntiles / g.tps, W * 32, g.smem, s,
-                      (const Desc<float>*)g.ddescs, (const int2*)g.dtiles, g.tps));
+        CU(launch_pdl(step_kernel_f32<W, KR, NC, 1>, g.grid, W * 32, g.smem, s, (const Desc<float>*)g.ddescs,
+                      (const int4*)g.dsegs, g.spc));
     else
-        CU(launch_pdl(step_kernel_f32<W, KR, NC, 0>, g.ntiles / g.tps, W * 32, g.smem, s,
-                      (const Desc<float>*)g.ddescs, (const int2*)g.dtiles, g.tps));
+        CU(launch_pdl(step_kernel_f32<W, KR, NC, 0>, g.grid, W * 32, g.smem, s, (const Desc<float>*)g.ddescs,
+                      (const int4*)g.dsegs, g.spc));
     return VFPS_OK;
 }
 
 template <int W, int NC>
 int launch_pair_k(const Group& g, cudaStream_t s)
 {
-    CU(launch_pdl(step_kernel_f32x2<W, NC>, g.ntiles / g.tps, W * 32, g.smem, s, (const Desc<float>*)g.ddescs,
-                  (const int2*)g.dtiles, g.tps));
+    CU(launch_pdl(step_kernel_f32x2<W, NC>, g.grid, W * 32, g.smem, s, (const Desc<float>*)g.ddescs,
+                  (const int4*)g.dsegs, g.spc));
     return VFPS_OK;
 }
 
@@ -829,6 +843,8 @@ Group single_group(const Instance& I)
     g.ntiles = I.ntiles;
     g.ddescs = I.ddesc;
     g.dtiles = I.dtiles;
+    g.dsegs = I.dsegs;
+    g.grid = I.ntiles;
     return g;
 }
 
@@ -1232,6 +1248,47 @@ void free_groups(vfps_batch* b)
     b->groups.clear();
 }
 
+// CTAs of an FP32 group's kernel that fit on one SM at width W with smem
+// bytes of dynamic shared memory.
+template <typename K>
+int blocks_per_sm(K kernel, int threads, size_t smem)
+{
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return std::max(nb, 1);
+}
+
+template <int W>
+int fast_blocks_t(const Group& g, size_t smem)
+{
+    if (g.pair) {
+        if (g.n == 256) return blocks_per_sm(step_kernel_f32x2<W, 256>, W * 32, smem);
+        if (g.n == 1024) return blocks_per_sm(step_kernel_f32x2<W, 1024>, W * 32, smem);
+        return blocks_per_sm(step_kernel_f32x2<W, 0>, W * 32, smem);
+    }
+    if (g.kr == 8) {
+        if (g.n == 256)
+            return blocks_per_sm(g.rot ? step_kernel_f32<W, 8, 256, 1> : step_kernel_f32<W, 8, 256, 0>, W * 32, smem);
+        if (g.n == 1024)
+            return blocks_per_sm(g.rot ? step_kernel_f32<W, 8, 1024, 1> : step_kernel_f32<W, 8, 1024, 0>, W * 32,
+                                 smem);
+        return blocks_per_sm(g.rot ? step_kernel_f32<W, 8, 0, 1> : step_kernel_f32<W, 8, 0, 0>, W * 32, smem);
+    }
+    return blocks_per_sm(g.rot ? step_kernel_f32<W, 4, 0, 1> : step_kernel_f32<W, 4, 0, 0>, W * 32, smem);
+}
+
+int fast_blocks(const Group& g, int W, size_t smem)
+{
+    switch (W) {
+    case 8: return fast_blocks_t<8>(g, smem);
+    case 4: return fast_blocks_t<4>(g, smem);
+    default: return fast_blocks_t<2>(g, smem);
+    }
+}
+
 // Shared memory of a group member's kernel at CTA width W.
 size_t member_smem(const Group& g, const Instance* I, int W)
 {
@@ -1247,31 +1304,89 @@ int group_tiles(const Group& g, int W)
     return g.pair ? nt / 2 : nt;
 }
 
-// Lay out a batch group for CTA width W and strips of tps tiles: its
-// members' descriptors (ntiles patched to CTAs per step) and its tile table,
-// in the host copy of the group arrays; shared memory and tile count.
-void layout_group(vfps_batch* b, Group& g, int W, int tps)
+// Lay out a batch group for CTA width W in the host copy of the group
+// arrays: its members' descriptors (ntiles patched to the CTAs that touch
+// each simulation per step) and its tile table.  FP32 groups get segments
+// (unit, first column, tiles): strips of tps tiles, one per CTA, or with
+// tps = -1 a balanced grid of one resident wave's share of CTAs, each taking
+// an equal run of the group's tiles split at simulation boundaries.  Other
+// groups get one tile per CTA.  Returns false if the segments do not fit.
+bool layout_group(vfps_batch* b, Group& g, int W, int tps)
 {
+    const size_t dsz = g.prec ? sizeof(Desc<double>) : sizeof(Desc<float>);
+    size_t smem = 0;
+    for (const Instance* I : g.members) {
+        smem = std::max(smem, step_smem(&I->p, W));
+        if (g.fast) smem = std::max(smem, member_smem(g, I, W));
+    }
+    if (!g.fast) {
+        int2* ht = (int2*)(b->hbuf.data() + g.off_t);
+        int nt = 0;
+        for (size_t k = 0; k < g.members.size(); ++k) {
+            Instance* I = g.members[k];
+            unsigned char* hd = b->hbuf.data() + g.off_d + k * dsz;
+            std::memcpy(hd, I->hdesc, dsz);
+            const int per_inst = (I->n + W - 1) / W;
+            for (int t = 0; t < per_inst; ++t) ht[nt++] = make_int2((int)k, t * W);
+            if (g.prec) ((Desc<double>*)hd)->ntiles = per_inst;
+            else ((Desc<float>*)hd)->ntiles = per_inst;
+        }
+        g.W = W;
+        g.tps = 1;
+        g.smem = smem;
+        g.ntiles = nt;
+        g.tab_bytes = g.off_t + sizeof(int2) * nt - g.off_d;
+        return true;
+    }
+    const int units = g.pair ? (int)g.members.size() / 2 : (int)g.members.size();
+    const int per = (g.n + W - 1) / W;  // tiles per unit (a group shares n)
+    std::vector<int4> segs;
+    std::vector<int> touch(units, 0);
+    int spc = 1, grid = 0;
+    if (tps > 0) {
+        for (int u = 0; u < units; ++u)
+            for (int k = 0; k < per / tps; ++k) segs.push_back(make_int4(u, k * tps * W, tps, 0));
+        std::fill(touch.begin(), touch.end(), per / tps);
+        grid = (int)segs.size();
+    } else {
+        const long long NT = (long long)units * per;
+        const int nb = fast_blocks(g, W, smem);
+        long long G = std::llround(g.share * nb * num_sms());
+        G = std::max(1LL, std::min(G, NT));
+        std::vector<std::vector<int4>> cta((size_t)G);
+        for (long long c = 0; c < G; ++c) {
+            long long t = c * NT / G;
+            const long long t1 = (c + 1) * NT / G;
+            while (t < t1) {
+                const int u = (int)(t / per), loc = (int)(t % per);
+                const int len = (int)(std::min(t1, (long long)(u + 1) * per) - t);
+                cta[(size_t)c].push_back(make_int4(u, loc * W, len, 0));
+                ++touch[u];
+                t += len;
+            }
+            spc = std::max(spc, (int)cta[(size_t)c].size());
+        }
+        for (auto& v : cta) {
+            v.resize((size_t)spc, make_int4(0, 0, 0, 0));
+            segs.insert(segs.end(), v.begin(), v.end());
+        }
+        grid = (int)G;
+    }
+    if (segs.size() > g.seg_cap) return false;
+    for (size_t k = 0; k < g.members.size(); ++k) {
+        unsigned char* hd = b->hbuf.data() + g.off_d + k * dsz;
+        std::memcpy(hd, g.members[k]->hdesc, dsz);
+        ((Desc<float>*)hd)->ntiles = touch[g.pair ? k / 2 : k];
+    }
+    std::memcpy(b->hbuf.data() + g.off_t, segs.data(), sizeof(int4) * segs.size());
     g.W = W;
     g.tps = tps;
-    g.smem = 0;
-    const size_t dsz = g.prec ? sizeof(Desc<double>) : sizeof(Desc<float>);
-    int2* ht = (int2*)(b->hbuf.data() + g.off_t);
-    int nt = 0;
-    for (size_t k = 0; k < g.members.size(); ++k) {
-        Instance* I = g.members[k];
-        unsigned char* hd = b->hbuf.data() + g.off_d + k * dsz;
-        std::memcpy(hd, I->hdesc, dsz);
-        const int per_inst = (I->n + W - 1) / W;
-        // a pair's tiles are listed once, by pair index
-        if (!g.pair || k % 2 == 0)
-            for (int t = 0; t < per_inst; ++t) ht[nt++] = make_int2(g.pair ? (int)k / 2 : (int)k, t * W);
-        if (g.prec) ((Desc<double>*)hd)->ntiles = per_inst / tps;
-        else ((Desc<float>*)hd)->ntiles = per_inst / tps;
-        g.smem = std::max(g.smem, step_smem(&I->p, W));
-        if (g.fast) g.smem = std::max(g.smem, member_smem(g, I, W));
-    }
-    g.ntiles = nt;
+    g.smem = smem;
+    g.spc = spc;
+    g.grid = grid;
+    g.ntiles = units * per;
+    g.tab_bytes = g.off_t + sizeof(int4) * segs.size() - g.off_d;
+    return true;
 }
 
 int default_tps(const Group& g, int W)
@@ -1315,7 +1430,7 @@ bool pin_fits(const Group& g, int W, int tps)
     const long long lim = device_smem_limit() - 1024;
     for (const Instance* I : g.members)
         if ((long long)member_smem(g, I, W) > lim) return false;
-    return tps >= 1 && ((g.n + W - 1) / W) % tps == 0;
+    return tps == -1 || (tps >= 1 && ((g.n + W - 1) / W) % tps == 0);
 }
 
 std::vector<std::pair<int, int>> tune_candidates(const Group& g)
@@ -1331,6 +1446,7 @@ std::vector<std::pair<int, int>> tune_candidates(const Group& g)
         for (int t : {1, 2, 4, 8, 16, 32})
             if (per_inst % t == 0 && nt / t >= num_sms()) c.push_back({W, t});
         if (c.empty() || c.back().first != W) c.push_back({W, default_tps(g, W)});
+        c.push_back({W, -1});  // balanced grid
     }
     return c;
 }
@@ -1432,13 +1548,22 @@ int rebuild_groups(vfps_batch* b)
     // descriptor and tile arrays, with room for the narrowest width (W = 2)
     size_t total = 0;
     std::vector<std::pair<size_t, size_t>> offs;
+    // tile or segment tables: room for one strip per tile at W = 2, or a
+    // balanced grid of up to 32 CTAs per SM with up to 4 segments each
+    std::vector<size_t> caps;
+    double fast_cells = 0.0;
     for (auto& kv : cls) {
         size_t nt = 0;
-        for (Instance* I : kv.members) nt += (size_t)(I->n + 1) / 2;
+        for (Instance* I : kv.members) {
+            nt += (size_t)(I->n + 1) / 2;
+            if (I->fast) fast_cells += double(I->n) * I->n;
+        }
+        const size_t cap = nt + 128 * (size_t)num_sms();
         size_t od = align_up(total, kAlign);
         size_t ot = align_up(od + kv.members.size() * sizeof(Desc<double>), kAlign);
-        total = ot + nt * sizeof(int2);
+        total = ot + cap * sizeof(int4);
         offs.push_back({od, ot});
+        caps.push_back(cap);
     }
     if (dev_alloc(&b->gmem, total) != cudaSuccess) {
         cudaGetLastError();
@@ -1461,6 +1586,13 @@ int rebuild_groups(vfps_batch* b)
         g.off_t = offs[gi].second;
         g.ddescs = (unsigned char*)b->gmem + g.off_d;
         g.dtiles = (int2*)((unsigned char*)b->gmem + g.off_t);
+        g.dsegs = (int4*)((unsigned char*)b->gmem + g.off_t);
+        g.seg_cap = caps[gi];
+        if (g.fast && fast_cells > 0.0) {
+            double cells = 0.0;
+            for (const Instance* I : kv.members) cells += double(I->n) * I->n;
+            g.share = cells / fast_cells;
+        }
         g.kr = fast_kr(kv.members[0]->p.n);  // a group shares n
         g.n = kv.members[0]->p.n;
         g.rot = kv.members[0]->p.rotation;
@@ -1501,7 +1633,10 @@ int rebuild_groups(vfps_batch* b)
                 g.cand = -1;
             }
         }
-        layout_group(b, g, W, tps);
+        if (!layout_group(b, g, W, tps)) {
+            g.cands.clear();
+            layout_group(b, g, W, default_tps(g, W));
+        }
         b->groups.push_back(g);
         ++gi;
     }
@@ -1532,9 +1667,8 @@ int tune_step_done(vfps_batch* b)
         }
         g.cands.clear();
         g.cand_ms.clear();
-        layout_group(b, g, choice.first, choice.second);
-        const size_t bytes = g.off_t + sizeof(int2) * g.ntiles - g.off_d;
-        CU(cudaMemcpyAsync((unsigned char*)b->gmem + g.off_d, b->hbuf.data() + g.off_d, bytes,
+        if (!layout_group(b, g, choice.first, choice.second)) layout_group(b, g, choice.first, default_tps(g, choice.first));
+        CU(cudaMemcpyAsync((unsigned char*)b->gmem + g.off_d, b->hbuf.data() + g.off_d, g.tab_bytes,
                            cudaMemcpyHostToDevice, b->stream));
     }
     return VFPS_OK;
@@ -1547,7 +1681,7 @@ extern "C" {
 int64_t vfps_batch_slot_bytes(const vfps_params* params)
 {
     if (check_params(params)) return -1;
-    size_t offs[14];
+    size_t offs[15];
     return (int64_t)instance_bytes(params, kRingDefault / 2, offs);
 }
 
@@ -1583,7 +1717,7 @@ int vfps_batch_add(vfps_batch* b, const vfps_params* params, const double* psi0,
             break;
         }
     if (free_slot < 0) return VFPS_EBUSY;
-    size_t offs[14];
+    size_t offs[15];
     long long need = (long long)instance_bytes(params, kRingDefault / 2, offs);
     if (b->budget > 0 && b->used + need > b->budget) return VFPS_EBUSY;
     size_t fr = 0, tot = 0;
@@ -1648,9 +1782,9 @@ int vfps_batch_run(vfps_batch* b, int64_t chunk_steps)
         for (Group& g : b->groups) {
             if (g.cands.empty()) continue;
             if (g.cand >= 0) {  // upload the layout of the candidate under test
-                layout_group(b, g, g.cands[g.cand].first, g.cands[g.cand].second);
-                const size_t bytes = g.off_t + sizeof(int2) * g.ntiles - g.off_d;
-                CU(cudaMemcpyAsync((unsigned char*)b->gmem + g.off_d, b->hbuf.data() + g.off_d, bytes,
+                const int cw = g.cands[g.cand].first;
+                if (!layout_group(b, g, cw, g.cands[g.cand].second)) layout_group(b, g, cw, default_tps(g, cw));
+                CU(cudaMemcpyAsync((unsigned char*)b->gmem + g.off_d, b->hbuf.data() + g.off_d, g.tab_bytes,
                                    cudaMemcpyHostToDevice, g.stream));
             }
             CU(cudaEventRecord(g.t0, g.stream));
@@ -1754,7 +1888,7 @@ int vfps_batch_pairing(vfps_batch* b, int32_t on)
 
 int vfps_batch_pin_shape(vfps_batch* b, int32_t W, int32_t tps)
 {
-    if (!b || !((W == 0 && tps == 0) || ((W == 2 || W == 4 || W == 8) && tps >= 1 && tps <= 256)))
+    if (!b || !((W == 0 && tps == 0) || ((W == 2 || W == 4 || W == 8) && ((tps >= 1 && tps <= 256) || tps == -1))))
         return VFPS_EINVAL;
     b->pin_W = W;
     b->pin_tps = tps;
@@ -1857,7 +1991,8 @@ constexpr size_t kSA = 256;
 constexpr size_t sa(size_t v) { return (v + kSA - 1) / kSA * kSA; }
 constexpr size_t kOffDesc = 0;
 constexpr size_t kOffTiles = kOffDesc + sa(sizeof(Desc<float>));
-constexpr size_t kOffState = kOffTiles + sa(sizeof(int2) * (kStaticMaxN / 2 + 1));
+constexpr size_t kOffSegs = kOffTiles + sa(sizeof(int2) * (kStaticMaxN / 2 + 1));
+constexpr size_t kOffState = kOffSegs + sa(sizeof(int4) * (kStaticMaxN / 2 + 1));
 constexpr size_t kOffColsum = kOffState + sa(sizeof(DevState));
 constexpr size_t kOffRho = kOffColsum + sa(sizeof(double) * kStaticMaxN);
 constexpr size_t kOffKick = kOffRho + sa(sizeof(double) * kStaticMaxN);
@@ -1979,7 +2114,11 @@ extern "C" int vfps_step_static(const vfps_params* params, int model, double Pi,
     unsigned char* h = g_static_host;
     std::memcpy(h + kOffDesc, I.hdesc, sizeof(Desc<float>));
     int2* tiles = (int2*)(h + kOffTiles);
-    for (int i = 0; i < I.ntiles; ++i) tiles[i] = make_int2(0, i * W);
+    int4* segs = (int4*)(h + kOffSegs);
+    for (int i = 0; i < I.ntiles; ++i) {
+        tiles[i] = make_int2(0, i * W);
+        segs[i] = make_int4(0, i * W, 1, 0);
+    }
     DevState st{};
     st.scale = 1.0;
     std::memcpy(h + kOffState, &st, sizeof(st));
@@ -2006,6 +2145,8 @@ extern "C" int vfps_step_static(const vfps_params* params, int model, double Pi,
     g.smem = fast ? std::max(fast_smem(params, W), step_smem(params, W)) : step_smem(params, W);
     g.ddescs = d + kOffDesc;
     g.dtiles = (int2*)(d + kOffTiles);
+    g.dsegs = (int4*)(d + kOffSegs);
+    g.grid = I.ntiles;
     rc = launch_project(g, s);   // profile, wake and P of psi_in
     if (rc) return rc;
     rc = launch_step(g, s);      // psi_out = one un-normalised step

@@ -432,24 +432,19 @@ __device__ __forceinline__ void drift_column(const float* __restrict__ ring, int
     }
 }
 
-// Streaming FP32 step.  CTA b takes the strip of tps consecutive W-column
-// tiles tiles[b*tps .. b*tps+tps-1] (one instance, consecutive columns) and
-// walks it tile by tile.  The slab columns live in a ring of R shared-memory
-// slots (R >= 2W + 2h): while tile j is computed, the W new columns of tile
-// j+1 are resident or landing and those of tile j+2 are requested, so each
-// column of psi is read from HBM once per strip and the copies overlap the
-// arithmetic.  psi_a stays unscaled; the pending renormalisation factor is
-// part of the kick weights.  The column sums of a strip are made visible
-// with one fence per thread before the CTA takes its ticket.
+// One strip of the streaming FP32 step: T consecutive W-column tiles of
+// simulation D from column xs.  The strip walks its tiles one by one.  The
+// slab columns live in a ring of R shared-memory slots (R >= 2W + 2h): while
+// tile j is computed, the W new columns of tile j+1 are resident or landing
+// and those of tile j+2 are requested, so each column of psi is read from
+// HBM once per strip and the copies overlap the arithmetic.  psi_a stays
+// unscaled; the pending renormalisation factor is part of the kick weights.
+// The column sums of a strip are made visible with one fence per thread
+// before the CTA takes the simulation's ticket; the CTA that takes the last
+// ticket runs the finaliser.
 template <int W, int KR, int NC, int ROT>
-__global__ void __launch_bounds__(W * 32, 32 / W)
-step_kernel_f32(const Desc<float>* __restrict__ descs, const int2* __restrict__ tiles, int tps)
+__device__ __forceinline__ void strip_f32(const Desc<float>& D, int xs, int T, unsigned char* smem, int& s_last)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_last;
-    const int2 first = tiles[blockIdx.x * tps];
-    const Desc<float>& D = descs[first.x];
-    const int xs = first.y;
     // NC > 0: the grid size is a compile-time constant (the hot sizes), so
     // loop bounds and pitches fold into the code; ld = n for FP32 then
     const int n = NC ? NC : D.n, ld = NC ? NC : D.ld, h = D.h;
@@ -459,7 +454,6 @@ step_kernel_f32(const Desc<float>* __restrict__ descs, const int2* __restrict__ 
     const int PA = cola_pitch(n);
     const int HC = PA / 8;  // chunks in half a psi_a column (split layout)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int T = min(tps, (n - xs + W - 1) / W);
     const float cm1 = D.cm1, sn = D.sn, c = D.c;
     const float4* __restrict__ kickw = D.kickw;
     double* __restrict__ colsum = D.colsum;
@@ -467,16 +461,11 @@ step_kernel_f32(const Desc<float>* __restrict__ descs, const int2* __restrict__ 
     float* ring = reinterpret_cast<float*>(smem);
     float* colA = ring + R * P;
     float* gtab = colA + W * PA;  // g_0(y) .. g_3(y), n each (split layout for KR = 8)
-#ifdef VFPS_DEBUG
-    if (threadIdx.x == 0) s_dbg_site = 0;
-    __syncthreads();
-#endif
     float* colcol = colA + warp * PA;  // this warp's psi_a column, padded
     float4* kbuf = reinterpret_cast<float4*>(gtab + 4 * n) + 2 * warp;  // stage k: kbuf + 2 W k
     constexpr int rot = ROT;            // 1: Manhattan rotation (every instance of the launch)
     const float hm = D.hm;
     float* colbcol = reinterpret_cast<float*>(reinterpret_cast<float4*>(gtab + 4 * n) + 8 * W) + warp * PA;
-    pdl_trigger();
 
     // padding rows of every ring slot and of this warp's psi_a column: zero
     // for the whole strip
@@ -644,6 +633,30 @@ step_kernel_f32(const Desc<float>* __restrict__ descs, const int2* __restrict__ 
     if (s_last) {
         __threadfence();
         finalise<float>(D, smem, 1);
+    }
+}
+
+// Streaming FP32 step.  CTA b walks its segments segs[b*spc .. b*spc+spc-1]
+// in order, each (simulation, first column, tiles) a strip of strip_f32; a
+// segment with no tiles ends the list.  With one segment per CTA the grid is
+// one CTA per strip; with balanced segments every CTA takes an equal share of
+// the launch's tiles, split at simulation boundaries.
+template <int W, int KR, int NC, int ROT>
+__global__ void __launch_bounds__(W * 32, 32 / W)
+step_kernel_f32(const Desc<float>* __restrict__ descs, const int4* __restrict__ segs, int spc)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_last;
+#ifdef VFPS_DEBUG
+    if (threadIdx.x == 0) s_dbg_site = 0;
+    __syncthreads();
+#endif
+    pdl_trigger();
+    for (int i = 0; i < spc; ++i) {
+        const int4 sg = segs[blockIdx.x * spc + i];
+        if (sg.z <= 0) break;
+        if (i > 0) __syncthreads();  // shared memory of the previous strip (or its finaliser) is free
+        strip_f32<W, KR, NC, ROT>(descs[sg.x], sg.y, sg.z, smem, s_last);
     }
 }
 

@@ -348,38 +348,25 @@ __device__ __forceinline__ float kick_fp_large(const unsigned char* __restrict__
     return lsum;
 }
 
-// Streaming FP32 step of pairs of simulations.  CTA b takes the strip of tps
-// consecutive W-column tiles tiles[b*tps ..] of pair first.x (descriptors
-// 2 first.x and 2 first.x + 1) and walks it as step_kernel_f32 does for one
-// simulation; at the end it takes a ticket of each simulation and runs the
+// One strip of the pair kernel: T consecutive W-column tiles of the pair
+// (DA, DB) from column xs, walked as strip_f32 walks one simulation's strip;
+// at the end the CTA takes a ticket of each simulation and runs the
 // finaliser of each one it completes.
 template <int W, int NC>
-__global__ void __launch_bounds__(W * 32, 16 / W)
-step_kernel_f32x2(const Desc<float>* __restrict__ descs, const int2* __restrict__ tiles, int tps)
+__device__ __forceinline__ void strip_f32x2(const Desc<float>& DA, const Desc<float>& DB, int xs, int T,
+                                            unsigned char* smem, int* s_last)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_last[2];
-    const int2 first = tiles[blockIdx.x * tps];
-    const Desc<float>& DA = descs[2 * first.x];
-    const Desc<float>& DB = descs[2 * first.x + 1];
-    const int xs = first.y;
     const int n = NC ? NC : DA.n, ld = NC ? NC : DA.ld, h = DA.h;
     const int R = ring_slots(W, h);
     const int SLOTB = pair_slot_bytes(n), HALFB = 16 * pair_half(n);
     const int QAB = 16 * pair_cola_q(n), CAB = 4 * QAB;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int T = min(tps, (n - xs + W - 1) / W);
     const float cm1 = DA.cm1, sn = DA.sn, c = DA.c;
 
     unsigned char* ring = smem;
     unsigned char* colA = ring + R * SLOTB + warp * CAB;  // this warp's psi_a column pair
     unsigned char* gtab = ring + R * SLOTB + W * CAB;
     float4* kbuf = reinterpret_cast<float4*>(gtab + 32 * n) + 4 * warp;  // stage k: kbuf + 4 W k
-#ifdef VFPS_DEBUG
-    if (threadIdx.x == 0) s_dbg_site = 0;
-    __syncthreads();
-#endif
-    pdl_trigger();
 
     // padding pair-rows of every ring slot (chunks 0..7 and n/2+8 .. n/2+15)
     // and of this warp's psi_a column: zero for the whole strip
@@ -521,6 +508,28 @@ step_kernel_f32x2(const Desc<float>* __restrict__ descs, const int2* __restrict_
         __syncthreads();
         __threadfence();
         finalise<float>(DB, smem, 1);
+    }
+}
+
+// Streaming FP32 step of pairs of simulations: CTA b walks its segments
+// segs[b*spc ..] (pair index, first column, tiles) as step_kernel_f32 walks
+// its own; pair k is descriptors 2k and 2k+1.
+template <int W, int NC>
+__global__ void __launch_bounds__(W * 32, 16 / W)
+step_kernel_f32x2(const Desc<float>* __restrict__ descs, const int4* __restrict__ segs, int spc)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_last[2];
+#ifdef VFPS_DEBUG
+    if (threadIdx.x == 0) s_dbg_site = 0;
+    __syncthreads();
+#endif
+    pdl_trigger();
+    for (int i = 0; i < spc; ++i) {
+        const int4 sg = segs[blockIdx.x * spc + i];
+        if (sg.z <= 0) break;
+        if (i > 0) __syncthreads();
+        strip_f32x2<W, NC>(descs[2 * sg.x], descs[2 * sg.x + 1], sg.y, sg.z, smem, s_last);
     }
 }
 

@@ -327,7 +327,7 @@ class Batch:
         _check(lib().vfps_batch_pairing(self._b, 1 if on else 0), "vfps_batch_pairing")
 
     def pin_shape(self, W: int = 0, tps: int = 0):
-        """Fix the CTA width and strip length of the FP32 groups (0, 0 releases)."""
+        """Fix the CTA width and strip length of the FP32 groups (tps=-1: balanced grid; 0, 0 releases)."""
         _check(lib().vfps_batch_pin_shape(self._b, int(W), int(tps)), "vfps_batch_pin_shape")
 
     def autotune(self, on: bool = True):

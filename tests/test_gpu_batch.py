@@ -262,3 +262,31 @@ def test_pairing_keeps_bits(V):
         assert np.all(np.isfinite(a["psi"])), i
         assert np.array_equal(a["psi"], c["psi"]), i
         assert np.array_equal(a["power"], c["power"]), i
+
+
+def test_balanced_grid_keeps_bits(V):
+    """The balanced grid (one resident wave of CTAs, each walking an equal
+    run of tiles across simulation boundaries, tps = -1) gives the same bits
+    as strips of one simulation per CTA, for single and paired simulations."""
+    n, spp, ns, count = 256, 1000, 3, 64
+    pts = W.scan_grid()
+    res = {}
+    for shape in ((4, 8), (4, -1), (2, -1), (8, -1)):
+        for pair in (False, True):
+            b = V.Batch(count)
+            b.pin_shape(*shape)
+            b.pairing(pair)
+            slots = [b.add(V.Params(n=n, steps_per_period=spp, beta=1e-2), W.noisy_gaussian(n, 1612 + i % 3),
+                           V.IMPEDANCE_PARALLEL_PLATES, pts[i % len(pts)][1], pts[i % len(pts)][0], nsteps=ns)
+                     for i in range(count)]
+            b.run(1)
+            sh = b.shapes()
+            assert all(g["tps"] == shape[1] for g in sh if g["W"] == shape[0]), sh
+            b.run(ns - 1)
+            res[(shape, pair)] = [b.take(s) for s in slots]
+            b.close()
+    ref = res[((4, 8), False)]
+    for key, r in res.items():
+        for i in range(count):
+            assert np.array_equal(r[i]["psi"], ref[i]["psi"]), (key, i)
+            assert np.array_equal(r[i]["power"], ref[i]["power"]), (key, i)

@@ -26,7 +26,7 @@ SCRIPT = textwrap.dedent("""
             p = V.Params(n=n, steps_per_period=500, beta=1e-2, rotation=rot)
             sim = V.Simulation(p, W.blobs(n, n + rot)); sim.set_impedance(2, 2.0, 0.9); sim.step(3)
             out[f"solo_{n}_{rot}"] = sim.get_state(); sim.close()
-            for Wd, tps in ((2, 1), (4, 4), (8, 1), (8, 4)):
+            for Wd, tps in ((2, 1), (4, 4), (8, 1), (8, 4), (4, -1), (8, -1)):
                 for pair in (False, True):
                     b = V.Batch(2); b.autotune(False); b.pin_shape(Wd, tps); b.pairing(pair)
                     s = [b.add(p, W.blobs(n, 7 * i + n), 2, 2.0, 0.7 + 0.2 * i, nsteps=3) for i in range(2)]
