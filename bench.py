@@ -146,9 +146,9 @@ def build_batch(V, count, n, spp, beta, stream, seed=1612, rotation=0, rank=0, w
     return b
 
 
-def calibrate(V, torch, stream, count, n=256, spp=1000, beta=1e-2, rotation=0, steps=96):
+def calibrate(V, torch, stream, count, n=256, spp=1000, beta=1e-2, rotation=0, steps=480):
     """Let the library's autotuner time its candidate launch shapes for this
-    batch configuration on a throwaway batch (96 steps), so that the timed
+    batch configuration on a throwaway batch (480 steps), so that the timed
     batch built next starts with the tuned shape (the choice is cached per
     configuration for the process)."""
     b = build_batch(V, count, n, spp, beta, stream, rotation=rotation)

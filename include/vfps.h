@@ -247,7 +247,7 @@ int vfps_batch_power_spectrum(vfps_batch* b, int32_t slot, int32_t length, doubl
  * size rounded up to a power of two -- the first steps of vfps_batch_run time
  * the candidate CTA widths W in {8, 4, 2} with strip lengths (1..32 tiles per
  * CTA) and with the balanced grid (one resident wave of CTAs, each taking an
- * equal run of the group's tiles), four back-to-back steps each after four
+ * equal run of the group's tiles), 16 back-to-back steps each after 16
  * warm-up steps, and keep the fastest for the rest of the process (a run
  * shorter than the tuning keeps tuning on its next call).  The timed steps
  * are ordinary steps: every candidate gives the same bits.  Setting

@@ -1406,7 +1406,7 @@ int default_tps(const Group& g, int W)
 // the strip length), so the timed steps are ordinary steps of the run.
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int, int, int>, std::pair<int, int>> g_tuned;
-constexpr int kTuneSteps = 4;  // steps timed per candidate
+constexpr int kTuneSteps = 16;  // steps timed per candidate (4 were too few to rank 8- and 16-tile strips)
 
 bool autotune_enabled()
 {

@@ -147,6 +147,23 @@ __device__ __forceinline__ void rotate_block(const float* __restrict__ ring, int
     out[3] = acc23.y;
 }
 
+// Offset of the psi_a column row kColPad + yb + 4 lane (start of a
+// lane's 4-row rotation block, yb a multiple of 128) in the column layout:
+// the lane part, to which 2 (kColPad/4 + yb/4) (split layout) or kColPad + yb
+// (plain layout) is added.
+template <int KR>
+__device__ __forceinline__ int cola_lane_base(int lane, int HC)
+{
+    if constexpr (KR == 8) return ((lane >> 1) + (lane & 1) * HC) << 2;
+    else return 4 * lane;
+}
+template <int KR>
+__device__ __forceinline__ int cola_block_off(int yb)
+{
+    if constexpr (KR == 8) return 2 * ((kColPad >> 2) + (yb >> 2));
+    else return kColPad + yb;
+}
+
 // Kick + Fokker-Planck for the lane's blocks of KR rows of one column.  The
 // psi_a window starts O2 rows above the first row the kick of row y0-1
 // needs (A2 = s - 2 + kColPad: column index of row y0+s-2, minus y0; PAR =
@@ -169,7 +186,10 @@ __device__ __forceinline__ float kick_fp_column(const float* __restrict__ colcol
     // psi_b(y) is 0 off the grid and where its source is > 1 cell outside
     const int lo = max(0, -1 - s), hi = min(n - 1, n - 1 - s);
     float lsum = 0.f;
-    for (int y0 = KR * lane; y0 < n; y0 += 32 * KR) {
+#pragma unroll
+    for (int yb = 0; yb < n; yb += 32 * KR) {
+        const int y0 = yb + KR * lane;
+        if ((n % (32 * KR)) && y0 >= n) break;
         float win[4 * NV];
         // window rows y0 + A2 - O2 .. + 4 NV - 1 of the padded column (8 HC rows)
         const bool wok = VFPS_GUARD(y0 + A2 - O2 >= 0 && y0 + A2 - O2 + 4 * NV <= 8 * HC, 4);
@@ -351,7 +371,11 @@ __device__ __forceinline__ void rotate_column(const float* __restrict__ ring, in
     const float2 snxc = f2(sn * xc, sn * xc), cmxc = f2(cm1 * xc, cm1 * xc);
     const float fyf = float(FY);
     const float2 mfy = f2(-fyf, -fyf);
-    for (int y0 = 4 * lane; y0 < n; y0 += 128) {
+    const int lbase = cola_lane_base<KR>(lane, HC);
+#pragma unroll 1
+    for (int yb = 0; yb < n; yb += 128) {
+        const int y0 = yb + 4 * lane;
+        if ((n & 127) && y0 >= n) break;
         const float yc0 = float(y0) - c;
         const float2 yc01 = f2(yc0, yc0 + 1.f), yc23 = f2(yc0 + 2.f, yc0 + 3.f);
         // dx = (cos phi - 1) xc - sin phi yc,  dy = sin phi xc + (cos phi - 1) yc
@@ -375,7 +399,7 @@ __device__ __forceinline__ void rotate_column(const float* __restrict__ ring, in
             }
         }
         if (VFPS_GUARD(kColPad + y0 + 4 <= 8 * HC, 5))
-            *reinterpret_cast<float4*>(colcol + split_idx<KR>(kColPad + y0, HC)) = make_float4(r[0], r[1], r[2], r[3]);
+            *reinterpret_cast<float4*>(colcol + lbase + cola_block_off<KR>(yb)) = make_float4(r[0], r[1], r[2], r[3]);
     }
 }
 
@@ -390,7 +414,11 @@ __device__ __forceinline__ void drift_column(const float* __restrict__ ring, int
                                              float* __restrict__ colcol, int HC, int x, int n, int lane, float c,
                                              float hm)
 {
-    for (int y0 = 4 * lane; y0 < n; y0 += 128) {
+    const int lbase = cola_lane_base<KR>(lane, HC);
+#pragma unroll 1
+    for (int yb = 0; yb < n; yb += 128) {
+        const int y0 = yb + 4 * lane;
+        if ((n & 127) && y0 >= n) break;
         const float yc0 = float(y0) - c;
         const float d0 = -hm * yc0, d1 = -hm * (yc0 + 1.f), d2 = -hm * (yc0 + 2.f), d3 = -hm * (yc0 + 3.f);
         const float fx0 = floorf(d0), fx1 = floorf(d1), fx2 = floorf(d2), fx3 = floorf(d3);
@@ -427,7 +455,7 @@ __device__ __forceinline__ void drift_column(const float* __restrict__ ring, int
             }
         }
         if (VFPS_GUARD(kColPad + y0 + 4 <= 8 * HC, 5))
-            *reinterpret_cast<float4*>(colcol + split_idx<KR>(kColPad + y0, HC)) =
+            *reinterpret_cast<float4*>(colcol + lbase + cola_block_off<KR>(yb)) =
                 make_float4(acc[0], acc[1], acc[2], acc[3]);
     }
 }
