@@ -16,8 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libvfps.so")
 LIB_DEBUG = os.path.join(HERE, "libvfps_debug.so")  # -DVFPS_DEBUG: shared-memory index checks
 SOURCES = [os.path.join(CSRC, f) for f in ("vfps.cu", "impedance_host.cpp")]
-DEPS = SOURCES + [os.path.join(CSRC, "vfps_kernels.cuh"), os.path.join(CSRC, "vfps_fast.cuh"),
-                  os.path.join(ROOT, "include", "vfps.h")]
+DEPS = SOURCES + [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC)) if f.endswith((".cuh", ".h"))] + \
+    [os.path.join(ROOT, "include", "vfps.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -147,6 +147,53 @@ __device__ __forceinline__ void rotate_block(const float* __restrict__ ring, int
     out[3] = acc23.y;
 }
 
+// rotate_block when no row of the block steps back: the x-node of all four
+// rows is row 0's, so only window columns 1..4 take part and the x-weights
+// need no selection (same operations as rotate_block for such a block, whose
+// column-0 terms are zeros).
+template <int O>
+__device__ __forceinline__ void rotate_block4(const float* __restrict__ ring, int slot0, int R, int P, int rowoff,
+                                              float2 tx01, float2 tx23, float2 ty01, float2 ty23, float out[4])
+{
+    float2 wy01[4], wy23[4], wx01[4], wx23[4];
+    lagrange2(ty01, wy01);
+    lagrange2(ty23, wy23);
+    lagrange2(tx01, wx01);
+    lagrange2(tx23, wx23);
+    const float wy[4][4] = {{wy01[0].x, wy01[1].x, wy01[2].x, wy01[3].x},
+                            {wy01[0].y, wy01[1].y, wy01[2].y, wy01[3].y},
+                            {wy23[0].x, wy23[1].x, wy23[2].x, wy23[3].x},
+                            {wy23[0].y, wy23[1].y, wy23[2].y, wy23[3].y}};
+    float2 acc01, acc23;
+#pragma unroll
+    for (int a = 1; a < 5; ++a) {
+        const float4* cp = reinterpret_cast<const float4*>(ring + ((slot0 + a) & (R - 1)) * P + rowoff);
+        const bool ok = VFPS_GUARD(rowoff >= 0 && rowoff + 12 <= P && slot0 >= 0 && slot0 < R, 2);
+        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 q0 = ok ? cp[0] : z4, q1 = ok ? cp[1] : z4, q2 = ok ? cp[2] : z4;
+        const float win[12] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, q2.x, q2.y, q2.z, q2.w};
+        float r[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float v = wy[k][0] * win[O + k];
+            v = fmaf(wy[k][1], win[O + k + 1], v);
+            v = fmaf(wy[k][2], win[O + k + 2], v);
+            r[k] = fmaf(wy[k][3], win[O + k + 3], v);
+        }
+        if (a == 1) {
+            acc01 = __fmul2_rn(wx01[0], f2(r[0], r[1]));
+            acc23 = __fmul2_rn(wx23[0], f2(r[2], r[3]));
+        } else {
+            acc01 = __ffma2_rn(wx01[a - 1], f2(r[0], r[1]), acc01);
+            acc23 = __ffma2_rn(wx23[a - 1], f2(r[2], r[3]), acc23);
+        }
+    }
+    out[0] = acc01.x;
+    out[1] = acc01.y;
+    out[2] = acc23.x;
+    out[3] = acc23.y;
+}
+
 // Offset of the psi_a column row kColPad + yb + 4 lane (start of a
 // lane's 4-row rotation block, yb a multiple of 128) in the column layout:
 // the lane part, to which 2 (kColPad/4 + yb/4) (split layout) or kColPad + yb
@@ -374,8 +421,10 @@ __device__ __forceinline__ void rotate_column(const float* __restrict__ ring, in
     const int lbase = cola_lane_base<KR>(lane, HC);
 #pragma unroll 1
     for (int yb = 0; yb < n; yb += 128) {
+        // every lane runs every pass (the vote below needs the whole warp);
+        // lanes past the last row only vote
         const int y0 = yb + 4 * lane;
-        if ((n & 127) && y0 >= n) break;
+        const bool live = !(n & 127) || y0 < n;
         const float yc0 = float(y0) - c;
         const float2 yc01 = f2(yc0, yc0 + 1.f), yc23 = f2(yc0 + 2.f, yc0 + 3.f);
         // dx = (cos phi - 1) xc - sin phi yc,  dy = sin phi xc + (cos phi - 1) yc
@@ -387,8 +436,15 @@ __device__ __forceinline__ void rotate_column(const float* __restrict__ ring, in
         const float2 tx01 = f2(dx01.x - fx0, dx01.y - fx1), tx23 = f2(dx23.x - fx2, dx23.y - fx3);
         const int mx0 = x + int(fx0);
         float r[4];
-        rotate_block<O>(ring, (mx0 - 2) & (R - 1), R, P, y0 + A - O, tx01, tx23, ty01, ty23, fx1 < fx0, fx2 < fx0,
-                        fx3 < fx0, r);
+        // the x-node steps back inside the block iff it does at row 3; most
+        // passes have no such block in the whole warp and skip window column 0
+        const bool anyback = __any_sync(0xffffffffu, live && fx3 < fx0);
+        if (!live) continue;
+        if (anyback)
+            rotate_block<O>(ring, (mx0 - 2) & (R - 1), R, P, y0 + A - O, tx01, tx23, ty01, ty23, fx1 < fx0,
+                            fx2 < fx0, fx3 < fx0, r);
+        else
+            rotate_block4<O>(ring, (mx0 - 2) & (R - 1), R, P, y0 + A - O, tx01, tx23, ty01, ty23, r);
         // sources more than one cell outside the grid give 0
         if (!((mx0 >= 0) && (mx0 <= n - 1) && (y0 + FY >= -1) && (y0 + 3 + FY <= n - 1))) {
             const float fxk[4] = {fx0, fx1, fx2, fx3};

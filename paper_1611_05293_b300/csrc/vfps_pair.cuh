@@ -148,7 +148,9 @@ __device__ __forceinline__ void rotate_column_pair(const unsigned char* __restri
     const float fyf = float(FY);
     const float2 mfy = f2(-fyf, -fyf);
     const int Kq = K >> 2;
-    for (int y0 = 4 * lane; y0 < n; y0 += 128) {
+    for (int yb = 0; yb < n; yb += 128) {
+        const int y0 = yb + 4 * lane;
+        if ((n & 127) && y0 >= n) break;
         const float yc0 = float(y0) - c;
         const float2 yc01 = f2(yc0, yc0 + 1.f), yc23 = f2(yc0 + 2.f, yc0 + 3.f);
         const float2 dx01 = __ffma2_rn(msn2, yc01, cmxc);
