@@ -41,10 +41,10 @@ HBM_FALLBACK_GBS = 6400.0
 # DRAM bytes (read + write) of one launch of step_kernel_f32 on a 256-instance
 # N=256 group, from the ncu capture summarised in
 # profiles/step_kernel_f32_batched_n256.md (launch shape W=4, 16-tile strips, the
-# autotuner's choice; 8-tile strips measured 96.3 MB); a step of the
+# autotuner's choice); a step of the
 # 512-instance benchmark is two such launches.  Set to None whenever the kernel
 # changes until a new capture is taken.
-MEASURED_TRAFFIC_PER_LAUNCH = None
+MEASURED_TRAFFIC_PER_LAUNCH = 98.1e6
 
 
 def measured_peaks():
