@@ -51,6 +51,7 @@ extern "C" {
 #define VFPS_EBOUNDS (-7)  /* debug build (VFPS_DEBUG) only: a shared-memory
                               index check failed; the site is named in
                               vfps_last_cuda_error()                         */
+#define VFPS_ECONVERGE (-8) /* an iterative solve did not reach its tolerance  */
 
 #define VFPS_IMPEDANCE_NONE 0            /* no collective effect                      */
 #define VFPS_IMPEDANCE_FREE_SPACE 1      /* CSR in free space (Sec. II.B)             */
@@ -147,6 +148,20 @@ int vfps_get_state(vfps_handle* h, double* psi_out);
 /* Replace psi by host psi (n*n doubles, normalised to charge 1 by the
  * library) and recompute its wake; the step counter is kept.  Errors: EINVAL. */
 int vfps_set_state(vfps_handle* h, const double* psi);
+
+/* Haissinski start (Appendix A names the equilibrium; Sec. II.B gives the
+ * wake): replace the current state by psi = rho_H(q) g(p), with g the unit
+ * Gaussian in p and rho_H the profile that solves
+ *   rho(q) = A exp(-q^2/2 + S_csr int_{-L}^{q} V[rho] dq'),  Delta sum rho = 1,
+ * for the simulation's own grid, impedance (set it first) and S_csr, V the
+ * wake potential of the step (same FFT length and impedance table).  The
+ * damped fixed-point iteration rho <- (rho + new)/2 from the unit Gaussian
+ * runs on the device in FP64 (trapezoid rule for the integral) until
+ * max|new - rho| < tol max rho, at most max_iter times; *iterations (may be
+ * NULL) gets the count.  Below the instability threshold the run then starts
+ * at equilibrium.  Synchronises.  Errors: EINVAL (tol <= 0, max_iter < 1,
+ * shared memory), ECONVERGE (not converged; the state is unchanged), ECUDA. */
+int vfps_haissinski(vfps_handle* h, double tol, int32_t max_iter, int32_t* iterations);
 
 /* Number of steps taken so far. */
 int vfps_steps_done(vfps_handle* h, int64_t* steps);
@@ -282,6 +297,10 @@ int vfps_batch_pairing(vfps_batch* b, int32_t on);
  * (shared memory, tps dividing the tiles per instance); W = tps = 0 releases
  * it.  Results do not depend on the shape.  Errors: EINVAL. */
 int vfps_batch_pin_shape(vfps_batch* b, int32_t W, int32_t tps);
+
+/* vfps_haissinski for one batch slot (before or between vfps_batch_run
+ * calls).  Errors as vfps_haissinski. */
+int vfps_batch_haissinski(vfps_batch* b, int32_t slot, double tol, int32_t max_iter, int32_t* iterations);
 
 /* Free a slot (its memory returns to the budget). */
 int vfps_batch_remove(vfps_batch* b, int32_t slot);

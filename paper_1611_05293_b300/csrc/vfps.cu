@@ -29,6 +29,7 @@
 #include "vfps_kernels.cuh"
 #include "vfps_fast.cuh"
 #include "vfps_pair.cuh"
+#include "vfps_haissinski.cuh"
 
 namespace vfps {
 void impedance_table(int model, int M, double delta, double Pi, std::vector<std::complex<double>>& z);
@@ -822,6 +823,8 @@ int init_kernels()
     CU(set_smem_attr_one(step_kernel_f32x2<8, 1024>, lim));
     CU(set_smem_attr_one(step_kernel_f32x2<4, 1024>, lim));
     CU(set_smem_attr_one(step_kernel_f32x2<2, 1024>, lim));
+    CU(set_smem_attr_one(haissinski_kernel<float>, lim));
+    CU(set_smem_attr_one(haissinski_kernel<double>, lim));
     CU(cudaFuncSetAttribute(power_spectrum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)(3 * 8192 * sizeof(float2))));
     g_kernels_ready = 1;
@@ -855,6 +858,46 @@ int prologue(Instance& I, cudaStream_t s)
     if (rc) return rc;
     Group g = single_group(I);
     return launch_project(g, s);
+}
+
+// Haissinski start (vfps_haissinski.cuh): solve for rho_H in one CTA, and if
+// it converged write psi = rho_H(q) g(p) as the current state and recompute
+// the wake and kick table of that state.  The column-sum and profile buffers
+// are the solver's scratch; the moments buffer holds its two result words.
+template <typename T>
+int haissinski_t(Instance& I, cudaStream_t s, double tol, int max_iter, int32_t* iters)
+{
+    const size_t sm = vfps::haissinski_smem(I.M, I.n);
+    if ((long long)sm > device_smem_limit() - 1024) return VFPS_EINVAL;
+    int* info_d = reinterpret_cast<int*>(I.mom);
+    haissinski_kernel<T><<<1, 256, sm, s>>>((const Desc<T>*)I.ddesc, I.S, tol, max_iter, I.rho, I.colsum, info_d);
+    CU(cudaGetLastError());
+    int info[2] = {0, 0};
+    CU(cudaMemcpyAsync(info, info_d, sizeof(info), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (iters) *iters = info[0];
+    if (!info[1]) {
+        // the state is untouched; restore the profile buffers the solver used
+        const int rc = prologue(I, s);
+        return rc ? rc : VFPS_ECONVERGE;
+    }
+    DevState st{};
+    CU(cudaMemcpyAsync(&st, I.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    const int nb = (int)std::min<long long>(1024, ((long long)I.n * I.n + 255) / 256);
+    outer_state_kernel<T><<<nb, 256, 0, s>>>((const Desc<T>*)I.ddesc, I.rho, I.colsum);
+    CU(cudaGetLastError());
+    st.scale = 1.0;
+    st.ticket = 0;
+    CU(cudaMemcpyAsync(I.st, &st, sizeof(DevState), cudaMemcpyHostToDevice, s));
+    return prologue(I, s);
+}
+
+int instance_haissinski(Instance& I, cudaStream_t s, double tol, int32_t max_iter, int32_t* iters)
+{
+    if (!(tol > 0.0) || max_iter < 1) return VFPS_EINVAL;
+    return I.p.precision ? haissinski_t<double>(I, s, tol, max_iter, iters)
+                         : haissinski_t<float>(I, s, tol, max_iter, iters);
 }
 
 // Status word -> API code.  -100 - k: the debug build's index check k failed.
@@ -1011,6 +1054,7 @@ const char* vfps_strerror(int code)
     case VFPS_ENAN: return "non-finite or non-positive charge";
     case VFPS_EBUSY: return "capacity exhausted";
     case VFPS_EBOUNDS: return "index check failed (debug build)";
+    case VFPS_ECONVERGE: return "iteration did not converge";
     }
     return "unknown error";
 }
@@ -1170,6 +1214,13 @@ int vfps_set_state(vfps_handle* h, const double* psi)
     int rc = upload_psi(*h->I, psi, h->stream);
     if (rc) return rc;
     return prologue(*h->I, h->stream);
+}
+
+int vfps_haissinski(vfps_handle* h, double tol, int32_t max_iter, int32_t* iterations)
+{
+    if (!h) return VFPS_EINVAL;
+    CU(cudaStreamSynchronize(h->stream));
+    return instance_haissinski(*h->I, h->stream, tol, max_iter, iterations);
 }
 
 int vfps_steps_done(vfps_handle* h, int64_t* steps)
@@ -1913,6 +1964,13 @@ int vfps_batch_moments(vfps_batch* b, int32_t slot, double* out)
 {
     if (!b || slot < 0 || slot >= b->max_slots || !b->slots[slot]) return VFPS_EINVAL;
     return instance_moments(*b->slots[slot], b->stream, out);
+}
+
+int vfps_batch_haissinski(vfps_batch* b, int32_t slot, double tol, int32_t max_iter, int32_t* iterations)
+{
+    if (!b || slot < 0 || slot >= b->max_slots || !b->slots[slot]) return VFPS_EINVAL;
+    CU(cudaStreamSynchronize(b->stream));
+    return instance_haissinski(*b->slots[slot], b->stream, tol, max_iter, iterations);
 }
 
 int vfps_batch_remove(vfps_batch* b, int32_t slot)

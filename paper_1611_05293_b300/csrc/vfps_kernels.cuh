@@ -406,6 +406,48 @@ __device__ __forceinline__ typename C2<T>::type* fft_h(const typename C2<T>::typ
     return const_cast<T2*>(in);
 }
 
+// Spectral step of the wake (Sec. II.B Eq. wakepotential), on the M/2-point
+// transform Z of z_j = rho_2j + i rho_2j+1: for each pair of bins (k, H-k),
+// H = M/2, split Z into the transforms of the even and odd samples, form the
+// profile spectrum rho~_k = sk (E_k + w_k O_k) (w_k = exp(-2 pi i k/M)),
+// multiply by the impedance, store the power term 2 Re Z_k |rho~_k|^2 (of k
+// and H-k) in pterm[p] (if given), and fold the product back so that the
+// inverse M/2-point transform gives the wake at the even and odd nodes.  DC
+// and Nyquist carry no wake.  All threads of the block take part.
+template <typename T>
+__device__ __forceinline__ void wake_pair_pass(typename C2<T>::type* Z, const typename C2<T>::type* tw,
+                                               const typename C2<T>::type* zh, int H, T sk, double* pterm, int tid,
+                                               int nt)
+{
+    using T2 = typename C2<T>::type;
+    for (int p = tid; p <= H / 2; p += nt) {
+        T term = T(0);
+        if (p == 0) {
+            Z[0] = T2{T(0), T(0)};  // DC and Nyquist carry no wake
+        } else {
+            const int k = p, kk = H - p;
+            const T2 zk = Z[k], zkk = Z[kk];
+            const T2 E = {T(0.5) * (zk.x + zkk.x), T(0.5) * (zk.y - zkk.y)};
+            const T2 O = {T(0.5) * (zk.y + zkk.y), T(0.5) * (zkk.x - zk.x)};
+            const T2 w = tw[k];
+            const T2 WO = cmul(w, O);
+            const T2 rk = {sk * (E.x + WO.x), sk * (E.y + WO.y)};
+            const T2 rkk = {sk * (E.x - WO.x), sk * (WO.y - E.y)};
+            const T2 Zk = zh[k], Zkk = zh[kk];
+            const T2 Bk = cmul(Zk, rk), Bkk = cmul(Zkk, rkk);
+            term = T(2) * Zk.x * (rk.x * rk.x + rk.y * rk.y);
+            if (kk != k) term += T(2) * Zkk.x * (rkk.x * rkk.x + rkk.y * rkk.y);
+            const T2 S = {Bk.x + Bkk.x, Bk.y - Bkk.y};    // B_k + conj B_{H-k}
+            const T2 Df = {Bk.x - Bkk.x, Bk.y + Bkk.y};   // B_k - conj B_{H-k}
+            const T2 uD = cmulc(Df, w);                    // exp(+2 pi i k/M) * Df
+            const T2 iuD = {-uD.y, uD.x};
+            Z[k] = cadd(S, iuD);
+            if (kk != k) Z[kk] = T2{S.x - iuD.x, iuD.y - S.y};  // conj(S - i u Df)
+        }
+        if (pterm) pterm[p] = double(term);
+    }
+}
+
 template <typename T>
 __device__ void finalise(const Desc<T>& D, unsigned char* smem, int is_step)
 {
@@ -463,33 +505,7 @@ __device__ void finalise(const Desc<T>& D, unsigned char* smem, int is_step)
     const double sd = s_new * D.delta;        // rho_x = sd * cs_x
     const T sk = T(sd * D.delta);             // rho~_k = Delta * DFT(rho)_k = sk * X_k
 
-    // per pair (k, H-k): split, multiply by the impedance, power, fold back
-    for (int p = tid; p <= H / 2; p += nt) {
-        T term = T(0);
-        if (p == 0) {
-            Z[0] = T2{T(0), T(0)};  // DC and Nyquist carry no wake
-        } else {
-            const int k = p, kk = H - p;
-            const T2 zk = Z[k], zkk = Z[kk];
-            const T2 E = {T(0.5) * (zk.x + zkk.x), T(0.5) * (zk.y - zkk.y)};
-            const T2 O = {T(0.5) * (zk.y + zkk.y), T(0.5) * (zkk.x - zk.x)};
-            const T2 w = tw[k];
-            const T2 WO = cmul(w, O);
-            const T2 rk = {sk * (E.x + WO.x), sk * (E.y + WO.y)};
-            const T2 rkk = {sk * (E.x - WO.x), sk * (WO.y - E.y)};
-            const T2 Zk = zh[k], Zkk = zh[kk];
-            const T2 Bk = cmul(Zk, rk), Bkk = cmul(Zkk, rkk);
-            term = T(2) * Zk.x * (rk.x * rk.x + rk.y * rk.y);
-            if (kk != k) term += T(2) * Zkk.x * (rkk.x * rkk.x + rkk.y * rkk.y);
-            const T2 S = {Bk.x + Bkk.x, Bk.y - Bkk.y};    // B_k + conj B_{H-k}
-            const T2 Df = {Bk.x - Bkk.x, Bk.y + Bkk.y};   // B_k - conj B_{H-k}
-            const T2 uD = cmulc(Df, w);                    // exp(+2 pi i k/M) * Df
-            const T2 iuD = {-uD.y, uD.x};
-            Z[k] = cadd(S, iuD);
-            if (kk != k) Z[kk] = T2{S.x - iuD.x, iuD.y - S.y};  // conj(S - i u Df)
-        }
-        pterm[p] = double(term);
-    }
+    wake_pair_pass<T>(Z, tw, zh, H, sk, pterm, tid, nt);
     __syncthreads();
 
     // inverse transform; meanwhile one warp sums the power terms into red[1]

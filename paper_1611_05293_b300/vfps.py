@@ -16,7 +16,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libvfps.so")
 
-OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENAN, EBUSY, EBOUNDS = 0, -1, -2, -3, -4, -5, -6, -7
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENAN, EBUSY, EBOUNDS, ECONVERGE = 0, -1, -2, -3, -4, -5, -6, -7, -8
 IMPEDANCE_NONE, IMPEDANCE_FREE_SPACE, IMPEDANCE_PARALLEL_PLATES, IMPEDANCE_TABLE = 0, 1, 2, 3
 
 # every symbol include/vfps.h declares
@@ -29,6 +29,7 @@ EXPORTS = [
     "vfps_batch_destroy", "vfps_step_static", "vfps_batch_launches_per_step",
     "vfps_moments", "vfps_batch_moments", "vfps_batch_autotune", "vfps_batch_shapes",
     "vfps_batch_pin_shape", "vfps_power_spectrum", "vfps_batch_power_spectrum", "vfps_batch_pairing",
+    "vfps_haissinski", "vfps_batch_haissinski",
 ]
 
 
@@ -103,6 +104,8 @@ def lib() -> ctypes.CDLL:
         "vfps_batch_autotune": (ctypes.c_int, [_VP, _I32]),
         "vfps_batch_pin_shape": (ctypes.c_int, [_VP, _I32, _I32]),
         "vfps_batch_pairing": (ctypes.c_int, [_VP, _I32]),
+        "vfps_haissinski": (ctypes.c_int, [_VP, ctypes.c_double, _I32, ctypes.POINTER(_I32)]),
+        "vfps_batch_haissinski": (ctypes.c_int, [_VP, _I32, ctypes.c_double, _I32, ctypes.POINTER(_I32)]),
         "vfps_batch_shapes": (ctypes.c_int, [_VP, ctypes.POINTER(_I32), _I32, ctypes.POINTER(_I32)]),
         "vfps_csr_power": (ctypes.c_int, [_VP, _D, _I64, ctypes.POINTER(_I64)]),
         "vfps_charge_series": (ctypes.c_int, [_VP, _D, _I64, ctypes.POINTER(_I64)]),
@@ -242,6 +245,13 @@ class Simulation:
         n = self.params.n
         _check(lib().vfps_set_state(self._h, _dptr(_f64(psi, (n, n)))), "vfps_set_state")
 
+    def haissinski(self, tol: float = 1e-13, max_iter: int = 20000) -> int:
+        """Replace the state by the Haissinski equilibrium rho_H(q) g(p) of the
+        current impedance and S_csr, solved on the device; returns iterations."""
+        it = _I32()
+        _check(lib().vfps_haissinski(self._h, float(tol), int(max_iter), ctypes.byref(it)), "vfps_haissinski")
+        return it.value
+
     def steps_done(self) -> int:
         k = _I64()
         _check(lib().vfps_steps_done(self._h, ctypes.byref(k)), "vfps_steps_done")
@@ -356,6 +366,13 @@ class Batch:
         _check(lib().vfps_batch_take(self._b, slot, _dptr(ps), _dptr(rh), _dptr(pw), power_cap,
                                      ctypes.byref(npow), ctypes.byref(steps)), "vfps_batch_take")
         return {"psi": ps, "rho": rh, "power": pw[:npow.value].copy(), "steps": steps.value}
+
+    def haissinski(self, slot: int, tol: float = 1e-13, max_iter: int = 20000) -> int:
+        """vfps_haissinski for one slot; returns iterations."""
+        it = _I32()
+        _check(lib().vfps_batch_haissinski(self._b, int(slot), float(tol), int(max_iter), ctypes.byref(it)),
+               "vfps_batch_haissinski")
+        return it.value
 
     def remove(self, slot: int):
         _check(lib().vfps_batch_remove(self._b, slot), "vfps_batch_remove")
