@@ -331,7 +331,9 @@ def run_reference(args):
         pr = O.Params(n=n, steps_per_period=spp, beta=beta, s_csr=S)
         zr, zi = O.impedance(pr, 2, Pi)
         sims.append([pr, zr, zi, O.normalize(pr, W.noisy_gaussian(n, 1612, 1e-6))])
-    per_step = 2 if args.steps > 20 else 4   # bounded sample per timed step
+    # bounded sample per timed step, long enough that the oracle's per-call
+    # set-up does not dominate (about 40 ms per timed step on 16 cores)
+    per_step = 32 if args.steps > 20 else 64
     for _ in range(args.warmup):
         for s in sims:
             s[3], _, _ = O.run(s[0], s[1], s[2], s[3], 1)
