@@ -221,24 +221,29 @@ int device_smem_per_sm()
 // kernels also use a few bytes of static shared memory; keep 1 KB for it.
 // Batches take the widest width that fits: fewest CTAs and the least halo
 // re-read per column.  With latency set (one simulation on its own) a step
-// lasts as long as its slowest CTA, so the narrowest width is taken whose
-// CTAs still all fit on the device at once (one wave: ceil(n/W) <= SMs x
-// CTAs per SM, the latter limited by shared memory and by 32 CTAs per SM).
+// lasts as long as its slowest CTA plus the finaliser that the last CTA
+// runs with W x 32 threads: the widest width is taken whose grid still has
+// at least 0.4 x SMs CTAs (measured per step: N = 256 at W = 2 / 4 / 8 10.8 /
+// 10.2 / 10.8 us, N = 1024 at W = 4 / 8 20.5 / 19.5 us); for grids too small
+// for that, the narrowest whose CTAs all fit on the device at once (one wave:
+// ceil(n/W) <= SMs x CTAs per SM, limited by shared memory and 32 per SM).
 int pick_width(const vfps_params* p, bool fast, bool latency)
 {
     const long long lim = device_smem_limit() - 1024;
     const int widths[3] = {8, 4, 2};
-    int best = 0;
+    int best = 0, wide = 0;
     for (int W : widths) {
         const long long need = (long long)(fast ? fast_smem(p, W) : step_smem(p, W));
         if (need > lim) continue;
         if (!best) best = W;
         if (latency) {
+            const long long ctas = (p->n + W - 1) / W;
             const long long per_sm = std::min<long long>(32, device_smem_per_sm() / (need + 1024));
-            if ((p->n + W - 1) / W <= (long long)num_sms() * per_sm) best = W;
+            if (!wide && 5 * ctas >= 2LL * num_sms()) wide = W;
+            if (ctas <= (long long)num_sms() * per_sm) best = W;
         }
     }
-    return best;
+    return (latency && wide) ? wide : best;
 }
 
 // *fast is set when the FP32 register-blocked kernel applies and fits.
