@@ -160,10 +160,6 @@ __device__ __forceinline__ void rotate_block4(const float* __restrict__ ring, in
     lagrange2(ty23, wy23);
     lagrange2(tx01, wx01);
     lagrange2(tx23, wx23);
-    const float wy[4][4] = {{wy01[0].x, wy01[1].x, wy01[2].x, wy01[3].x},
-                            {wy01[0].y, wy01[1].y, wy01[2].y, wy01[3].y},
-                            {wy23[0].x, wy23[1].x, wy23[2].x, wy23[3].x},
-                            {wy23[0].y, wy23[1].y, wy23[2].y, wy23[3].y}};
     float2 acc01, acc23;
 #pragma unroll
     for (int a = 1; a < 5; ++a) {
@@ -172,14 +168,15 @@ __device__ __forceinline__ void rotate_block4(const float* __restrict__ ring, in
         const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
         const float4 q0 = ok ? cp[0] : z4, q1 = ok ? cp[1] : z4, q2 = ok ? cp[2] : z4;
         const float win[12] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, q2.x, q2.y, q2.z, q2.w};
-        float r[4];
+        // rows (0, 1) and (2, 3) as packed pairs: the same operations per row
+        float2 r01 = __fmul2_rn(wy01[0], f2(win[O], win[O + 1]));
+        float2 r23 = __fmul2_rn(wy23[0], f2(win[O + 2], win[O + 3]));
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            float v = wy[k][0] * win[O + k];
-            v = fmaf(wy[k][1], win[O + k + 1], v);
-            v = fmaf(wy[k][2], win[O + k + 2], v);
-            r[k] = fmaf(wy[k][3], win[O + k + 3], v);
+        for (int b = 1; b < 4; ++b) {
+            r01 = __ffma2_rn(wy01[b], f2(win[O + b], win[O + b + 1]), r01);
+            r23 = __ffma2_rn(wy23[b], f2(win[O + b + 2], win[O + b + 3]), r23);
         }
+        const float r[4] = {r01.x, r01.y, r23.x, r23.y};
         if (a == 1) {
             acc01 = __fmul2_rn(wx01[0], f2(r[0], r[1]));
             acc23 = __fmul2_rn(wx23[0], f2(r[2], r[3]));
