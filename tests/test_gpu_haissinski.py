@@ -24,21 +24,22 @@ def V():
     return vfps
 
 
-def oracle_start(n, spp, S, Pi):
-    op = O.Params(n=n, steps_per_period=spp, beta=1e-2, s_csr=S)
+def oracle_start(n, spp, S, Pi, pad=2):
+    op = O.Params(n=n, steps_per_period=spp, beta=1e-2, s_csr=S, pad_factor=pad)
     zr, zi = O.impedance(op, 2, Pi)
     return H.profile(op, zr, zi), H.density(op, zr, zi)
 
 
-@pytest.mark.parametrize("n,precision,S,Pi,tol", [(64, 1, 0.3, 2.0, 1e-10), (100, 1, 0.6, 1.0, 1e-10),
-                                                  (256, 0, 0.6, 1.0, 2e-6), (128, 0, 0.4, 3.0, 2e-6)])
-def test_device_haissinski_matches_oracle(V, n, precision, S, Pi, tol):
+@pytest.mark.parametrize("n,precision,S,Pi,tol,pad", [(64, 1, 0.3, 2.0, 1e-10, 2), (100, 1, 0.6, 1.0, 1e-10, 2),
+                                                      (256, 0, 0.6, 1.0, 2e-6, 2), (128, 0, 0.4, 3.0, 2e-6, 2),
+                                                      (64, 1, 0.5, 2.0, 1e-10, 8), (1024, 0, 0.5, 2.0, 2e-6, 2)])
+def test_device_haissinski_matches_oracle(V, n, precision, S, Pi, tol, pad):
     spp = 500
-    sim = V.Simulation(V.Params(n=n, steps_per_period=spp, beta=1e-2, precision=precision))
+    sim = V.Simulation(V.Params(n=n, steps_per_period=spp, beta=1e-2, precision=precision, pad_factor=pad))
     sim.set_impedance(V.IMPEDANCE_PARALLEL_PLATES, Pi, S)
     iters = sim.haissinski(tol=1e-13)
     assert 1 < iters < 20000
-    rho_ref, psi_ref = oracle_start(n, spp, S, Pi)
+    rho_ref, psi_ref = oracle_start(n, spp, S, Pi, pad)
     rho = sim.profile()
     psi = sim.get_state()
     sim.close()
