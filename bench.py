@@ -484,7 +484,8 @@ def main():
                                  if MEASURED_TRAFFIC_PER_LAUNCH and args.instances == 512 and n == 256 else None),
                      "traffic_unit": "DRAM bytes per step (all launches of the step, ncu)",
                      "algorithmic_bytes_per_step": 8 * cells_step,
-                     "peak_kind": peak_kind, "algorithmic_bytes_per_cell": 8},
+                     "peak_kind": peak_kind, "algorithmic_bytes_per_cell": 8,
+                     "frac_vs_nominal_8tbs": achieved / 8000.0},
         "gpu_launches": args.steps * launches,
         "launches_per_step": launches,
         "launch_shapes": shapes,
