@@ -378,6 +378,8 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the serving / C3 / C5 side measurements")
     ap.add_argument("--shape", default="", help="W,tps: fixed batch launch shape (profiling runs)")
     ap.add_argument("--pairing", action="store_true", help="pair kernel for simulations of one geometry")
+    ap.add_argument("--rotation", type=int, default=0, choices=[0, 1],
+                    help="1: the Manhattan rotation for the batched scan (profiling runs)")
     args = ap.parse_args()
     global PIN_SHAPE, PAIRING
     PAIRING = args.pairing
@@ -404,8 +406,8 @@ def main():
 
     # ---- batched scan (the headline)
     if not PIN_SHAPE:
-        calibrate(V, torch, stream, args.instances, n, spp, beta)
-    b = build_batch(V, args.instances, n, spp, beta, stream, rank=rank, world=world)
+        calibrate(V, torch, stream, args.instances, n, spp, beta, rotation=args.rotation)
+    b = build_batch(V, args.instances, n, spp, beta, stream, rotation=args.rotation, rank=rank, world=world)
     b.run(args.warmup)
     launches = b.launches_per_step()
     shapes = b.shapes()
@@ -472,7 +474,8 @@ def main():
         "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"batched N={n} parallel-plates scan, {args.instances} instances per GPU "
-                               f"(S in [0.2,1.5] x Pi in {{1,2,3}}), {spp} steps/period, FP32 psi + FP64 sums",
+                               f"(S in [0.2,1.5] x Pi in {{1,2,3}}), {spp} steps/period, FP32 psi + FP64 sums"
+                               + (", Manhattan rotation" if args.rotation else ""),
                    "instances": args.instances, "grid": n, "steps_per_period": spp, "beta": beta,
                    "l2": f"inputs larger than L2: state {2 * cells_step * 4 / 2**20:.0f} MiB > 126 MiB",
                    "parallelism": f"replicas x{world}"},
@@ -481,7 +484,8 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm,
                      "traffic": (MEASURED_TRAFFIC_PER_LAUNCH * launches
-                                 if MEASURED_TRAFFIC_PER_LAUNCH and args.instances == 512 and n == 256 else None),
+                                 if MEASURED_TRAFFIC_PER_LAUNCH and args.instances == 512 and n == 256
+                                 and not args.rotation else None),
                      "traffic_unit": "DRAM bytes per step (all launches of the step, ncu)",
                      "algorithmic_bytes_per_step": 8 * cells_step,
                      "peak_kind": peak_kind, "algorithmic_bytes_per_cell": 8,
