@@ -457,7 +457,10 @@ def main():
     # ---- end to end through the C ABI with host buffers
     t0 = time.perf_counter()
     bb = build_batch(V, args.instances, n, spp, beta, stream)
+    t_add = time.perf_counter()
     bb.run(args.steps)
+    bb.poll()  # waits for the run
+    t_run = time.perf_counter()
     outs = [bb.take(s, psi=True, rho=False) for s in range(args.instances)]
     torch.cuda.synchronize()
     e2e_dt = time.perf_counter() - t0
@@ -466,7 +469,8 @@ def main():
     d2h = sum(o["psi"].size * 8 + o["power"].size * 8 for o in outs) / args.steps
     e2e = {"value": args.instances * n * n * args.steps / e2e_dt, "unit": "cell-updates/s",
            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-           "what": "vfps_batch_add from host psi0 (fp64) + run + vfps_batch_take of psi and P(t), wall clock"}
+           "what": "vfps_batch_add from host psi0 (fp64) + run + vfps_batch_take of psi and P(t), wall clock",
+           "split_ms": {"add": 1e3 * (t_add - t0), "run": 1e3 * (t_run - t_add), "take": 1e3 * (t0 + e2e_dt - t_run)}}
 
     line = {
         "metric": "phase-space cell-updates/s", "value": value, "unit": "cell-updates/s",

@@ -30,7 +30,9 @@
  *  - host pointers are read or written before the call returns and stay
  *    owned by the caller; the library owns every device allocation;
  *  - a handle is not thread-safe; work is queued on the handle's stream;
- *  - calls that return data to the host synchronise that stream.
+ *  - calls that return data to the host synchronise that stream; state,
+ *    status and series move through a pinned staging buffer of the calling
+ *    thread (grown to the largest transfer, freed when the thread ends).
  */
 #ifndef VFPS_H
 #define VFPS_H

@@ -390,6 +390,45 @@ void destroy_instance(Instance* I)
     delete I;
 }
 
+// Pinned host staging for the state, status and series copies, one per host
+// thread (a thread's calls are sequential; threads do not share one), grown
+// to the largest transfer and released when the thread ends.  Pinned copies
+// skip the driver's pageable bounce buffer, and a buffer kept for the
+// thread's life takes no page faults.  Every user finishes with the staged
+// data (after a stream synchronisation) before it returns.
+struct HostStage {
+    unsigned char* p = nullptr;
+    size_t cap = 0;
+    unsigned char* get(size_t bytes)
+    {
+        if (bytes <= cap) return p;
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        cap = 0;
+        const size_t want = std::max(bytes, (size_t)1 << 20);
+        if (cudaHostAlloc((void**)&p, want, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            return nullptr;
+        }
+        cap = want;
+        return p;
+    }
+    ~HostStage()
+    {
+        if (p) cudaFreeHost(p);
+    }
+};
+
+HostStage& host_stage()
+{
+    thread_local HostStage st;
+    return st;
+}
+
+// Staged layout of a state transfer: the status word, then the psi buffer.
+constexpr size_t kStageHead = 256;
+
 // psi (host, n*n doubles) -> normalised device psi[parity]; the pending scale is 1.
 int upload_psi(Instance& I, const double* psi, cudaStream_t s)
 {
@@ -417,18 +456,25 @@ int upload_psi(Instance& I, const double* psi, cudaStream_t s)
     }
     if (!(sum > 0.0)) return VFPS_EINVAL;
     double inv = 1.0 / (d2 * sum);
-    size_t es = elem_size(&I.p);
-    std::vector<unsigned char> buf((size_t)n * I.ld * es, 0);
-    for (int i = 0; i < n; ++i)
+    const size_t es = elem_size(&I.p), bytes = (size_t)n * I.ld * es;
+    unsigned char* hs = host_stage().get(kStageHead + bytes);
+    if (!hs) return VFPS_ENOMEM;
+    DevState& st = *reinterpret_cast<DevState*>(hs);
+    CU(cudaMemcpyAsync(&st, I.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    unsigned char* buf = hs + kStageHead;
+    for (int i = 0; i < n; ++i) {
         for (int j = 0; j < n; ++j) {
             double v = src[(size_t)i * n + j] * inv;
-            if (es == 8) reinterpret_cast<double*>(buf.data())[(size_t)i * I.ld + j] = v;
-            else reinterpret_cast<float*>(buf.data())[(size_t)i * I.ld + j] = (float)v;
+            if (es == 8) reinterpret_cast<double*>(buf)[(size_t)i * I.ld + j] = v;
+            else reinterpret_cast<float*>(buf)[(size_t)i * I.ld + j] = (float)v;
         }
-    DevState st{};
-    CU(cudaMemcpyAsync(&st, I.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+        for (int j = n; j < I.ld; ++j) {  // row padding
+            if (es == 8) reinterpret_cast<double*>(buf)[(size_t)i * I.ld + j] = 0.0;
+            else reinterpret_cast<float*>(buf)[(size_t)i * I.ld + j] = 0.f;
+        }
+    }
     CU(cudaStreamSynchronize(s));
-    CU(cudaMemcpyAsync(I.psi[st.parity], buf.data(), buf.size(), cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(I.psi[st.parity], buf, bytes, cudaMemcpyHostToDevice, s));
     st.scale = 1.0;
     st.ticket = 0;
     CU(cudaMemcpyAsync(I.st, &st, sizeof(DevState), cudaMemcpyHostToDevice, s));
@@ -917,10 +963,11 @@ int status_code(int status)
 
 int read_status(Instance& I, cudaStream_t s)
 {
-    DevState st;
-    CU(cudaMemcpyAsync(&st, I.st, sizeof(st), cudaMemcpyDeviceToHost, s));
+    DevState* st = reinterpret_cast<DevState*>(host_stage().get(kStageHead));
+    if (!st) return VFPS_ENOMEM;
+    CU(cudaMemcpyAsync(st, I.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
-    return status_code(st.status);
+    return status_code(st->status);
 }
 
 // Move ring entries [drained, steps_queued) to the host series (synchronises).
@@ -930,39 +977,46 @@ int drain(Instance& I, cudaStream_t s)
     if (hi <= lo) return VFPS_OK;
     // only the new entries: [lo, hi) wraps around the ring at most once
     const long long cnt = hi - lo, mask = I.ring - 1;
-    const size_t old = I.pw.size();
-    I.pw.resize(old + cnt);
-    I.qw.resize(old + cnt);
+    double* hp = reinterpret_cast<double*>(host_stage().get(2 * sizeof(double) * cnt));
+    if (!hp) return VFPS_ENOMEM;
+    double* hq = hp + cnt;
     const long long a = lo & mask, first = std::min<long long>(cnt, I.ring - a);
-    CU(cudaMemcpyAsync(I.pw.data() + old, I.pring + a, sizeof(double) * first, cudaMemcpyDeviceToHost, s));
-    CU(cudaMemcpyAsync(I.qw.data() + old, I.qring + a, sizeof(double) * first, cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(hp, I.pring + a, sizeof(double) * first, cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(hq, I.qring + a, sizeof(double) * first, cudaMemcpyDeviceToHost, s));
     if (cnt > first) {
-        CU(cudaMemcpyAsync(I.pw.data() + old + first, I.pring, sizeof(double) * (cnt - first),
-                           cudaMemcpyDeviceToHost, s));
-        CU(cudaMemcpyAsync(I.qw.data() + old + first, I.qring, sizeof(double) * (cnt - first),
-                           cudaMemcpyDeviceToHost, s));
+        CU(cudaMemcpyAsync(hp + first, I.pring, sizeof(double) * (cnt - first), cudaMemcpyDeviceToHost, s));
+        CU(cudaMemcpyAsync(hq + first, I.qring, sizeof(double) * (cnt - first), cudaMemcpyDeviceToHost, s));
     }
     CU(cudaStreamSynchronize(s));
+    I.pw.insert(I.pw.end(), hp, hp + cnt);
+    I.qw.insert(I.qw.end(), hq, hq + cnt);
     I.drained = hi;
     return VFPS_OK;
 }
 
 int copy_state(Instance& I, cudaStream_t s, double* psi_out)
 {
-    int n = I.n;
-    DevState st;
-    CU(cudaMemcpyAsync(&st, I.st, sizeof(st), cudaMemcpyDeviceToHost, s));
+    const int n = I.n;
+    const size_t es = elem_size(&I.p), bytes = (size_t)n * I.ld * es;
+    unsigned char* hs = host_stage().get(kStageHead + bytes);
+    if (!hs) return VFPS_ENOMEM;
+    const DevState& st = *reinterpret_cast<const DevState*>(hs);
+    CU(cudaMemcpyAsync(hs, I.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
-    size_t es = elem_size(&I.p);
-    std::vector<unsigned char> buf((size_t)n * I.ld * es);
-    CU(cudaMemcpyAsync(buf.data(), I.psi[st.parity], buf.size(), cudaMemcpyDeviceToHost, s));
+    const unsigned char* buf = hs + kStageHead;
+    CU(cudaMemcpyAsync(hs + kStageHead, I.psi[st.parity], bytes, cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
-    for (int i = 0; i < n; ++i)
-        for (int j = 0; j < n; ++j) {
-            double v = es == 8 ? reinterpret_cast<double*>(buf.data())[(size_t)i * I.ld + j]
-                               : (double)reinterpret_cast<float*>(buf.data())[(size_t)i * I.ld + j];
-            psi_out[(size_t)i * n + j] = v * st.scale;
+    const double scale = st.scale;
+    for (int i = 0; i < n; ++i) {
+        double* o = psi_out + (size_t)i * n;
+        if (es == 8) {
+            const double* r = reinterpret_cast<const double*>(buf) + (size_t)i * I.ld;
+            for (int j = 0; j < n; ++j) o[j] = r[j] * scale;
+        } else {
+            const float* r = reinterpret_cast<const float*>(buf) + (size_t)i * I.ld;
+            for (int j = 0; j < n; ++j) o[j] = (double)r[j] * scale;
         }
+    }
     return status_code(st.status);
 }
 

@@ -284,6 +284,7 @@ class Batch:
                "vfps_batch_create")
         self._b = b
         self.params = {}
+        self.nsteps = {}   # slot -> upper bound on the steps it has taken (its P(t) length)
 
     @staticmethod
     def slot_bytes(params: Params) -> int:
@@ -302,6 +303,7 @@ class Batch:
         _check(lib().vfps_batch_add(self._b, ctypes.byref(params.c()), _dptr(psi), model, Pi, S_csr,
                                     _dptr(tab), int(nsteps), ctypes.byref(s)), "vfps_batch_add")
         self.params[s.value] = params
+        self.nsteps[s.value] = (int(nsteps), 0)
         return s.value
 
     def try_add(self, *a, **kw):
@@ -314,6 +316,10 @@ class Batch:
             raise
 
     def run(self, chunk_steps: int):
+        # every unfinished slot advances by up to chunk_steps, and never past
+        # its target: the bound holds whether or not the call succeeds
+        for k, (target, done) in self.nsteps.items():
+            self.nsteps[k] = (target, min(target, done + int(chunk_steps)))
         _check(lib().vfps_batch_run(self._b, int(chunk_steps)), "vfps_batch_run")
 
     def poll(self) -> list[int]:
@@ -361,6 +367,9 @@ class Batch:
         n = self.params[slot].n
         ps = np.empty((n, n)) if psi else None
         rh = np.empty(n) if rho else None
+        # a slot's series holds one value per step taken: a buffer of that
+        # bound (a huge one costs more in first-touch faults than the copy)
+        power_cap = min(power_cap, max(1, self.nsteps.get(slot, (0, power_cap))[1]))
         pw = np.empty(max(1, power_cap))
         npow, steps = _I64(), _I64()
         _check(lib().vfps_batch_take(self._b, slot, _dptr(ps), _dptr(rh), _dptr(pw), power_cap,
@@ -377,6 +386,7 @@ class Batch:
     def remove(self, slot: int):
         _check(lib().vfps_batch_remove(self._b, slot), "vfps_batch_remove")
         self.params.pop(slot, None)
+        self.nsteps.pop(slot, None)
 
     def usage(self):
         a, b = _I32(), _I64()
