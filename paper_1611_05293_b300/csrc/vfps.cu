@@ -448,12 +448,24 @@ int upload_psi(Instance& I, const double* psi, cudaStream_t s)
     // Interpolation overshoots leave small negative densities in evolved
     // states (Sec. IV.B), so only non-finite values and a non-positive total
     // charge are rejected.
-    double sum = 0.0;
-    for (size_t i = 0; i < (size_t)n * n; ++i) {
-        double v = src[i];
-        if (!std::isfinite(v)) return VFPS_EINVAL;
-        sum += v;
+    // eight interleaved partial sums: a single chain of dependent FP64 adds
+    // is bound by the add latency (n*n of them)
+    const size_t cells = (size_t)n * n;
+    double part[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    bool finite = true;
+    size_t i = 0;
+    for (; i + 8 <= cells; i += 8)
+        for (int k = 0; k < 8; ++k) {
+            const double v = src[i + k];
+            finite = finite && std::isfinite(v);
+            part[k] += v;
+        }
+    for (; i < cells; ++i) {
+        finite = finite && std::isfinite(src[i]);
+        part[0] += src[i];
     }
+    if (!finite) return VFPS_EINVAL;
+    const double sum = ((part[0] + part[1]) + (part[2] + part[3])) + ((part[4] + part[5]) + (part[6] + part[7]));
     if (!(sum > 0.0)) return VFPS_EINVAL;
     double inv = 1.0 / (d2 * sum);
     const size_t es = elem_size(&I.p), bytes = (size_t)n * I.ld * es;
@@ -486,6 +498,8 @@ int upload_psi(Instance& I, const double* psi, cudaStream_t s)
 // parameter scan reuses a few (model, M, Delta, Pi): keep the last 64.
 void cached_impedance(int model, int M, double delta, double Pi, std::vector<std::complex<double>>& z)
 {
+    static std::mutex mu;  // handles and batches may be driven from several threads
+    std::lock_guard<std::mutex> lk(mu);
     static std::map<std::tuple<int, int, double, double>, std::vector<std::complex<double>>> cache;
     static std::deque<std::tuple<int, int, double, double>> order;
     auto key = std::make_tuple(model, M, delta, model == 2 ? Pi : 0.0);
@@ -599,9 +613,9 @@ int create_instance(const vfps_params* p, const double* psi0, int ring, cudaStre
                 reinterpret_cast<float*>(buf.data())[2 * k + 1] = (float)s;
             }
         }
+        // a copy from pageable memory returns once the data is staged: buf may go
         if (cudaMemcpyAsync(I->tw, buf.data(), buf.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
             return VFPS_ECUDA;
-        if (cudaStreamSynchronize(s) != cudaSuccess) return VFPS_ECUDA;
     }
     {
         std::vector<int2> t(I->ntiles);
@@ -618,7 +632,6 @@ int create_instance(const vfps_params* p, const double* psi0, int ring, cudaStre
         DevState st{};
         st.scale = 1.0;
         if (cudaMemcpyAsync(I->st, &st, sizeof(st), cudaMemcpyHostToDevice, s) != cudaSuccess) return VFPS_ECUDA;
-        if (cudaStreamSynchronize(s) != cudaSuccess) return VFPS_ECUDA;
     }
     rc = upload_impedance(*I, 0, 0.0, 0.0, nullptr, s);
     if (rc) return rc;
