@@ -363,9 +363,17 @@ class Batch:
         _check(lib().vfps_batch_moments(self._b, int(slot), _dptr(out)), "vfps_batch_moments")
         return out
 
-    def take(self, slot: int, psi=True, rho=True, power_cap: int = 1 << 22):
+    def take(self, slot: int, psi=True, rho=True, power_cap: int = 1 << 22, psi_out=None):
+        """vfps_batch_take.  psi_out: an (n, n) C-contiguous float64 array to
+        write the state into (e.g. a row of one preallocated array for all
+        slots) instead of a new one."""
         n = self.params[slot].n
-        ps = np.empty((n, n)) if psi else None
+        if psi_out is not None:
+            if psi_out.shape != (n, n) or psi_out.dtype != np.float64 or not psi_out.flags.c_contiguous:
+                raise ValueError(f"psi_out must be a C-contiguous float64 array of shape {(n, n)}")
+            ps = psi_out
+        else:
+            ps = np.empty((n, n)) if psi else None
         rh = np.empty(n) if rho else None
         # a slot's series holds one value per step taken: a buffer of that
         # bound (a huge one costs more in first-touch faults than the copy)

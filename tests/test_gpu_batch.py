@@ -290,3 +290,29 @@ def test_balanced_grid_keeps_bits(V):
         for i in range(count):
             assert np.array_equal(r[i]["psi"], ref[i]["psi"]), (key, i)
             assert np.array_equal(r[i]["power"], ref[i]["power"]), (key, i)
+
+
+def test_take_into_preallocated_rows_and_series_bound(V):
+    """Batch.take with psi_out (rows of one array) returns the same state as
+    a fresh array; the P(t) series is complete whether the slot's target is
+    reached or far away (the binding sizes its series buffer by the steps a
+    slot can have taken), and a wrong psi_out is refused."""
+    n, spp = 48, 400
+    b = V.Batch(3)
+    slots = [b.add(V.Params(n=n, steps_per_period=spp, beta=1e-2), W.blobs(n, 7 + i),
+                   V.IMPEDANCE_PARALLEL_PLATES, 2.0, 0.6, nsteps=ns) for i, ns in enumerate((50, 1 << 40, 80))]
+    b.run(30)
+    b.run(40)
+    rows = np.empty((3, n, n))
+    got = [b.take(s, psi_out=rows[i]) for i, s in enumerate(slots)]
+    ref = [b.take(s) for s in slots]
+    for i, ns in enumerate((50, 70, 70)):
+        assert got[i]["steps"] == ns and got[i]["power"].shape == (ns,), i
+        assert got[i]["psi"] is rows[i] or np.shares_memory(got[i]["psi"], rows)
+        assert np.array_equal(rows[i], ref[i]["psi"]), i
+        assert np.array_equal(got[i]["power"], ref[i]["power"]), i
+    with pytest.raises(ValueError):
+        b.take(slots[0], psi_out=np.empty((n, n), dtype=np.float32))
+    with pytest.raises(ValueError):
+        b.take(slots[0], psi_out=np.empty((n, n + 1)))
+    b.close()
