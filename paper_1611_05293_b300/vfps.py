@@ -194,6 +194,7 @@ class Simulation:
         _check(lib().vfps_create(ctypes.byref(params.c()), _dptr(psi), _stream_ptr(stream),
                                  ctypes.byref(h)), "vfps_create")
         self._h = h
+        self._taken = {}  # series name -> values drained so far
 
     def set_impedance(self, model: int, Pi: float = 0.0, S_csr: float = 0.0, table=None):
         tab = None
@@ -224,9 +225,14 @@ class Simulation:
         return out
 
     def _series(self, fn, cap):
+        # one value per step since the series was last drained: a buffer of
+        # that size (a huge one costs more in first-touch faults than the copy)
+        taken = self._taken.get(fn.__name__, 0)
+        cap = min(cap, max(1, self.steps_done() - taken))
         out = np.empty(max(cap, 1))
         k = _I64()
         _check(fn(self._h, _dptr(out), cap, ctypes.byref(k)), fn.__name__)
+        self._taken[fn.__name__] = taken + k.value
         return out[:k.value].copy()
 
     def csr_power(self, cap: int = 1 << 22) -> np.ndarray:
