@@ -337,16 +337,20 @@ __device__ __forceinline__ void dft_r(typename C2<T>::type* v)
     }
 }
 
-// One Stockham pass of an H-point transform: sub-transforms of length Ns are
-// combined R at a time into length Ns*R.  tw[m] = exp(-2 pi i m/M), m < H.
+// One Stockham pass of an H-point transform: sub-transforms of length Ns =
+// 2^lgNs are combined R at a time into length Ns*R.  tw[m] = exp(-2 pi i
+// m/M), m < H.  Sizes are powers of two: shifts, not integer divisions (a
+// division by a run-time value is a long dependent chain, and one transform
+// runs in a single CTA, latency-bound).
 template <typename T, int R, bool INV>
 __device__ __forceinline__ void fft_pass(const typename C2<T>::type* __restrict__ src,
                                          typename C2<T>::type* __restrict__ dst,
-                                         const typename C2<T>::type* __restrict__ tw, int H, int Ns)
+                                         const typename C2<T>::type* __restrict__ tw, int H, int Ns, int lgNs)
 {
     using T2 = typename C2<T>::type;
-    const int Q = H / R;
-    const int mstep = 2 * H / (Ns * R);  // twiddle r*k of this pass is exp(-2 pi i r k mstep/M)
+    constexpr int lgR = R == 8 ? 3 : (R == 4 ? 2 : 1);
+    const int Q = H >> lgR;
+    const int mstep = (2 * H) >> (lgNs + lgR);  // twiddle r*k of this pass is exp(-2 pi i r k mstep/M)
     for (int j = threadIdx.x; j < Q; j += blockDim.x) {
         const int k = j & (Ns - 1);
         T2 v[R];
@@ -381,20 +385,22 @@ __device__ __forceinline__ typename C2<T>::type* fft_h(const typename C2<T>::typ
     const T2* in = src;
     T2* out = x;
     T2* other = y;
-    int Ns = 1;
+    int Ns = 1, lgNs = 0;
+    const int lgH = __ffs(H) - 1;
     bool first = true;
     while (Ns < H) {
-        const int left = H / Ns;
-        if (left >= 8) {
-            fft_pass<T, 8, INV>(in, out, tw, H, Ns);
-            Ns *= 8;
-        } else if (left == 4) {
-            fft_pass<T, 4, INV>(in, out, tw, H, Ns);
-            Ns *= 4;
+        const int lgleft = lgH - lgNs;
+        if (lgleft >= 3) {
+            fft_pass<T, 8, INV>(in, out, tw, H, Ns, lgNs);
+            lgNs += 3;
+        } else if (lgleft == 2) {
+            fft_pass<T, 4, INV>(in, out, tw, H, Ns, lgNs);
+            lgNs += 2;
         } else {
-            fft_pass<T, 2, INV>(in, out, tw, H, Ns);
-            Ns *= 2;
+            fft_pass<T, 2, INV>(in, out, tw, H, Ns, lgNs);
+            lgNs += 1;
         }
+        Ns = 1 << lgNs;
         if (first) after_first();
         first = false;
         __syncthreads();
