@@ -345,13 +345,14 @@ __device__ __forceinline__ void dft_r(typename C2<T>::type* v)
 template <typename T, int R, bool INV>
 __device__ __forceinline__ void fft_pass(const typename C2<T>::type* __restrict__ src,
                                          typename C2<T>::type* __restrict__ dst,
-                                         const typename C2<T>::type* __restrict__ tw, int H, int Ns, int lgNs)
+                                         const typename C2<T>::type* __restrict__ tw, int H, int Ns, int lgNs,
+                                         int t0 = threadIdx.x, int nthr = blockDim.x)
 {
     using T2 = typename C2<T>::type;
     constexpr int lgR = R == 8 ? 3 : (R == 4 ? 2 : 1);
     const int Q = H >> lgR;
     const int mstep = (2 * H) >> (lgNs + lgR);  // twiddle r*k of this pass is exp(-2 pi i r k mstep/M)
-    for (int j = threadIdx.x; j < Q; j += blockDim.x) {
+    for (int j = t0; j < Q; j += nthr) {
         const int k = j & (Ns - 1);
         T2 v[R];
 #pragma unroll
@@ -404,6 +405,57 @@ __device__ __forceinline__ typename C2<T>::type* fft_h(const typename C2<T>::typ
         if (first) after_first();
         first = false;
         __syncthreads();
+        in = out;
+        T2* t = out;
+        out = other;
+        other = t;
+    }
+    return const_cast<T2*>(in);
+}
+
+// The same transform on the first nthr threads of the block (whole warps),
+// which synchronise among themselves on named barrier 1, so that the other
+// warps can work meanwhile; every output is computed by the same operations
+// as in fft_h.  Returns the buffer that holds the result (fft_result gives it
+// to threads that did not take part).
+__device__ __forceinline__ int fft_passes(int H)
+{
+    int p = 0;
+    for (int lg = __ffs(H) - 1; lg > 0; lg -= (lg >= 3 ? 3 : lg)) ++p;
+    return p;
+}
+
+template <typename T2>
+__device__ __forceinline__ T2* fft_result(const T2* src, T2* x, T2* y, int H)
+{
+    const int p = fft_passes(H);
+    return p == 0 ? const_cast<T2*>(src) : ((p & 1) ? x : y);
+}
+
+template <typename T, bool INV>
+__device__ __forceinline__ typename C2<T>::type* fft_h_part(const typename C2<T>::type* src,
+                                                            typename C2<T>::type* x, typename C2<T>::type* y,
+                                                            const typename C2<T>::type* tw, int H, int nthr)
+{
+    using T2 = typename C2<T>::type;
+    const T2* in = src;
+    T2* out = x;
+    T2* other = y;
+    int lgNs = 0;
+    const int lgH = __ffs(H) - 1, t0 = threadIdx.x;
+    while (lgNs < lgH) {
+        const int lgleft = lgH - lgNs, Ns = 1 << lgNs;
+        if (lgleft >= 3) {
+            fft_pass<T, 8, INV>(in, out, tw, H, Ns, lgNs, t0, nthr);
+            lgNs += 3;
+        } else if (lgleft == 2) {
+            fft_pass<T, 4, INV>(in, out, tw, H, Ns, lgNs, t0, nthr);
+            lgNs += 2;
+        } else {
+            fft_pass<T, 2, INV>(in, out, tw, H, Ns, lgNs, t0, nthr);
+            lgNs += 1;
+        }
+        asm volatile("bar.sync 1, %0;" ::"r"(nthr) : "memory");
         in = out;
         T2* t = out;
         out = other;
@@ -495,16 +547,20 @@ __device__ void finalise(const Desc<T>& D, unsigned char* smem, int is_step)
     }
     __syncthreads();
 
-    // forward transform; meanwhile one warp sums the charge Q = Delta^2 sum cs
-    // into red[0] in FP64
-    // (the last warp: with H/8 <= 32 butterflies per pass it has no FFT work)
-    const int sum_warp = (nt >> 5) - 1;
-    T2* Z = fft_h<T, false>(bufB, bufA, bufB, tw, H, [&] {
-        if ((tid >> 5) == sum_warp) {
-            const double sum = warp_fixed_sum<double>(cs, n);
-            if ((tid & 31) == 0) red[0] = sum;
-        }
-    });
+    // forward transform on all warps but the last, which meanwhile sums the
+    // charge Q = Delta^2 sum cs into red[0] in FP64 (FP64 adds are slow on
+    // this GPU: the sum takes longer than a transform pass, so it runs beside
+    // the whole transform rather than inside one pass; a one-warp block runs
+    // the two in turn)
+    const int sum_warp = (nt >> 5) - 1, nfft = nt >= 64 ? nt - 32 : nt;
+    const bool fft_thread = nt < 64 || (tid >> 5) != sum_warp, sum_thread = (tid >> 5) == sum_warp;
+    T2* Z = fft_result<T2>(bufB, bufA, bufB, H);
+    if (fft_thread) fft_h_part<T, false>(bufB, bufA, bufB, tw, H, nfft);
+    if (sum_thread) {
+        const double sum = warp_fixed_sum<double>(cs, n);
+        if ((tid & 31) == 0) red[0] = sum;
+    }
+    __syncthreads();
     const double Q = D.delta * D.delta * red[0];
     const bool bad = !(Q > 0.0) || !isfinite(Q);
     const double s_new = (D.renorm && !bad) ? 1.0 / Q : 1.0;
@@ -514,14 +570,16 @@ __device__ void finalise(const Desc<T>& D, unsigned char* smem, int is_step)
     wake_pair_pass<T>(Z, tw, zh, H, sk, pterm, tid, nt);
     __syncthreads();
 
-    // inverse transform; meanwhile one warp sums the power terms into red[1]
-    // in FP64
-    T2* y = fft_h<T, true>(Z, Z == bufA ? bufB : bufA, Z, tw, H, [&] {
-        if ((tid >> 5) == sum_warp) {
-            const double sum = warp_fixed_sum<double>(pterm, H / 2 + 1);
-            if ((tid & 31) == 0) red[1] = sum;
-        }
-    });
+    // inverse transform likewise, beside the FP64 sum of the power terms into
+    // red[1]
+    T2* const Zo = Z == bufA ? bufB : bufA;
+    T2* y = fft_result<T2>(Z, Zo, Z, H);
+    if (fft_thread) fft_h_part<T, true>(Z, Zo, Z, tw, H, nfft);
+    if (sum_thread) {
+        const double sum = warp_fixed_sum<double>(pterm, H / 2 + 1);
+        if ((tid & 31) == 0) red[1] = sum;
+    }
+    __syncthreads();
     const T kpv = T(D.kick_per_v * D.dkappa);
     for (int x = tid; x < n; x += nt) {
         const T2 v = y[x >> 1];
