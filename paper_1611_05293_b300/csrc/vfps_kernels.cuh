@@ -548,8 +548,8 @@ __device__ void finalise(const Desc<T>& D, unsigned char* smem, int is_step)
     __syncthreads();
 
     // forward transform on all warps but the last, which meanwhile sums the
-    // charge Q = Delta^2 sum cs into red[0] in FP64 (FP64 adds are slow on
-    // this GPU: the sum takes longer than a transform pass, so it runs beside
+    // charge Q = Delta^2 sum cs into red[0] in FP64 (FP64 adds are slow on the
+    // B300: the sum takes longer than a transform pass, so it runs beside
     // the whole transform rather than inside one pass; a one-warp block runs
     // the two in turn)
     const int sum_warp = (nt >> 5) - 1, nfft = nt >= 64 ? nt - 32 : nt;
