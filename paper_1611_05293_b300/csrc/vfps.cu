@@ -231,18 +231,23 @@ int pick_width(const vfps_params* p, bool fast, bool latency)
 {
     const long long lim = device_smem_limit() - 1024;
     const int widths[3] = {8, 4, 2};
-    int best = 0, wide = 0;
+    int best = 0, wide = 0, four = 0;
     for (int W : widths) {
         const long long need = (long long)(fast ? fast_smem(p, W) : step_smem(p, W));
         if (need > lim) continue;
         if (!best) best = W;
+        if (W == 4) four = 4;
         if (latency) {
             const long long ctas = (p->n + W - 1) / W;
             const long long per_sm = std::min<long long>(32, device_smem_per_sm() / (need + 1024));
-            if (!wide && 5 * ctas >= 2LL * num_sms()) wide = W;
+            // FP32 kernel: never the 2-wide CTA for a lone simulation, whose
+            // last CTA then finalises with one transform warp (measured
+            // slower at every n from 48 to 384)
+            if (!wide && 5 * ctas >= 2LL * num_sms() && (!fast || W >= 4)) wide = W;
             if (ctas <= (long long)num_sms() * per_sm) best = W;
         }
     }
+    if (latency && fast && !wide && four) wide = four;
     return (latency && wide) ? wide : best;
 }
 
