@@ -38,13 +38,37 @@ sys.path.insert(0, ROOT)
 
 HBM_FALLBACK_GBS = 6400.0
 
-# DRAM bytes (read + write) of one launch of step_kernel_f32 on a 256-instance
-# N=256 group, from the ncu capture summarised in
-# profiles/step_kernel_f32_batched_n256.md (launch shape W=4, 16-tile strips, the
-# autotuner's choice); a step of the
-# 512-instance benchmark is two such launches.  Set to None whenever the kernel
-# changes until a new capture is taken.
-MEASURED_TRAFFIC_PER_LAUNCH = 95.5e6
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "step_kernel_f32_batched_n256.md")
+
+
+def kernel_source_digest() -> str:
+    """sha256 (16 hex digits) of the CUDA sources the step kernels are built from."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_1611_05293_b300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(f.encode() + b"\0" + fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic_per_launch():
+    """DRAM bytes (read + write) of one launch of the batched step kernel, from
+    the ncu summary of the headline kernel -- only if that capture was taken of
+    the kernel sources built now (its `kernel-sources` digest matches);
+    otherwise None."""
+    try:
+        kv = {}
+        for line in open(PROFILE_SUMMARY):
+            if line.startswith("<!-- ") and ":" in line:
+                k, v = line[5:].split("-->")[0].split(":", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("kernel-sources") == kernel_source_digest():
+            return float(kv["dram-bytes-per-launch"]), kv.get("launch-shape", "")
+    except (OSError, KeyError, ValueError):
+        pass
+    return None, ""
 
 
 def measured_peaks():
@@ -110,6 +134,19 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+def head_start(torch, stream, ms: float = 3.0):
+    """A few milliseconds of dense GEMMs on `stream`, queued right before the
+    first event of a timed region: the SMs are busy (and clocked up) while the
+    host queues the timed steps, so the region measures the steps and not the
+    GPU's wake-up from idle or the host's launch pace (measured: 20 steps
+    after a 0.3 s idle gap 149 us per step, after busy work 114, steady
+    state 113.5)."""
+    a = torch.randn(4096, 4096, device="cuda", dtype=torch.bfloat16)
+    with torch.cuda.stream(stream):
+        for _ in range(max(1, int(ms / 0.1))):  # ~0.1 ms per 4096^3 GEMM
+            torch.mm(a, a)
+
+
 def scan_points(count: int, rank: int = 0, world: int = 1):
     """(S, Pi) of this rank's `count` instances: ranks take consecutive,
     disjoint slices of one scan of count * world points (replicas, weak
@@ -165,6 +202,7 @@ def manhattan_scan(V, torch, stream, warmup, count=512, steps=200):
     b.run(warmup)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    head_start(torch, stream)
     e0.record(stream)
     b.run(steps)
     e1.record(stream)
@@ -235,6 +273,7 @@ def c5_single(V, torch, stream, warmup, steps=512):
     solo_warmup(sim, warmup)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    head_start(torch, stream)
     e0.record(stream)
     sim.step(steps)
     e1.record(stream)
@@ -256,6 +295,7 @@ def m6_rotation(V, torch, stream, warmup, steps=1024):
         solo_warmup(sim, warmup)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        head_start(torch, stream)
         e0.record(stream)
         sim.step(steps)
         e1.record(stream)
@@ -436,15 +476,16 @@ def main():
         calibrate(V, torch, stream, args.instances, n, spp, beta, rotation=args.rotation)
     e2e = measure_e2e(V, torch, args, n, spp, beta, stream) if rank == 0 else None
     b = build_batch(V, args.instances, n, spp, beta, stream, rotation=args.rotation, rank=rank, world=world)
-    b.run(args.warmup)
-    launches = b.launches_per_step()
-    shapes = b.shapes()
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
+        b.run(args.warmup)
+        launches = b.launches_per_step()
+        shapes = b.shapes()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        head_start(torch, stream)
         t0 = time.perf_counter()
         e0.record(stream)
         b.run(args.steps)
@@ -473,6 +514,7 @@ def main():
     torch.cuda.synchronize()
     p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     plain_steps = -(-max(args.steps, 256) // GRAPH_STEPS) * GRAPH_STEPS  # whole graphs
+    head_start(torch, stream)
     p0.record(stream)
     sim.step(plain_steps)
     p1.record(stream)
@@ -482,6 +524,11 @@ def main():
     plain = {"value": n * n * plain_steps / pdt, "unit": "cell-updates/s",
              "ms_per_step": 1e3 * pdt / plain_steps, "workload": "single simulation N=256 FP32, Pi=2, S=0.9"}
 
+    tpl, tshape = measured_traffic_per_launch()
+    shape_now = ",".join(f"{g['W']}x{g['tps']}" for g in shapes)
+    traffic, traffic_src = None, "no ncu capture of the kernel sources built now"
+    if tpl and args.instances == 512 and n == 256 and not args.rotation and not PAIRING and tshape == shape_now:
+        traffic, traffic_src = tpl * launches, "ncu capture of this kernel build and launch shape"
     line = {
         "metric": "phase-space cell-updates/s", "value": value, "unit": "cell-updates/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -497,10 +544,9 @@ def main():
         "batched_vs_plain": value / world / plain["value"],
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm,
-                     "traffic": (MEASURED_TRAFFIC_PER_LAUNCH * launches
-                                 if MEASURED_TRAFFIC_PER_LAUNCH and args.instances == 512 and n == 256
-                                 and not args.rotation else None),
+                     "traffic": traffic,
                      "traffic_unit": "DRAM bytes per step (all launches of the step, ncu)",
+                     "traffic_source": traffic_src,
                      "algorithmic_bytes_per_step": 8 * cells_step,
                      "peak_kind": peak_kind, "algorithmic_bytes_per_cell": 8,
                      "frac_vs_nominal_8tbs": achieved / 8000.0},

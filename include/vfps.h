@@ -194,7 +194,8 @@ int vfps_impedance_table(int model, int32_t n, double half_width, int32_t pad_fa
  * cudaMalloc's implicit synchronisation and failure path.
  *   psi_in:  device, n*n FP32 [q][p] row-major (any positive charge);
  *   psi_out: device, n*n FP32, distinct from psi_in; receives the next state
- *            normalised to charge 1 (as vfps_step with renormalize = 1);
+ *            normalised to charge 1 (as vfps_step with renormalize = 1; the
+ *            renormalize field of params is not used);
  *            both 16-byte aligned when n is a multiple of 4;
  *   model, Pi, S_csr: as in vfps_set_impedance (models 0-2);
  *   power_out: host, NULL or one double: P(psi_in); when given, the call

@@ -1362,14 +1362,25 @@ struct vfps_batch {
     bool autotune = true;
     bool pairing = false;             // vfps_batch_pairing: pair kernel for equal geometries
     int pin_W = 0, pin_tps = 0;       // vfps_batch_pin_shape: fixed shape of FP32 groups
+    // kGraphSteps steps of the current group layout (fork, every group's
+    // launches on its stream, join) captured as one CUDA graph; dropped
+    // whenever a layout changes
+    cudaGraphExec_t graph = nullptr;
 };
 
 namespace {
 
 long long remaining(const Instance* I) { return I->target - I->steps_queued; }
 
+void drop_graph(vfps_batch* b)
+{
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+}
+
 void free_groups(vfps_batch* b)
 {
+    drop_graph(b);
     if (b->gmem) cudaFree(b->gmem);
     b->gmem = nullptr;
     b->gbytes = 0;
@@ -1795,9 +1806,69 @@ int tune_step_done(vfps_batch* b)
         }
         g.cands.clear();
         g.cand_ms.clear();
+        drop_graph(b);
         if (!layout_group(b, g, choice.first, choice.second)) layout_group(b, g, choice.first, default_tps(g, choice.first));
         CU(cudaMemcpyAsync((unsigned char*)b->gmem + g.off_d, b->hbuf.data() + g.off_d, g.tab_bytes,
                            cudaMemcpyHostToDevice, b->stream));
+    }
+    return VFPS_OK;
+}
+
+// Queue k steps of every group: each group stream waits for the batch
+// stream (fork), runs its k launches, and the batch stream waits for all of
+// them again (join).  With timing, a group under tuning gets the layout of
+// its candidate and start/stop events around its launches.
+int enqueue_steps(vfps_batch* b, long long k, bool timing)
+{
+    cudaEvent_t fork = b->events.back();
+    CU(cudaEventRecord(fork, b->stream));
+    for (const Group& g : b->groups) CU(cudaStreamWaitEvent(g.stream, fork, 0));
+    for (Group& g : b->groups) {
+        if (!timing || g.cands.empty()) continue;
+        if (g.cand >= 0) {  // upload the layout of the candidate under test
+            const int cw = g.cands[g.cand].first;
+            if (!layout_group(b, g, cw, g.cands[g.cand].second)) layout_group(b, g, cw, default_tps(g, cw));
+            CU(cudaMemcpyAsync((unsigned char*)b->gmem + g.off_d, b->hbuf.data() + g.off_d, g.tab_bytes,
+                               cudaMemcpyHostToDevice, g.stream));
+        }
+        CU(cudaEventRecord(g.t0, g.stream));
+    }
+    for (long long s = 0; s < k; ++s)
+        for (const Group& g : b->groups) {
+            const int rc = launch_step(g, g.stream);
+            if (rc) return rc;
+        }
+    for (size_t i = 0; i < b->groups.size(); ++i) {
+        if (timing && !b->groups[i].cands.empty()) CU(cudaEventRecord(b->groups[i].t1, b->groups[i].stream));
+        CU(cudaEventRecord(b->events[i], b->groups[i].stream));
+        CU(cudaStreamWaitEvent(b->stream, b->events[i], 0));
+    }
+    return VFPS_OK;
+}
+
+// Capture kGraphSteps steps of the current layout (no group under tuning)
+// into the batch's graph, once per layout.
+int ensure_batch_graph(vfps_batch* b)
+{
+    if (b->graph) return VFPS_OK;
+    cudaGraph_t graph;
+    CU(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    const int rc = enqueue_steps(b, kGraphSteps, false);
+    const cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
+    if (rc) {
+        if (e == cudaSuccess) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) {
+        note_cuda_error(e, "cudaStreamEndCapture (batch)");
+        return VFPS_ECUDA;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&b->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+        b->graph = nullptr;
+        note_cuda_error(ei, "cudaGraphInstantiate (batch)");
+        return VFPS_ECUDA;
     }
     return VFPS_OK;
 }
@@ -1902,30 +1973,17 @@ int vfps_batch_run(vfps_batch* b, int64_t chunk_steps)
         bool tuning = false;
         for (const Group& g : b->groups) tuning = tuning || !g.cands.empty();
         if (tuning) k = std::min<long long>(k, kTuneSteps);
-        // fork: every group stream waits for the batch stream, runs its k
-        // steps, and the batch stream waits for all of them again
-        cudaEvent_t fork = b->events.back();
-        CU(cudaEventRecord(fork, b->stream));
-        for (const Group& g : b->groups) CU(cudaStreamWaitEvent(g.stream, fork, 0));
-        for (Group& g : b->groups) {
-            if (g.cands.empty()) continue;
-            if (g.cand >= 0) {  // upload the layout of the candidate under test
-                const int cw = g.cands[g.cand].first;
-                if (!layout_group(b, g, cw, g.cands[g.cand].second)) layout_group(b, g, cw, default_tps(g, cw));
-                CU(cudaMemcpyAsync((unsigned char*)b->gmem + g.off_d, b->hbuf.data() + g.off_d, g.tab_bytes,
-                                   cudaMemcpyHostToDevice, g.stream));
-            }
-            CU(cudaEventRecord(g.t0, g.stream));
-        }
-        for (long long s = 0; s < k; ++s)
-            for (const Group& g : b->groups) {
-                rc = launch_step(g, g.stream);
-                if (rc) return rc;
-            }
-        for (size_t i = 0; i < b->groups.size(); ++i) {
-            if (!b->groups[i].cands.empty()) CU(cudaEventRecord(b->groups[i].t1, b->groups[i].stream));
-            CU(cudaEventRecord(b->events[i], b->groups[i].stream));
-            CU(cudaStreamWaitEvent(b->stream, b->events[i], 0));
+        if (!tuning && k >= kGraphSteps) {
+            // whole graphs of kGraphSteps steps: one host call per graph
+            // instead of a fork, a launch per group and step, and a join
+            rc = ensure_batch_graph(b);
+            if (rc) return rc;
+            const long long ng = k / kGraphSteps;
+            for (long long i = 0; i < ng; ++i) CU(cudaGraphLaunch(b->graph, b->stream));
+            k = ng * kGraphSteps;
+        } else {
+            rc = enqueue_steps(b, k, true);
+            if (rc) return rc;
         }
         if (tuning) {
             rc = tune_step_done(b);
@@ -2222,6 +2280,7 @@ extern "C" int vfps_step_static(const vfps_params* params, int model, double Pi,
     // the simulation's buffers: caller's psi, scratch for everything else
     Instance I;
     I.p = *params;
+    I.p.renormalize = 1;  // psi_out is normalised to charge 1 whatever the caller's flag
     I.n = params->n;
     I.ld = params->n;
     I.M = M;
