@@ -134,6 +134,34 @@ int vfps_moments(vfps_handle* h, double* out);
  * EINVAL, ECUDA, ENAN. */
 int vfps_power_spectrum(vfps_handle* h, int32_t length, double* out);
 
+/* Record the bunch moments of the state every `every` steps (0: stop) as part
+ * of the step itself: on a recording step the step kernel also sums p psi and
+ * p^2 psi per column of the state it writes (FP32 lane partials, FP64 across
+ * lanes), and the finaliser forms {<q>, sigma_q, <p>, sigma_p} of that state
+ * (Sec. IV's bunch length and energy spread; <f> = sum f psi / sum psi over
+ * the nodes, as vfps_moments) in FP64 from those sums and the column sums the
+ * wake already needs -- no extra pass over psi.  States t >= 1 produced by
+ * later steps with t a multiple of `every` are recorded; the records move to
+ * the host with the CSR-power series.  A device ring of 32 bytes per ring
+ * entry is allocated on first use.  Synchronises (draining what was
+ * recorded so far).  Errors: EINVAL, ENOMEM, ECUDA. */
+int vfps_record_moments(vfps_handle* h, int32_t every);
+
+/* Drain the recorded moments: up to cap records of five doubles
+ * {t, <q>, sigma_q, <p>, sigma_p}, oldest first; *n_written gets the
+ * number of records.  Synchronises.  Errors: EINVAL, ECUDA, ENAN. */
+int vfps_moment_series(vfps_handle* h, double* out, int64_t cap, int64_t* n_written);
+
+/* Bursting spectrogram of the CSR-power series (Sec. IV.C: the Fourier
+ * transform of P(t) over successive windows), on the device: `count` windows
+ * of `length` values, `hop` steps apart, the last one ending at the newest
+ * entry of the series; each window as vfps_power_spectrum (mean removed,
+ * Hann window).  out (host): count x (length/2 + 1) doubles, oldest window
+ * first.  length: power of two, 16..8192; hop >= 1; the span length + (count
+ * - 1) hop at most the steps done and at most the ring size minus one.  One
+ * launch, one CTA per window.  Synchronises.  Errors: EINVAL, ECUDA, ENAN. */
+int vfps_spectrogram(vfps_handle* h, int32_t length, int32_t hop, int32_t count, double* out);
+
 /* Drain the CSR-power series: out[k] = P(psi_t) for the steps t taken since
  * the last drain, oldest first (P of the state each step started from).
  * Writes min(cap, pending) values and *n_written; values beyond cap stay
@@ -150,6 +178,24 @@ int vfps_get_state(vfps_handle* h, double* psi_out);
 /* Replace psi by host psi (n*n doubles, normalised to charge 1 by the
  * library) and recompute its wake; the step counter is kept.  Errors: EINVAL. */
 int vfps_set_state(vfps_handle* h, const double* psi);
+
+/* Checkpoint and resume (the paper restarts runs from result files, Sec.
+ * IV.C "adiabatic" scans; App. B option -i).  A checkpoint is the state
+ * exactly as the device holds it between two steps -- the stored psi with its
+ * pending renormalisation factor, the step count, the kick table and profile
+ * of the next step, and the CSR power and charge of the current step -- so a
+ * run resumed from it continues with the same bits as the uninterrupted run
+ * (vfps_set_state, in contrast, takes a normalised psi and recomputes the
+ * rest, which agrees only to rounding).  The loading handle must have been
+ * created with the same parameters and impedance (model, Pi, S_csr);
+ * anything else is refused with EINVAL.  After a load the step counter is the
+ * checkpoint's and the series start again at that step.  buf: host memory of
+ * at least vfps_checkpoint_bytes bytes, owned by the caller (raw bytes of this
+ * library build; not a portable file format).  Both synchronise.
+ * Errors: EINVAL, ECUDA, ENAN (the saved state had a bad charge). */
+int vfps_checkpoint_bytes(vfps_handle* h, int64_t* bytes);
+int vfps_save_checkpoint(vfps_handle* h, void* buf, int64_t bytes);
+int vfps_load_checkpoint(vfps_handle* h, const void* buf, int64_t bytes);
 
 /* Haissinski start (Appendix A names the equilibrium; Sec. II.B gives the
  * wake): replace the current state by psi = rho_H(q) g(p), with g the unit
@@ -234,12 +280,41 @@ int vfps_batch_add(vfps_batch* b, const vfps_params* params, const double* psi0,
                    int model, double Pi, double S_csr, const double* table_re_im,
                    int64_t nsteps, int32_t* slot);
 
+/* Add `count` simulations of one set of parameters at once (a scan): one
+ * host-to-device copy of all starting states, their charges summed and their
+ * values normalised and converted on the device, then each slot's impedance
+ * and wake -- the same states, bit for bit, as `count` vfps_batch_add calls.
+ *   psi0: host, count consecutive n*n row-major states (NULL: unit
+ *         Gaussians); pinned memory makes the copy run at link speed;
+ *   model: 0, 1 or 2 for every slot; Pi, S_csr: host, count values each;
+ *   slots: host, receives the count slot ids.
+ * All or nothing: on any error no slot is added.  Errors: EINVAL (a
+ * non-finite value or non-positive charge in any state, bad arguments),
+ * EBUSY (free slots or memory budget), ENOMEM, ECUDA. */
+int vfps_batch_add_many(vfps_batch* b, int32_t count, const vfps_params* params, const double* psi0,
+                        int model, const double* Pi, const double* S_csr, int64_t nsteps, int32_t* slots);
+
+/* Results of `count` slots at once: psi_out (host, may be NULL) receives the
+ * states back to back (n*n doubles each, in the order of `slots`), gathered
+ * and converted on the device and copied to the host in one transfer;
+ * power_out (host, may be NULL) row i (power_cap doubles) receives slot i's
+ * CSR-power series so far (as vfps_batch_take), n_power[i] its length.
+ * Synchronises.  Errors: EINVAL, ECUDA, ENAN. */
+int vfps_batch_take_many(vfps_batch* b, int32_t count, const int32_t* slots, double* psi_out,
+                         double* power_out, int64_t power_cap, int64_t* n_power);
+
 /* Bytes of device memory a slot with these parameters needs (for admission). */
 int64_t vfps_batch_slot_bytes(const vfps_params* params);
 
 /* Advance every unfinished slot by up to chunk_steps steps (asynchronous).
  * A slot stops exactly at its own nsteps. */
 int vfps_batch_run(vfps_batch* b, int64_t chunk_steps);
+
+/* Without blocking: *idle = 1 if every step and set-up queued on the batch
+ * so far has finished on the device, else 0 (a serving loop polls this while
+ * it admits arrivals; vfps_batch_add queues a new slot's set-up on its own
+ * stream and never waits for the chunk in flight).  Errors: EINVAL, ECUDA. */
+int vfps_batch_idle(vfps_batch* b, int32_t* idle);
 
 /* Synchronise; list the finished slots not yet removed.  Writes up to cap ids. */
 int vfps_batch_poll(vfps_batch* b, int32_t* done_slots, int32_t cap, int32_t* n_done);
@@ -258,6 +333,21 @@ int vfps_batch_moments(vfps_batch* b, int32_t slot, double* out);
 /* out (host, length/2 + 1 doubles): vfps_power_spectrum of a slot.  Errors:
  * EINVAL, ECUDA, ENAN. */
 int vfps_batch_power_spectrum(vfps_batch* b, int32_t slot, int32_t length, double* out);
+
+/* vfps_record_moments for one slot (the slot leaves the pair kernel while it
+ * records; its ring counts toward the batch's memory budget).  Errors as
+ * vfps_record_moments. */
+int vfps_batch_record_moments(vfps_batch* b, int32_t slot, int32_t every);
+
+/* The slot's moment records so far (five doubles each, as
+ * vfps_moment_series), up to cap, without consuming them.  Synchronises. */
+int vfps_batch_moment_series(vfps_batch* b, int32_t slot, double* out, int64_t cap, int64_t* n_written);
+
+/* vfps_spectrogram of several slots in one launch: out (host) holds nslots x
+ * count x (length/2 + 1) doubles, slot-major in the order of `slots`.  Every
+ * slot must have the span of steps.  Errors: EINVAL, ECUDA, ENAN. */
+int vfps_batch_spectrogram(vfps_batch* b, const int32_t* slots, int32_t nslots, int32_t length, int32_t hop,
+                           int32_t count, double* out);
 
 /* Autotuner of the batch's FP32 launch groups (on = 1, the default; 0 keeps
  * the built-in rules).  For a group of a configuration not seen before in the

@@ -298,6 +298,12 @@ struct Instance {
     int parity0 = 0;
     std::vector<double> pw, qw;   // drained series
     size_t pw_taken = 0, qw_taken = 0;
+    // moments recorded by the step's epilogue (vfps_record_moments)
+    int mom_every = 0;            // 0: off
+    double* mring = nullptr;      // ring entries x 4 doubles, allocated on first use
+    long long mdrained = 0;       // states t <= mdrained are on the host (or not recorded)
+    std::vector<double> mw;       // drained records: t, <q>, sigma_q, <p>, sigma_p
+    size_t mw_taken = 0;
 };
 
 size_t instance_bytes(const vfps_params* p, int ring, size_t* offs)
@@ -344,6 +350,9 @@ void fill_desc(Instance& I)
     d.kickw = (float4*)I.kickw;
     d.pring = I.pring;
     d.qring = I.qring;
+    d.mring = I.mring;
+    d.colmom = I.mom;  // the moments scratch (3n + 4 doubles) holds the 2n column sums
+    d.mom_every = I.mring ? I.mom_every : 0;
     d.st = I.st;
     d.n = I.n;
     d.ld = I.ld;
@@ -391,6 +400,7 @@ int upload_desc(Instance& I, cudaStream_t s)
 void destroy_instance(Instance* I)
 {
     if (!I) return;
+    if (I->mring) cudaFree(I->mring);
     if (I->dmem) cudaFree(I->dmem);
     delete I;
 }
@@ -434,69 +444,100 @@ HostStage& host_stage()
 // Staged layout of a state transfer: the status word, then the psi buffer.
 constexpr size_t kStageHead = 256;
 
-// psi (host, n*n doubles) -> normalised device psi[parity]; the pending scale is 1.
+// Unit Gaussian exp(-(q^2+p^2)/2) on an instance's grid (the default start).
+void unit_gaussian(const Instance& I, double* g)
+{
+    const int n = I.n;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            const double q = -I.p.half_width + i * I.delta, pp = -I.p.half_width + j * I.delta;
+            g[(size_t)i * n + j] = std::exp(-0.5 * (q * q + pp * pp));
+        }
+}
+
+// Host states -> normalised device states of `count` instances of one
+// precision: one copy of all of them to the device, FP64 charge sums there
+// (stage_sum_kernel), a check that every value is finite and every charge
+// positive, then psi[parity] = psi * 1/(Delta^2 sum) in the instance's type
+// with a pending scale of 1 (stage_store_kernel).  src: the states back to
+// back (n*n doubles each) or null for unit Gaussians.  Interpolation
+// overshoots leave small negative densities in evolved states (Sec. IV.B), so
+// only non-finite values and a non-positive total charge are refused
+// (EINVAL, before anything is stored).  Synchronises s.
+template <typename T>
+int upload_states_t(Instance* const* inst, int count, const double* src, cudaStream_t s)
+{
+    std::vector<long long> off((size_t)count);
+    long long total = 0;
+    for (int i = 0; i < count; ++i) {
+        off[(size_t)i] = total;
+        total += (long long)inst[i]->n * inst[i]->n;
+    }
+    std::vector<double> gauss;
+    if (!src) {
+        gauss.resize((size_t)total);
+        for (int i = 0; i < count; ++i) unit_gaussian(*inst[i], gauss.data() + off[(size_t)i]);
+        src = gauss.data();
+    }
+    const size_t vb = align_up((size_t)total * 8, kAlign), sb = align_up((size_t)count * 16, kAlign);
+    const size_t jb = sizeof(StateJob<T>) * (size_t)count;
+    std::vector<StateJob<T>> jobs((size_t)count);
+    for (int i = 0; i < count; ++i) {
+        const Instance& I = *inst[i];
+        jobs[(size_t)i] = StateJob<T>{{(T*)I.psi[0], (T*)I.psi[1]}, I.st, off[(size_t)i], I.delta * I.delta, I.n, I.ld};
+    }
+    unsigned char* d = nullptr;
+    CU(cudaMallocAsync((void**)&d, vb + sb + jb, s));
+    double* dv = (double*)d;
+    double* ds = (double*)(d + vb);
+    StateJob<T>* dj = (StateJob<T>*)(d + vb + sb);
+    std::vector<double> sums((size_t)count * 2);
+    cudaError_t e = cudaMemcpyAsync(dv, src, (size_t)total * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dj, jobs.data(), jb, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        stage_sum_kernel<<<count, 256, 0, s>>>(dv, (long long)inst[0]->n * inst[0]->n, ds);
+        e = cudaGetLastError();
+    }
+    // (one grid size per call: stage_sum_kernel strides by the first state's size)
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sums.data(), ds, sums.size() * 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    int rc = VFPS_OK;
+    if (e != cudaSuccess) {
+        note_cuda_error(e, "state upload");
+        rc = VFPS_ECUDA;
+    }
+    for (int i = 0; i < count && rc == VFPS_OK; ++i)
+        if (!(sums[2 * (size_t)i + 1] == 1.0) || !(sums[2 * (size_t)i] > 0.0)) rc = VFPS_EINVAL;
+    if (rc == VFPS_OK) {
+        int rows = 1;
+        while (rows < 64 && (long long)rows * 256 * 16 < (long long)inst[0]->n * inst[0]->ld) rows <<= 1;
+        stage_store_kernel<T><<<dim3((unsigned)rows, (unsigned)count), 256, 0, s>>>(dv, ds, dj);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            note_cuda_error(e, "state upload");
+            rc = VFPS_ECUDA;
+        }
+    }
+    cudaFreeAsync(d, s);
+    return rc;
+}
+
+int upload_states(Instance* const* inst, int count, const double* src, cudaStream_t s)
+{
+    if (count < 1) return VFPS_OK;
+    for (int i = 1; i < count; ++i)
+        if (inst[i]->p.precision != inst[0]->p.precision || inst[i]->n != inst[0]->n) return VFPS_EINVAL;
+    return inst[0]->p.precision ? upload_states_t<double>(inst, count, src, s)
+                                : upload_states_t<float>(inst, count, src, s);
+}
+
+// psi (host, n*n doubles, or null for the unit Gaussian) -> normalised device
+// psi[parity]; the pending scale is 1.
 int upload_psi(Instance& I, const double* psi, cudaStream_t s)
 {
-    int n = I.n;
-    double d2 = I.delta * I.delta;
-    std::vector<double> g;
-    const double* src = psi;
-    if (!psi) {
-        g.resize((size_t)n * n);
-        for (int i = 0; i < n; ++i)
-            for (int j = 0; j < n; ++j) {
-                double q = -I.p.half_width + i * I.delta, pp = -I.p.half_width + j * I.delta;
-                g[(size_t)i * n + j] = std::exp(-0.5 * (q * q + pp * pp));
-            }
-        src = g.data();
-    }
-    // Interpolation overshoots leave small negative densities in evolved
-    // states (Sec. IV.B), so only non-finite values and a non-positive total
-    // charge are rejected.
-    // eight interleaved partial sums: a single chain of dependent FP64 adds
-    // is bound by the add latency (n*n of them)
-    const size_t cells = (size_t)n * n;
-    double part[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    bool finite = true;
-    size_t i = 0;
-    for (; i + 8 <= cells; i += 8)
-        for (int k = 0; k < 8; ++k) {
-            const double v = src[i + k];
-            finite = finite && std::isfinite(v);
-            part[k] += v;
-        }
-    for (; i < cells; ++i) {
-        finite = finite && std::isfinite(src[i]);
-        part[0] += src[i];
-    }
-    if (!finite) return VFPS_EINVAL;
-    const double sum = ((part[0] + part[1]) + (part[2] + part[3])) + ((part[4] + part[5]) + (part[6] + part[7]));
-    if (!(sum > 0.0)) return VFPS_EINVAL;
-    double inv = 1.0 / (d2 * sum);
-    const size_t es = elem_size(&I.p), bytes = (size_t)n * I.ld * es;
-    unsigned char* hs = host_stage().get(kStageHead + bytes);
-    if (!hs) return VFPS_ENOMEM;
-    DevState& st = *reinterpret_cast<DevState*>(hs);
-    CU(cudaMemcpyAsync(&st, I.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
-    unsigned char* buf = hs + kStageHead;
-    for (int i = 0; i < n; ++i) {
-        for (int j = 0; j < n; ++j) {
-            double v = src[(size_t)i * n + j] * inv;
-            if (es == 8) reinterpret_cast<double*>(buf)[(size_t)i * I.ld + j] = v;
-            else reinterpret_cast<float*>(buf)[(size_t)i * I.ld + j] = (float)v;
-        }
-        for (int j = n; j < I.ld; ++j) {  // row padding
-            if (es == 8) reinterpret_cast<double*>(buf)[(size_t)i * I.ld + j] = 0.0;
-            else reinterpret_cast<float*>(buf)[(size_t)i * I.ld + j] = 0.f;
-        }
-    }
-    CU(cudaStreamSynchronize(s));
-    CU(cudaMemcpyAsync(I.psi[st.parity], buf, bytes, cudaMemcpyHostToDevice, s));
-    st.scale = 1.0;
-    st.ticket = 0;
-    CU(cudaMemcpyAsync(I.st, &st, sizeof(DevState), cudaMemcpyHostToDevice, s));
-    CU(cudaStreamSynchronize(s));
-    return VFPS_OK;
+    Instance* p = &I;
+    return upload_states(&p, 1, psi, s);
 }
 
 // Tables are costly for the shielded model (an Airy sum per frequency), and a
@@ -560,7 +601,7 @@ int upload_impedance(Instance& I, int model, double Pi, double S, const double* 
 }
 
 int create_instance(const vfps_params* p, const double* psi0, int ring, cudaStream_t s, Instance** out,
-                    bool latency = false)
+                    bool latency = false, bool upload = true)
 {
     int rc = check_params(p);
     if (rc) return rc;
@@ -640,8 +681,10 @@ int create_instance(const vfps_params* p, const double* psi0, int ring, cudaStre
     }
     rc = upload_impedance(*I, 0, 0.0, 0.0, nullptr, s);
     if (rc) return rc;
-    rc = upload_psi(*I, psi0, s);
-    if (rc) return rc;
+    if (upload) {
+        rc = upload_psi(*I, psi0, s);
+        if (rc) return rc;
+    }
     *out = I.release();
     return VFPS_OK;
 }
@@ -896,6 +939,8 @@ int init_kernels()
     CU(set_smem_attr_one(haissinski_kernel<double>, lim));
     CU(cudaFuncSetAttribute(power_spectrum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)(3 * 8192 * sizeof(float2))));
+    CU(cudaFuncSetAttribute(spectrogram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)(3 * 8192 * sizeof(float2))));
     g_kernels_ready = 1;
     return VFPS_OK;
 }
@@ -988,11 +1033,80 @@ int read_status(Instance& I, cudaStream_t s)
     return status_code(st->status);
 }
 
+// Move the moment records of states t in (mdrained, steps_queued] with t a
+// multiple of mom_every to the host (synchronises).  The ring holds the last
+// `ring` states, and the callers keep steps_queued - drained below that.
+int drain_moments(Instance& I, cudaStream_t s)
+{
+    const long long lo = I.mdrained + 1, hi = I.steps_queued;
+    if (!I.mring || I.mom_every <= 0 || hi < lo) {
+        I.mdrained = std::max(I.mdrained, hi);
+        return VFPS_OK;
+    }
+    const long long cnt = hi - lo + 1, mask = I.ring - 1;
+    double* hm = reinterpret_cast<double*>(host_stage().get(4 * sizeof(double) * cnt));
+    if (!hm) return VFPS_ENOMEM;
+    const long long a = lo & mask, first = std::min<long long>(cnt, I.ring - a);
+    CU(cudaMemcpyAsync(hm, I.mring + 4 * a, 4 * sizeof(double) * first, cudaMemcpyDeviceToHost, s));
+    if (cnt > first)
+        CU(cudaMemcpyAsync(hm + 4 * first, I.mring, 4 * sizeof(double) * (cnt - first), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    for (long long t = lo; t <= hi; ++t) {
+        if (t % I.mom_every) continue;
+        const double* r = hm + 4 * (t - lo);
+        I.mw.insert(I.mw.end(), {(double)t, r[0], r[1], r[2], r[3]});
+    }
+    I.mdrained = hi;
+    return VFPS_OK;
+}
+
+int drain(Instance& I, cudaStream_t s);
+
+// Turn the epilogue's moment records on every `every` steps (0: off).  Drains
+// what was recorded so far; allocates the ring on first use; the descriptor
+// is re-uploaded (callers that copy descriptors must refresh their copies).
+int set_moment_recording(Instance& I, cudaStream_t s, int every)
+{
+    if (every < 0) return VFPS_EINVAL;
+    CU(cudaStreamSynchronize(s));
+    int rc = drain(I, s);
+    if (rc) return rc;
+    if (every > 0 && !I.mring) {
+        if (dev_alloc((void**)&I.mring, sizeof(double) * 4 * (size_t)I.ring) != cudaSuccess) {
+            cudaGetLastError();
+            I.mring = nullptr;
+            return VFPS_ENOMEM;
+        }
+    }
+    I.mom_every = every;
+    I.mdrained = I.steps_queued;
+    rc = upload_desc(I, s);
+    if (rc) return rc;
+    CU(cudaStreamSynchronize(s));
+    return VFPS_OK;
+}
+
+// Up to cap records (5 doubles each) from the drained moment series.
+int64_t take_moments(Instance& I, double* out, int64_t cap, bool consume)
+{
+    const int64_t have = (int64_t)(I.mw.size() - I.mw_taken) / 5;
+    const int64_t k = std::min<int64_t>(cap, have);
+    std::memcpy(out, I.mw.data() + I.mw_taken, sizeof(double) * 5 * k);
+    if (consume) {
+        I.mw_taken += 5 * k;
+        if (I.mw_taken == I.mw.size()) {
+            I.mw.clear();
+            I.mw_taken = 0;
+        }
+    }
+    return k;
+}
+
 // Move ring entries [drained, steps_queued) to the host series (synchronises).
 int drain(Instance& I, cudaStream_t s)
 {
     long long lo = I.drained, hi = I.steps_queued;
-    if (hi <= lo) return VFPS_OK;
+    if (hi <= lo) return drain_moments(I, s);
     // only the new entries: [lo, hi) wraps around the ring at most once
     const long long cnt = hi - lo, mask = I.ring - 1;
     double* hp = reinterpret_cast<double*>(host_stage().get(2 * sizeof(double) * cnt));
@@ -1009,7 +1123,7 @@ int drain(Instance& I, cudaStream_t s)
     I.pw.insert(I.pw.end(), hp, hp + cnt);
     I.qw.insert(I.qw.end(), hq, hq + cnt);
     I.drained = hi;
-    return VFPS_OK;
+    return drain_moments(I, s);
 }
 
 int copy_state(Instance& I, cudaStream_t s, double* psi_out)
@@ -1078,6 +1192,47 @@ int instance_power_spectrum(Instance& I, cudaStream_t s, int L, double* out)
         return VFPS_ECUDA;
     }
     return read_status(I, s);
+}
+
+// Spectrogram of the CSR-power series of several instances (Sec. IV.C: the
+// Fourier transform of P(t) over successive windows): count windows of L
+// values, hop steps apart, the last ending at each instance's latest entry,
+// one CTA per (window, instance), one launch.  out: nslots x count x (L/2+1)
+// doubles.  Synchronises.
+int spectrogram(Instance* const* inst, int nslots, int L, int hop, int count, cudaStream_t s, double* out)
+{
+    if (!out || nslots < 1 || nslots > 65535 || L < 16 || L > 8192 || (L & (L - 1)) || hop < 1 || count < 1)
+        return VFPS_EINVAL;
+    const long long span = (long long)L + (long long)(count - 1) * hop;
+    std::vector<SpecSeries> tab((size_t)nslots);
+    for (int i = 0; i < nslots; ++i) {
+        const Instance& I = *inst[i];
+        if (span > I.ring - 1 || span > I.steps_queued) return VFPS_EINVAL;
+        tab[(size_t)i] = SpecSeries{I.pring, (long long)I.ring - 1, I.steps_queued - span};
+    }
+    const size_t rows = (size_t)nslots * count, outb = rows * (size_t)(L / 2 + 1) * sizeof(double);
+    const size_t tab_off = align_up(outb, kAlign), total = tab_off + sizeof(SpecSeries) * tab.size();
+    unsigned char* d = nullptr;
+    CU(cudaMallocAsync((void**)&d, total, s));
+    cudaError_t e = cudaMemcpyAsync(d + tab_off, tab.data(), sizeof(SpecSeries) * tab.size(),
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        spectrogram_kernel<<<dim3((unsigned)count, (unsigned)nslots), 256, (size_t)3 * L * sizeof(float2), s>>>(
+            (const SpecSeries*)(d + tab_off), L, hop, (double*)d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, d, outb, cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(d, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        note_cuda_error(e, "spectrogram");
+        return VFPS_ECUDA;
+    }
+    for (int i = 0; i < nslots; ++i) {
+        const int rc = read_status(*inst[i], s);
+        if (rc) return rc;
+    }
+    return VFPS_OK;
 }
 
 int instance_moments(Instance& I, cudaStream_t s, double* out)
@@ -1241,6 +1396,29 @@ int vfps_moments(vfps_handle* h, double* out)
     return instance_moments(*h->I, h->stream, out);
 }
 
+int vfps_record_moments(vfps_handle* h, int32_t every)
+{
+    if (!h || every < 0) return VFPS_EINVAL;
+    return set_moment_recording(*h->I, h->stream, every);
+}
+
+int vfps_moment_series(vfps_handle* h, double* out, int64_t cap, int64_t* n_written)
+{
+    if (!h || !n_written || cap < 0 || (cap > 0 && !out)) return VFPS_EINVAL;
+    Instance& I = *h->I;
+    int rc = drain(I, h->stream);
+    if (rc) return rc;
+    *n_written = take_moments(I, out, cap, true);
+    return read_status(I, h->stream);
+}
+
+int vfps_spectrogram(vfps_handle* h, int32_t length, int32_t hop, int32_t count, double* out)
+{
+    if (!h) return VFPS_EINVAL;
+    Instance* I = h->I;
+    return spectrogram(&I, 1, length, hop, count, h->stream, out);
+}
+
 int vfps_profile(vfps_handle* h, double* rho_out)
 {
     if (!h || !rho_out) return VFPS_EINVAL;
@@ -1291,6 +1469,104 @@ int vfps_set_state(vfps_handle* h, const double* psi)
     int rc = upload_psi(*h->I, psi, h->stream);
     if (rc) return rc;
     return prologue(*h->I, h->stream);
+}
+
+// Checkpoint: the state exactly as the device holds it between steps.
+struct vfps_checkpoint_head {
+    char magic[8];          // "VFPSCKP1"
+    vfps_params params;     // must match the loading handle's
+    int32_t model, pad0;
+    double Pi, S;           // impedance of the run (must match)
+    int32_t n, ld, M, es;
+    DevState st;            // pending scale, step count, parity (ticket 0)
+    double p_t, q_t;        // ring entries of step t: P(psi_t), charge of the step that made psi_t
+};
+
+static size_t checkpoint_bytes(const Instance& I)
+{
+    const size_t es = elem_size(&I.p);
+    return sizeof(vfps_checkpoint_head) + (size_t)I.n * I.ld * es + (size_t)I.n * es + (size_t)I.n * 32 +
+           (size_t)I.n * 8;
+}
+
+int vfps_checkpoint_bytes(vfps_handle* h, int64_t* bytes)
+{
+    if (!h || !bytes) return VFPS_EINVAL;
+    *bytes = (int64_t)checkpoint_bytes(*h->I);
+    return VFPS_OK;
+}
+
+int vfps_save_checkpoint(vfps_handle* h, void* buf, int64_t bytes)
+{
+    if (!h || !buf || bytes < (int64_t)checkpoint_bytes(*h->I)) return VFPS_EINVAL;
+    Instance& I = *h->I;
+    const size_t es = elem_size(&I.p);
+    unsigned char* o = (unsigned char*)buf;
+    vfps_checkpoint_head hd{};
+    std::memcpy(hd.magic, "VFPSCKP1", 8);
+    hd.params = I.p;
+    hd.model = I.model;
+    hd.Pi = I.Pi;
+    hd.S = I.S;
+    hd.n = I.n;
+    hd.ld = I.ld;
+    hd.M = I.M;
+    hd.es = (int32_t)es;
+    CU(cudaMemcpyAsync(&hd.st, I.st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    const long long t = hd.st.t, mask = I.ring - 1;
+    CU(cudaMemcpyAsync(&hd.p_t, I.pring + (t & mask), sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaMemcpyAsync(&hd.q_t, I.qring + ((t - 1) & mask), sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    size_t off = sizeof(hd);
+    CU(cudaMemcpyAsync(o + off, I.psi[hd.st.parity], (size_t)I.n * I.ld * es, cudaMemcpyDeviceToHost, h->stream));
+    off += (size_t)I.n * I.ld * es;
+    CU(cudaMemcpyAsync(o + off, I.kick, (size_t)I.n * es, cudaMemcpyDeviceToHost, h->stream));
+    off += (size_t)I.n * es;
+    CU(cudaMemcpyAsync(o + off, I.kickw, (size_t)I.n * 32, cudaMemcpyDeviceToHost, h->stream));
+    off += (size_t)I.n * 32;
+    CU(cudaMemcpyAsync(o + off, I.rho, (size_t)I.n * 8, cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    hd.st.ticket = 0;
+    std::memcpy(o, &hd, sizeof(hd));
+    return status_code(hd.st.status);
+}
+
+int vfps_load_checkpoint(vfps_handle* h, const void* buf, int64_t bytes)
+{
+    if (!h || !buf || bytes < (int64_t)sizeof(vfps_checkpoint_head)) return VFPS_EINVAL;
+    Instance& I = *h->I;
+    vfps_checkpoint_head hd;
+    std::memcpy(&hd, buf, sizeof(hd));
+    const size_t es = elem_size(&I.p);
+    if (std::memcmp(hd.magic, "VFPSCKP1", 8) || std::memcmp(&hd.params, &I.p, sizeof(vfps_params)) ||
+        hd.model != I.model || hd.Pi != I.Pi || hd.S != I.S || hd.n != I.n || hd.ld != I.ld || hd.M != I.M ||
+        hd.es != (int32_t)es || bytes < (int64_t)checkpoint_bytes(I) || hd.st.parity < 0 || hd.st.parity > 1 ||
+        hd.st.t < 0)
+        return VFPS_EINVAL;
+    CU(cudaStreamSynchronize(h->stream));
+    const unsigned char* in = (const unsigned char*)buf;
+    size_t off = sizeof(hd);
+    CU(cudaMemcpyAsync(I.psi[hd.st.parity], in + off, (size_t)I.n * I.ld * es, cudaMemcpyHostToDevice, h->stream));
+    off += (size_t)I.n * I.ld * es;
+    CU(cudaMemcpyAsync(I.kick, in + off, (size_t)I.n * es, cudaMemcpyHostToDevice, h->stream));
+    off += (size_t)I.n * es;
+    CU(cudaMemcpyAsync(I.kickw, in + off, (size_t)I.n * 32, cudaMemcpyHostToDevice, h->stream));
+    off += (size_t)I.n * 32;
+    CU(cudaMemcpyAsync(I.rho, in + off, (size_t)I.n * 8, cudaMemcpyHostToDevice, h->stream));
+    const long long t = hd.st.t, mask = I.ring - 1;
+    CU(cudaMemcpyAsync(I.pring + (t & mask), &hd.p_t, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CU(cudaMemcpyAsync(I.qring + ((t - 1) & mask), &hd.q_t, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    DevState st = hd.st;
+    st.ticket = 0;
+    CU(cudaMemcpyAsync(I.st, &st, sizeof(st), cudaMemcpyHostToDevice, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    // the host bookkeeping restarts at step t: series drained from there on
+    I.steps_queued = I.drained = I.mdrained = t;
+    I.pw.clear();
+    I.qw.clear();
+    I.mw.clear();
+    I.pw_taken = I.qw_taken = I.mw_taken = 0;
+    return status_code(st.status);
 }
 
 int vfps_haissinski(vfps_handle* h, double tol, int32_t max_iter, int32_t* iterations)
@@ -1366,6 +1642,11 @@ struct vfps_batch {
     // launches on its stream, join) captured as one CUDA graph; dropped
     // whenever a layout changes
     cudaGraphExec_t graph = nullptr;
+    // admissions set up new slots (upload, prologue) on their own stream, so
+    // that a vfps_batch_add never waits for the chunk in flight; the batch
+    // stream waits for that set-up before its next work
+    cudaStream_t adm = nullptr;
+    cudaEvent_t adm_ev = nullptr;
 };
 
 namespace {
@@ -1639,7 +1920,7 @@ int rebuild_groups(vfps_batch* b)
         std::vector<Instance*> single;
         std::vector<std::vector<Instance*>> sigs;
         for (Instance* I : kv.second) {
-            if (!(b->pairing && I->fast && pair_eligible(&I->p) &&
+            if (!(b->pairing && I->fast && I->mom_every == 0 && pair_eligible(&I->p) &&
                   (long long)pair_smem(&I->p, 2) <= device_smem_limit() - 1024)) {
                 single.push_back(I);
                 continue;
@@ -1921,16 +2202,23 @@ int vfps_batch_add(vfps_batch* b, const vfps_params* params, const double* psi0,
     if (b->budget > 0 && b->used + need > b->budget) return VFPS_EBUSY;
     size_t fr = 0, tot = 0;
     if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && (long long)fr < need + (64ll << 20)) return VFPS_EBUSY;
-    CU(cudaStreamSynchronize(b->stream));
     rc = init_kernels();
     if (rc) return rc;
+    if (!b->adm) {
+        CU(cudaStreamCreateWithFlags(&b->adm, cudaStreamNonBlocking));
+        CU(cudaEventCreateWithFlags(&b->adm_ev, cudaEventDisableTiming));
+    }
     Instance* I = nullptr;
-    rc = create_instance(params, psi0, kRingDefault / 2, b->stream, &I);
+    rc = create_instance(params, psi0, kRingDefault / 2, b->adm, &I);
     if (rc) return rc;
     I->target = nsteps;
-    rc = upload_impedance(*I, model, Pi, S_csr, table, b->stream);
-    if (rc == VFPS_OK) rc = prologue(*I, b->stream);
+    rc = upload_impedance(*I, model, Pi, S_csr, table, b->adm);
+    if (rc == VFPS_OK) rc = prologue(*I, b->adm);
+    if (rc == VFPS_OK && (cudaEventRecord(b->adm_ev, b->adm) != cudaSuccess ||
+                          cudaStreamWaitEvent(b->stream, b->adm_ev, 0) != cudaSuccess))
+        rc = VFPS_ECUDA;
     if (rc) {
+        cudaStreamSynchronize(b->adm);
         destroy_instance(I);
         return rc;
     }
@@ -1996,6 +2284,182 @@ int vfps_batch_run(vfps_batch* b, int64_t chunk_steps)
         }
         chunk_steps -= k;
     }
+    return VFPS_OK;
+}
+
+int vfps_batch_add_many(vfps_batch* b, int32_t count, const vfps_params* params, const double* psi0, int model,
+                        const double* Pi, const double* S_csr, int64_t nsteps, int32_t* slots)
+{
+    if (!b || count < 1 || !Pi || !S_csr || !slots || nsteps < 0 || model < 0 || model > 2) return VFPS_EINVAL;
+    int rc = check_params(params);
+    if (rc) return rc;
+    std::vector<int> free_slots;
+    for (int i = 0; i < b->max_slots && (int)free_slots.size() < count; ++i)
+        if (!b->slots[i]) free_slots.push_back(i);
+    if ((int)free_slots.size() < count) return VFPS_EBUSY;
+    size_t offs[15];
+    const long long need = (long long)instance_bytes(params, kRingDefault / 2, offs) * count;
+    if (b->budget > 0 && b->used + need > b->budget) return VFPS_EBUSY;
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && (long long)fr < need + (64ll << 20)) return VFPS_EBUSY;
+    for (int i = 0; i < count; ++i)
+        if ((model == 2 && !(Pi[i] > 0.0)) || !std::isfinite(S_csr[i])) return VFPS_EINVAL;
+    rc = init_kernels();
+    if (rc) return rc;
+    if (!b->adm) {
+        CU(cudaStreamCreateWithFlags(&b->adm, cudaStreamNonBlocking));
+        CU(cudaEventCreateWithFlags(&b->adm_ev, cudaEventDisableTiming));
+    }
+    std::vector<Instance*> made;
+    auto fail = [&](int code) {
+        cudaStreamSynchronize(b->adm);
+        for (Instance* I : made) destroy_instance(I);
+        return code;
+    };
+    for (int i = 0; i < count; ++i) {
+        Instance* I = nullptr;
+        rc = create_instance(params, nullptr, kRingDefault / 2, b->adm, &I, false, false);
+        if (rc) return fail(rc);
+        I->target = nsteps;
+        made.push_back(I);
+    }
+    rc = upload_states(made.data(), count, psi0, b->adm);
+    for (int i = 0; i < count && rc == VFPS_OK; ++i) {
+        rc = upload_impedance(*made[(size_t)i], model, Pi[i], S_csr[i], nullptr, b->adm);
+        if (rc == VFPS_OK) rc = prologue(*made[(size_t)i], b->adm);
+    }
+    if (rc == VFPS_OK && (cudaEventRecord(b->adm_ev, b->adm) != cudaSuccess ||
+                          cudaStreamWaitEvent(b->stream, b->adm_ev, 0) != cudaSuccess))
+        rc = VFPS_ECUDA;
+    if (rc) return fail(rc);
+    for (int i = 0; i < count; ++i) {
+        b->slots[(size_t)free_slots[(size_t)i]] = made[(size_t)i];
+        b->used += (long long)made[(size_t)i]->dbytes;
+        slots[i] = free_slots[(size_t)i];
+    }
+    b->dirty = true;
+    return VFPS_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Queue the gather of the states of one precision among inst (FP64 values
+// at off[i] of the staged block d); the job table goes to d + job_off.
+template <typename T>
+int take_states_t(std::vector<Instance*>& inst, const std::vector<long long>& off, unsigned char* d,
+                  size_t job_off, cudaStream_t s)
+{
+    std::vector<StateJob<T>> jobs;
+    for (size_t i = 0; i < inst.size(); ++i) {
+        const Instance& I = *inst[i];
+        if ((I.p.precision != 0) != (sizeof(T) == 8)) continue;
+        jobs.push_back(StateJob<T>{{(T*)I.psi[0], (T*)I.psi[1]}, I.st, off[i], 0.0, I.n, I.ld});
+    }
+    if (jobs.empty()) return VFPS_OK;
+    StateJob<T>* dj = (StateJob<T>*)(d + job_off);
+    CU(cudaMemcpyAsync(dj, jobs.data(), sizeof(StateJob<T>) * jobs.size(), cudaMemcpyHostToDevice, s));
+    int rows = 1;
+    while (rows < 64 && (long long)rows * 256 * 16 < (long long)jobs[0].n * jobs[0].n) rows <<= 1;
+    stage_load_kernel<T><<<dim3((unsigned)rows, (unsigned)jobs.size()), 256, 0, s>>>((double*)d, dj);
+    CU(cudaGetLastError());
+    return VFPS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int vfps_batch_take_many(vfps_batch* b, int32_t count, const int32_t* slots, double* psi_out, double* power_out,
+                         int64_t power_cap, int64_t* n_power)
+{
+    if (!b || count < 1 || !slots || power_cap < 0 || (power_out && power_cap > 0 && !n_power)) return VFPS_EINVAL;
+    std::vector<Instance*> inst((size_t)count);
+    std::vector<long long> off((size_t)count);
+    long long total = 0, kmax = 0;
+    for (int i = 0; i < count; ++i) {
+        const int sl = slots[i];
+        if (sl < 0 || sl >= b->max_slots || !b->slots[(size_t)sl]) return VFPS_EINVAL;
+        Instance* I = b->slots[(size_t)sl];
+        inst[(size_t)i] = I;
+        off[(size_t)i] = total;
+        total += (long long)I->n * I->n;
+        kmax = std::max(kmax, I->steps_queued - I->drained);
+    }
+    // staged block: states (FP64), the undrained ring entries of every state
+    // (kmax per row), the status words, then the job tables
+    const size_t vb = align_up((size_t)total * 8, kAlign);
+    const size_t pb = align_up((size_t)count * 2 * (size_t)std::max<long long>(kmax, 1) * 8, kAlign);
+    const size_t stb = align_up((size_t)count * 4, kAlign);
+    const size_t jb = align_up(sizeof(SeriesJob) * (size_t)count, kAlign);
+    const size_t tjb = sizeof(StateJob<double>) * (size_t)count;
+    unsigned char* d = nullptr;
+    CU(cudaMallocAsync((void**)&d, vb + pb + stb + jb + 2 * tjb, b->stream));
+    std::vector<SeriesJob> sj((size_t)count);
+    for (int i = 0; i < count; ++i) {
+        const Instance& I = *inst[(size_t)i];
+        sj[(size_t)i] = SeriesJob{I.pring, I.qring, I.st, I.drained, I.steps_queued - I.drained, (long long)I.ring - 1};
+    }
+    std::vector<double> series((size_t)count * 2 * (size_t)std::max<long long>(kmax, 1));
+    std::vector<int> status((size_t)count);
+    int rc = VFPS_OK;
+    cudaError_t e = cudaMemcpyAsync(d + vb + pb + stb, sj.data(), sizeof(SeriesJob) * sj.size(),
+                                    cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && psi_out) {
+        rc = take_states_t<float>(inst, off, d, vb + pb + stb + jb, b->stream);
+        if (rc == VFPS_OK) rc = take_states_t<double>(inst, off, d, vb + pb + stb + jb + tjb, b->stream);
+    }
+    if (e == cudaSuccess && rc == VFPS_OK) {
+        stage_series_kernel<<<count, 256, 0, b->stream>>>((double*)(d + vb), std::max<long long>(kmax, 1),
+                                                          (const SeriesJob*)(d + vb + pb + stb), (int*)(d + vb + pb));
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && rc == VFPS_OK && psi_out)
+        e = cudaMemcpyAsync(psi_out, d, (size_t)total * 8, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess && rc == VFPS_OK)
+        e = cudaMemcpyAsync(series.data(), d + vb, series.size() * 8, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess && rc == VFPS_OK)
+        e = cudaMemcpyAsync(status.data(), d + vb + pb, status.size() * 4, cudaMemcpyDeviceToHost, b->stream);
+    cudaFreeAsync(d, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+        note_cuda_error(e, "vfps_batch_take_many");
+        return VFPS_ECUDA;
+    }
+    if (rc) return rc;
+    for (int i = 0; i < count; ++i) {
+        Instance& I = *inst[(size_t)i];
+        const size_t cap = (size_t)std::max<long long>(kmax, 1);
+        const double* rp = series.data() + (size_t)(2 * i) * cap;
+        I.pw.insert(I.pw.end(), rp, rp + sj[(size_t)i].cnt);
+        I.qw.insert(I.qw.end(), rp + cap, rp + cap + sj[(size_t)i].cnt);
+        I.drained = I.steps_queued;
+        rc = drain_moments(I, b->stream);
+        if (rc) return rc;
+        if (power_out && power_cap > 0) {
+            const int64_t k = std::min<int64_t>(power_cap, (int64_t)I.pw.size());
+            std::memcpy(power_out + (size_t)i * (size_t)power_cap, I.pw.data(), sizeof(double) * (size_t)k);
+            n_power[i] = k;
+        }
+    }
+    for (int i = 0; i < count; ++i) {
+        rc = status_code(status[(size_t)i]);
+        if (rc) return rc;
+    }
+    return VFPS_OK;
+}
+
+int vfps_batch_idle(vfps_batch* b, int32_t* idle)
+{
+    if (!b || !idle) return VFPS_EINVAL;
+    const cudaError_t e = cudaStreamQuery(b->stream);
+    if (e == cudaErrorNotReady) {
+        *idle = 0;
+        return VFPS_OK;
+    }
+    CU(e);
+    *idle = 1;
     return VFPS_OK;
 }
 
@@ -2101,6 +2565,43 @@ int vfps_batch_moments(vfps_batch* b, int32_t slot, double* out)
     return instance_moments(*b->slots[slot], b->stream, out);
 }
 
+int vfps_batch_record_moments(vfps_batch* b, int32_t slot, int32_t every)
+{
+    if (!b || slot < 0 || slot >= b->max_slots || !b->slots[slot] || every < 0) return VFPS_EINVAL;
+    Instance& I = *b->slots[slot];
+    const bool had = I.mring != nullptr;
+    CU(cudaStreamSynchronize(b->stream));
+    const int rc = set_moment_recording(I, b->stream, every);
+    if (rc) return rc;
+    if (!had && I.mring) b->used += (long long)(sizeof(double) * 4 * (size_t)I.ring);
+    b->dirty = true;  // the launch groups hold copies of the descriptor
+    return VFPS_OK;
+}
+
+int vfps_batch_moment_series(vfps_batch* b, int32_t slot, double* out, int64_t cap, int64_t* n_written)
+{
+    if (!b || slot < 0 || slot >= b->max_slots || !b->slots[slot] || !n_written || cap < 0 || (cap > 0 && !out))
+        return VFPS_EINVAL;
+    Instance& I = *b->slots[slot];
+    int rc = drain(I, b->stream);
+    if (rc) return rc;
+    *n_written = take_moments(I, out, cap, false);
+    return read_status(I, b->stream);
+}
+
+int vfps_batch_spectrogram(vfps_batch* b, const int32_t* slots, int32_t nslots, int32_t length, int32_t hop,
+                           int32_t count, double* out)
+{
+    if (!b || !slots || nslots < 1) return VFPS_EINVAL;
+    std::vector<Instance*> inst((size_t)nslots);
+    for (int i = 0; i < nslots; ++i) {
+        const int sl = slots[i];
+        if (sl < 0 || sl >= b->max_slots || !b->slots[sl]) return VFPS_EINVAL;
+        inst[(size_t)i] = b->slots[sl];
+    }
+    return spectrogram(inst.data(), nslots, length, hop, count, b->stream, out);
+}
+
 int vfps_batch_haissinski(vfps_batch* b, int32_t slot, double tol, int32_t max_iter, int32_t* iterations)
 {
     if (!b || slot < 0 || slot >= b->max_slots || !b->slots[slot]) return VFPS_EINVAL;
@@ -2113,6 +2614,7 @@ int vfps_batch_remove(vfps_batch* b, int32_t slot)
     if (!b || slot < 0 || slot >= b->max_slots || !b->slots[slot]) return VFPS_EINVAL;
     CU(cudaStreamSynchronize(b->stream));
     b->used -= (long long)b->slots[slot]->dbytes;
+    if (b->slots[slot]->mring) b->used -= (long long)(sizeof(double) * 4 * (size_t)b->slots[slot]->ring);
     destroy_instance(b->slots[slot]);
     b->slots[slot] = nullptr;
     b->dirty = true;
@@ -2150,6 +2652,11 @@ int vfps_batch_destroy(vfps_batch* b)
     free_groups(b);
     for (cudaStream_t st : b->pool) cudaStreamDestroy(st);
     for (cudaEvent_t ev : b->events) cudaEventDestroy(ev);
+    if (b->adm) {
+        cudaStreamSynchronize(b->adm);
+        cudaStreamDestroy(b->adm);
+        cudaEventDestroy(b->adm_ev);
+    }
     if (b->own_stream) cudaStreamDestroy(b->stream);
     delete b;
     return VFPS_OK;

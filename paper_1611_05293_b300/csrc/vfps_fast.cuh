@@ -31,6 +31,12 @@ namespace vfps {
 
 constexpr int kColPad = 16;  // zero rows above and below each psi_a column
 
+// Rotation passes (128 rows each) unrolled together in rotate_column.
+#ifndef VFPS_ROT_UNROLL
+#define VFPS_ROT_UNROLL 1
+#endif
+constexpr int kRotUnroll = VFPS_ROT_UNROLL;
+
 // Row padding of the staged slab: covers the largest y-node offset plus the
 // 12-row window, rounded to a multiple of 4 for 16-byte rows.
 __host__ __device__ inline int fast_row_pad(int h) { return ((h + 4 + 3) / 4) * 4; }
@@ -416,7 +422,7 @@ __device__ __forceinline__ void rotate_column(const float* __restrict__ ring, in
     const float fyf = float(FY);
     const float2 mfy = f2(-fyf, -fyf);
     const int lbase = cola_lane_base<KR>(lane, HC);
-#pragma unroll 1
+#pragma unroll kRotUnroll
     for (int yb = 0; yb < n; yb += 128) {
         // every lane runs every pass (the vote below needs the whole warp);
         // lanes past the last row only vote
@@ -513,6 +519,36 @@ __device__ __forceinline__ void drift_column(const float* __restrict__ ring, int
     }
 }
 
+// Moment-recording steps only: for the ncols columns from xs that this CTA
+// has just written to out, sum_y p_y psi_c(y) and sum_y p_y^2 psi_c(y) (FP32
+// lane partials, FP64 across lanes) into D.colmom[2x], [2x+1]; p_y = (y - c)
+// Delta.  Warp w takes columns xs+w, xs+w+W, ...
+__device__ __noinline__ void strip_p_moments(const Desc<float>& D, const float* out, int xs, int ncols, int n, int ld)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const float dl = float(D.delta), cc = D.c;
+    for (int k = warp; k < ncols && xs + k < n; k += nw) {
+        const int x = xs + k;
+        const float* col = out + (size_t)x * ld;
+        float a1 = 0.f, a2 = 0.f;
+        for (int y = lane; y < n; y += 32) {
+            const float p = (float(y) - cc) * dl, pv = p * col[y];
+            a1 += pv;
+            a2 = fmaf(p, pv, a2);
+        }
+        double s1 = double(a1), s2 = double(a2);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            s1 += __shfl_down_sync(0xffffffffu, s1, o);
+            s2 += __shfl_down_sync(0xffffffffu, s2, o);
+        }
+        if (lane == 0) {
+            D.colmom[2 * x] = s1;
+            D.colmom[2 * x + 1] = s2;
+        }
+    }
+}
+
 // One strip of the streaming FP32 step: T consecutive W-column tiles of
 // simulation D from column xs.  The strip walks its tiles one by one.  The
 // slab columns live in a ring of R shared-memory slots (R >= 2W + 2h): while
@@ -568,6 +604,8 @@ __device__ __forceinline__ void strip_f32(const Desc<float>& D, int xs, int T, u
     const int par = D.st->parity;
     const float* __restrict__ in = D.psi[par];
     float* __restrict__ out = D.psi[par ^ 1];
+    // a moment-recording step (the finaliser also needs each column's p-moments)
+    const bool mom_now = D.mom_every > 0 && (D.st->t + 1) % D.mom_every == 0;
     // window of tile 0, then the new columns of tile 1
     load_columns<W>(ring, R, P, RP, in, ld, n, xs - h, W + 2 * h);
     load_kick(kbuf, kickw, xs + warp, n, lane);
@@ -701,6 +739,10 @@ __device__ __forceinline__ void strip_f32(const Desc<float>& D, int xs, int T, u
         cp_async_commit();
     }
     cp_async_wait_0();
+    // moment-recording steps: the p-moments of the strip's columns, read back
+    // after the loop (every tile ended with a barrier, so all are written),
+    // keeping the hot loop free of the extra work
+    if (mom_now) strip_p_moments(D, out, xs, T * W, n, ld);
     __threadfence();  // this thread's column sums, before the ticket
     __syncthreads();
 #ifdef VFPS_DEBUG
@@ -722,8 +764,14 @@ __device__ __forceinline__ void strip_f32(const Desc<float>& D, int xs, int T, u
 // segment with no tiles ends the list.  With one segment per CTA the grid is
 // one CTA per strip; with balanced segments every CTA takes an equal share of
 // the launch's tiles, split at simulation boundaries.
+// Resident CTAs per SM the register allocation is sized for (x W warps):
+// 32 warps by default, i.e. 64 registers per thread.
+#ifndef VFPS_FAST_WARPS_PER_SM
+#define VFPS_FAST_WARPS_PER_SM 32
+#endif
+
 template <int W, int KR, int NC, int ROT>
-__global__ void __launch_bounds__(W * 32, 32 / W)
+__global__ void __launch_bounds__(W * 32, VFPS_FAST_WARPS_PER_SM / W)
 step_kernel_f32(const Desc<float>* __restrict__ descs, const int4* __restrict__ segs, int spc)
 {
     extern __shared__ __align__(16) unsigned char smem[];

@@ -19,6 +19,9 @@
 //            floor(-kick) as int bits
 //   pring    ring of CSR powers, pring[t] = P(psi_t)
 //   qring    ring of charges before renormalisation, qring[t] = Q of step t
+//   mring    (optional) ring of bunch moments, mring[4t..4t+3] = <q>, sigma_q,
+//            <p>, sigma_p of psi_t for the recorded steps t
+//   colmom   (moment steps) per column x: sum_y p_y psi_c, sum_y p_y^2 psi_c
 //   st       DevState: pending scale, step count, ticket, parity, status
 //
 // The stored psi is the un-normalised result psi_c of the last step; the
@@ -68,7 +71,10 @@ struct Desc {
     float4* kickw;                     // FP32 path: 2 per column, see layout above
     double* pring;
     double* qring;
+    double* mring;                     // moments ring (4 doubles per step), or null
+    double* colmom;                    // 2n: per column sum p psi and sum p^2 psi (moment steps)
     DevState* st;
+    int mom_every;                     // record moments of psi_t when t % mom_every == 0 (0: off)
     int n, ld, M, logM;
     int ring_mask, renorm, clamp, h;  // h: column halo of the staged slab
     int ntiles;                        // CTAs per step of this instance
@@ -506,6 +512,38 @@ __device__ __forceinline__ void wake_pair_pass(typename C2<T>::type* Z, const ty
     }
 }
 
+// Moment sums of a recording step, on the finaliser's FP64 sum warp beside
+// the forward transform: red[2..5] = sum q cs, sum q^2 cs (from the column
+// sums cs in shared memory), sum of the per-column p psi and p^2 psi sums the
+// step kernel wrote (colmom); each in the fixed order of warp_fixed_sum.
+__device__ __forceinline__ void moment_sums_warp(const double* cs, const double* colmom, int n, double delta,
+                                                 double* red)
+{
+    const int lane = threadIdx.x & 31;
+    const double cq = 0.5 * (n - 1);
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    for (int x = lane; x < n; x += 32) {
+        const double q = (x - cq) * delta, c = cs[x];
+        a0 += q * c;
+        a1 += q * q * c;
+        a2 += __ldcg(colmom + 2 * x);
+        a3 += __ldcg(colmom + 2 * x + 1);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a0 += __shfl_down_sync(0xffffffffu, a0, o);
+        a1 += __shfl_down_sync(0xffffffffu, a1, o);
+        a2 += __shfl_down_sync(0xffffffffu, a2, o);
+        a3 += __shfl_down_sync(0xffffffffu, a3, o);
+    }
+    if (lane == 0) {
+        red[2] = a0;
+        red[3] = a1;
+        red[4] = a2;
+        red[5] = a3;
+    }
+}
+
 template <typename T>
 __device__ void finalise(const Desc<T>& D, unsigned char* smem, int is_step)
 {
@@ -521,7 +559,9 @@ __device__ void finalise(const Desc<T>& D, unsigned char* smem, int is_step)
     double* red = pterm + H / 2 + 2;
 
     // the step counter, read early (its latency overlaps the transforms)
-    const long long t_now = tid == 0 ? D.st->t : 0;
+    // (every thread reads it: the moment steps below depend on it, and thread
+    // 0 only advances it after the last barrier)
+    const long long t_now = D.st->t;
     // one round of asynchronous copies: twiddles, impedance, column sums
     // (written by the other CTAs of this step; .cg keeps L1 out of the way)
     {
@@ -556,9 +596,12 @@ __device__ void finalise(const Desc<T>& D, unsigned char* smem, int is_step)
     const bool fft_thread = nt < 64 || (tid >> 5) != sum_warp, sum_thread = (tid >> 5) == sum_warp;
     T2* Z = fft_result<T2>(bufB, bufA, bufB, H);
     if (fft_thread) fft_h_part<T, false>(bufB, bufA, bufB, tw, H, nfft);
+    // (a moment-recording step also forms the moment sums there)
+    const bool mom_now = is_step && D.mom_every > 0 && D.mring && (t_now + 1) % D.mom_every == 0;
     if (sum_thread) {
         const double sum = warp_fixed_sum<double>(cs, n);
         if ((tid & 31) == 0) red[0] = sum;
+        if (mom_now) moment_sums_warp(cs, D.colmom, n, D.delta, red);
     }
     __syncthreads();
     const double Q = D.delta * D.delta * red[0];
@@ -600,6 +643,14 @@ __device__ void finalise(const Desc<T>& D, unsigned char* smem, int is_step)
         const double P = D.dkappa * red[1];
         DevState* st = D.st;
         const long long t = t_now;
+        if (mom_now) {  // bunch length and energy spread of the new state (Sec. IV)
+            const double s0 = red[0], mq = red[2] / s0, mp = red[4] / s0;
+            double* m = D.mring + 4 * ((t + 1) & D.ring_mask);
+            m[0] = mq;
+            m[1] = sqrt(fmax(red[3] / s0 - mq * mq, 0.0));
+            m[2] = mp;
+            m[3] = sqrt(fmax(red[5] / s0 - mp * mp, 0.0));
+        }
         if (is_step) {
             D.qring[t & D.ring_mask] = Q;
             D.pring[(t + 1) & D.ring_mask] = P;
@@ -691,11 +742,14 @@ step_kernel(const Desc<T>* __restrict__ descs, const int2* __restrict__ tiles)
     }
     __syncwarp();
 
-    // Fokker-Planck -> psi_c, column sum
+    // Fokker-Planck -> psi_c, column sum (and on moment-recording steps the
+    // column's sums of p psi_c and p^2 psi_c, p_y = (y - c) Delta)
+    const bool mom_now = D.mom_every > 0 && (D.st->t + 1) % D.mom_every == 0;
     double csum = 0.0;
     if (active) {
         T* dst = out + (size_t)x * ld;
-        T lsum = T(0);
+        T lsum = T(0), lp1 = T(0), lp2 = T(0);
+        const T dl = T(D.delta);
         const T ga0 = D.ga[0], ga1 = D.ga[1], ga2 = D.ga[2], ga3 = D.ga[3];
         const T gb0 = D.gb[0], gb1 = D.gb[1], gb2 = D.gb[2], gb3 = D.gb[3];
         for (int y = lane; y < n; y += 32) {
@@ -709,10 +763,27 @@ step_kernel(const Desc<T>* __restrict__ descs, const int2* __restrict__ tiles)
             T v = f0 + inc;
             dst[y] = v;
             lsum += v;
+            if (mom_now) {
+                const T pp = (yf - D.c) * dl, pv = pp * v;
+                lp1 += pv;
+                lp2 += pp * pv;
+            }
         }
         csum = double(lsum);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) csum += __shfl_down_sync(0xffffffffu, csum, o);
+        if (mom_now) {
+            double s1 = double(lp1), s2 = double(lp2);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                s1 += __shfl_down_sync(0xffffffffu, s1, o);
+                s2 += __shfl_down_sync(0xffffffffu, s2, o);
+            }
+            if (lane == 0) {
+                D.colmom[2 * x] = s1;
+                D.colmom[2 * x + 1] = s2;
+            }
+        }
         if (lane == 0) {
             D.colsum[x] = csum;
             __threadfence();
@@ -841,18 +912,16 @@ __global__ void __launch_bounds__(256) moments_finish_kernel(const Desc<T>* __re
 }
 
 // ----------------------------------------------------------------------------
-// Power spectrum of the last L values of an instance's CSR-power series (a
+// Power spectrum of L consecutive values of an instance's CSR-power series (a
 // row of the paper's bursting spectrogram, Sec. IV.C): mean removed (FP64),
 // Hann window, L-point complex FFT in FP32 (the Stockham passes of the
 // finaliser), out[k] = |X_k|^2 for k = 0..L/2.  One CTA of 256 threads;
 // shared memory 3 L float2 (two transform buffers and the twiddles
 // exp(-pi i m/L), m < L).  P(psi_t) for t = t0 .. t0+L-1 sits in
 // ring[t & mask].
-__global__ void __launch_bounds__(256)
-power_spectrum_kernel(const double* __restrict__ ring, int mask, long long t0, int L, double* __restrict__ out)
+__device__ __forceinline__ void window_spectrum(const double* __restrict__ ring, long long mask, long long t0, int L,
+                                                double* __restrict__ out, unsigned char* smem, double* part)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ double part[256];
     float2* A = reinterpret_cast<float2*>(smem);
     float2* B = A + L;
     float2* tw = B + L;
@@ -881,6 +950,142 @@ power_spectrum_kernel(const double* __restrict__ ring, int mask, long long t0, i
         const float2 v = X[k];
         out[k] = (double)v.x * v.x + (double)v.y * v.y;
     }
+}
+
+__global__ void __launch_bounds__(256)
+power_spectrum_kernel(const double* __restrict__ ring, int mask, long long t0, int L, double* __restrict__ out)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double part[256];
+    window_spectrum(ring, mask, t0, L, out, smem, part);
+}
+
+// One spectrogram window of one simulation per CTA: the series of simulation
+// blockIdx.y starts its windows at t_first, window blockIdx.x at t_first +
+// blockIdx.x hop; out[(y * count + x) * (L/2 + 1) ..].
+struct SpecSeries {
+    const double* ring;
+    long long mask;
+    long long t_first;
+};
+
+__global__ void __launch_bounds__(256)
+spectrogram_kernel(const SpecSeries* __restrict__ series, int L, int hop, double* __restrict__ out)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double part[256];
+    const SpecSeries sr = series[blockIdx.y];
+    const size_t row = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+    window_spectrum(sr.ring, sr.mask, sr.t_first + (long long)blockIdx.x * hop, L, out + row * (L / 2 + 1), smem,
+                    part);
+}
+
+// ----------------------------------------------------------------------------
+// Host <-> device state transfers of many simulations at once.
+//
+// Upload: staged FP64 states (host copies in one block) are normalised to
+// charge 1 on the device.  stage_sum_kernel: one CTA per state, FP64 sum of
+// its n*n values in a fixed order (thread t adds t, t+256, ...; then a fixed
+// tree) and whether all are finite: sums[2i], sums[2i+1].
+__global__ void __launch_bounds__(256)
+stage_sum_kernel(const double* __restrict__ src, long long per_state, double* __restrict__ sums)
+{
+    __shared__ double part[256];
+    __shared__ int bad;
+    const double* v = src + (size_t)blockIdx.x * per_state;
+    if (threadIdx.x == 0) bad = 0;
+    __syncthreads();
+    double acc = 0.0;
+    bool fin = true;
+    for (long long i = threadIdx.x; i < per_state; i += 256) {
+        const double x = v[i];
+        fin = fin && isfinite(x);
+        acc += x;
+    }
+    part[threadIdx.x] = acc;
+    if (!fin) bad = 1;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (threadIdx.x < h) part[threadIdx.x] += part[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        sums[2 * blockIdx.x] = part[0];
+        sums[2 * blockIdx.x + 1] = bad ? 0.0 : 1.0;
+    }
+}
+
+// One state of a transfer: its device psi (row pitch ld), grid size, and the
+// factor applied on the way (upload: 1/(Delta^2 sum); download: read from st).
+template <typename T>
+struct StateJob {
+    T* psi[2];
+    DevState* st;        // parity; upload: the pending scale becomes 1, the ticket 0
+    long long off;       // first value of this state in the staged block
+    double delta2;       // upload: Delta^2
+    int n, ld;
+};
+
+// Upload: psi[parity] = (T)(staged * inv), inv = 1/(Delta^2 sum), rows padded
+// with zeros to ld; the state's pending scale becomes 1.  Grid (row blocks,
+// states).
+template <typename T>
+__global__ void __launch_bounds__(256)
+stage_store_kernel(const double* __restrict__ src, const double* __restrict__ sums, const StateJob<T>* jobs)
+{
+    const StateJob<T> j = jobs[blockIdx.y];
+    const double inv = 1.0 / (j.delta2 * sums[2 * blockIdx.y]);
+    T* dst = j.psi[j.st->parity];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        j.st->scale = 1.0;
+        j.st->ticket = 0u;
+    }
+    const long long cells = (long long)j.n * j.ld;
+    for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < cells; i += (long long)gridDim.x * 256) {
+        const int x = (int)(i / j.ld), y = (int)(i - (long long)x * j.ld);
+        dst[i] = y < j.n ? (T)(src[j.off + (long long)x * j.n + y] * inv) : T(0);
+    }
+}
+
+// Download: staged[off + x n + y] = (double)psi[parity][x][y] * scale (the
+// stored state with its pending renormalisation applied, as a single
+// vfps_get_state computes it).  Grid (row blocks, states).
+template <typename T>
+__global__ void __launch_bounds__(256)
+stage_load_kernel(double* __restrict__ dst, const StateJob<T>* jobs)
+{
+    const StateJob<T> j = jobs[blockIdx.y];
+    const T* src = j.psi[j.st->parity];
+    const double scale = j.st->scale;
+    const long long cells = (long long)j.n * j.n;
+    for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < cells; i += (long long)gridDim.x * 256) {
+        const int x = (int)(i / j.n), y = (int)(i - (long long)x * j.n);
+        dst[j.off + i] = (double)src[(size_t)x * j.ld + y] * scale;
+    }
+}
+
+// Ring entries [lo_i, lo_i + cnt_i) of each state's CSR-power and charge
+// rings into rows 2i and 2i+1 of a staged block (row r at out + r * cap),
+// with the state's status word.
+struct SeriesJob {
+    const double* pring;
+    const double* qring;
+    const DevState* st;
+    long long lo, cnt, mask;
+};
+
+__global__ void __launch_bounds__(256)
+stage_series_kernel(double* __restrict__ out, long long cap, const SeriesJob* __restrict__ jobs,
+                    int* __restrict__ status)
+{
+    const SeriesJob j = jobs[blockIdx.x];
+    double* rp = out + (size_t)(2 * blockIdx.x) * cap;
+    double* rq = rp + cap;
+    for (long long i = threadIdx.x; i < j.cnt; i += 256) {
+        rp[i] = j.pring[(j.lo + i) & j.mask];
+        rq[i] = j.qring[(j.lo + i) & j.mask];
+    }
+    if (threadIdx.x == 0) status[blockIdx.x] = j.st->status;
 }
 
 }  // namespace vfps

@@ -30,6 +30,10 @@ EXPORTS = [
     "vfps_moments", "vfps_batch_moments", "vfps_batch_autotune", "vfps_batch_shapes",
     "vfps_batch_pin_shape", "vfps_power_spectrum", "vfps_batch_power_spectrum", "vfps_batch_pairing",
     "vfps_haissinski", "vfps_batch_haissinski",
+    "vfps_record_moments", "vfps_moment_series", "vfps_spectrogram",
+    "vfps_batch_record_moments", "vfps_batch_moment_series", "vfps_batch_spectrogram", "vfps_batch_idle",
+    "vfps_checkpoint_bytes", "vfps_save_checkpoint", "vfps_load_checkpoint",
+    "vfps_batch_add_many", "vfps_batch_take_many",
 ]
 
 
@@ -131,6 +135,20 @@ def lib() -> ctypes.CDLL:
         "vfps_batch_destroy": (ctypes.c_int, [_VP]),
         "vfps_step_static": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_double, ctypes.c_double, _VP, _VP,
                                             _D, _VP]),
+        "vfps_record_moments": (ctypes.c_int, [_VP, _I32]),
+        "vfps_moment_series": (ctypes.c_int, [_VP, _D, _I64, ctypes.POINTER(_I64)]),
+        "vfps_spectrogram": (ctypes.c_int, [_VP, _I32, _I32, _I32, _D]),
+        "vfps_batch_record_moments": (ctypes.c_int, [_VP, _I32, _I32]),
+        "vfps_batch_idle": (ctypes.c_int, [_VP, ctypes.POINTER(_I32)]),
+        "vfps_checkpoint_bytes": (ctypes.c_int, [_VP, ctypes.POINTER(_I64)]),
+        "vfps_batch_add_many": (ctypes.c_int, [_VP, _I32, P, _D, ctypes.c_int, _D, _D, _I64,
+                                               ctypes.POINTER(_I32)]),
+        "vfps_batch_take_many": (ctypes.c_int, [_VP, _I32, ctypes.POINTER(_I32), _D, _D, _I64,
+                                                ctypes.POINTER(_I64)]),
+        "vfps_save_checkpoint": (ctypes.c_int, [_VP, ctypes.c_void_p, _I64]),
+        "vfps_load_checkpoint": (ctypes.c_int, [_VP, ctypes.c_void_p, _I64]),
+        "vfps_batch_moment_series": (ctypes.c_int, [_VP, _I32, _D, _I64, ctypes.POINTER(_I64)]),
+        "vfps_batch_spectrogram": (ctypes.c_int, [_VP, ctypes.POINTER(_I32), _I32, _I32, _I32, _I32, _D]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -224,6 +242,24 @@ class Simulation:
         _check(lib().vfps_moments(self._h, _dptr(out)), "vfps_moments")
         return out
 
+    def record_moments(self, every: int):
+        """Record (<q>, sigma_q, <p>, sigma_p) of every `every`-th state as part
+        of the step (0 stops)."""
+        _check(lib().vfps_record_moments(self._h, int(every)), "vfps_record_moments")
+
+    def moment_series(self, cap: int = 1 << 20) -> np.ndarray:
+        """Drain the recorded moments: rows (t, <q>, sigma_q, <p>, sigma_p)."""
+        out = np.empty((max(1, cap), 5))
+        k = _I64()
+        _check(lib().vfps_moment_series(self._h, _dptr(out), int(cap), ctypes.byref(k)), "vfps_moment_series")
+        return out[:k.value].copy()
+
+    def spectrogram(self, length: int, hop: int, count: int) -> np.ndarray:
+        """(count, length/2 + 1) power spectra of CSR-power windows, on the device."""
+        out = np.empty((count, length // 2 + 1))
+        _check(lib().vfps_spectrogram(self._h, int(length), int(hop), int(count), _dptr(out)), "vfps_spectrogram")
+        return out
+
     def _series(self, fn, cap):
         # one value per step since the series was last drained: a buffer of
         # that size (a huge one costs more in first-touch faults than the copy)
@@ -250,6 +286,20 @@ class Simulation:
     def set_state(self, psi):
         n = self.params.n
         _check(lib().vfps_set_state(self._h, _dptr(_f64(psi, (n, n)))), "vfps_set_state")
+
+    def save_checkpoint(self) -> bytes:
+        """The device state between steps, as raw bytes (bitwise resume)."""
+        k = _I64()
+        _check(lib().vfps_checkpoint_bytes(self._h, ctypes.byref(k)), "vfps_checkpoint_bytes")
+        buf = ctypes.create_string_buffer(k.value)
+        _check(lib().vfps_save_checkpoint(self._h, buf, k.value), "vfps_save_checkpoint")
+        return buf.raw
+
+    def load_checkpoint(self, data: bytes):
+        """Resume from save_checkpoint's bytes (same parameters and impedance)."""
+        buf = ctypes.create_string_buffer(bytes(data), len(data))
+        _check(lib().vfps_load_checkpoint(self._h, buf, len(data)), "vfps_load_checkpoint")
+        self._taken = {}
 
     def haissinski(self, tol: float = 1e-13, max_iter: int = 20000) -> int:
         """Replace the state by the Haissinski equilibrium rho_H(q) g(p) of the
@@ -312,6 +362,39 @@ class Batch:
         self.nsteps[s.value] = (int(nsteps), 0)
         return s.value
 
+    def add_many(self, params: Params, psi0, model: int, Pi, S_csr, nsteps: int = 0) -> list[int]:
+        """vfps_batch_add_many: len(Pi) simulations of one parameter set; psi0 is
+        None or a (count, n, n) float64 array (pinned memory copies fastest)."""
+        Pi = _f64(Pi)
+        S = _f64(S_csr)
+        count = int(Pi.size)
+        n = params.n
+        ps = None if psi0 is None else _f64(psi0, (count, n, n))
+        out = (_I32 * count)()
+        _check(lib().vfps_batch_add_many(self._b, count, ctypes.byref(params.c()), _dptr(ps), int(model),
+                                         _dptr(Pi), _dptr(S), int(nsteps), out), "vfps_batch_add_many")
+        slots = [out[i] for i in range(count)]
+        for sl in slots:
+            self.params[sl] = params
+            self.nsteps[sl] = (int(nsteps), 0)
+        return slots
+
+    def take_many(self, slots, psi_out=None, power_cap: int = 0):
+        """vfps_batch_take_many: states of `slots` into psi_out (a C-contiguous
+        (len(slots), n, n) float64 array, e.g. pinned) and, with power_cap > 0,
+        their CSR-power series (list of arrays)."""
+        count = len(slots)
+        sl = (_I32 * count)(*[int(x) for x in slots])
+        if psi_out is not None:
+            n = self.params[slots[0]].n
+            if psi_out.shape != (count, n, n) or psi_out.dtype != np.float64 or not psi_out.flags.c_contiguous:
+                raise ValueError(f"psi_out must be a C-contiguous float64 array of shape {(count, n, n)}")
+        pw = np.empty((count, max(1, power_cap))) if power_cap > 0 else None
+        npw = (_I64 * count)()
+        _check(lib().vfps_batch_take_many(self._b, count, sl, _dptr(psi_out), _dptr(pw), int(power_cap), npw),
+               "vfps_batch_take_many")
+        return [pw[i, :npw[i]].copy() for i in range(count)] if pw is not None else None
+
     def try_add(self, *a, **kw):
         """add(), but returns None instead of raising when the batch is full (EBUSY)."""
         try:
@@ -327,6 +410,12 @@ class Batch:
         for k, (target, done) in self.nsteps.items():
             self.nsteps[k] = (target, min(target, done + int(chunk_steps)))
         _check(lib().vfps_batch_run(self._b, int(chunk_steps)), "vfps_batch_run")
+
+    def idle(self) -> bool:
+        """True once every queued step and set-up has finished (never blocks)."""
+        k = _I32()
+        _check(lib().vfps_batch_idle(self._b, ctypes.byref(k)), "vfps_batch_idle")
+        return bool(k.value)
 
     def poll(self) -> list[int]:
         cap = max(1, len(self.params))
@@ -367,6 +456,26 @@ class Batch:
         """(<q>, sigma_q, <p>, sigma_p) of a slot's current state, on the device."""
         out = np.empty(4)
         _check(lib().vfps_batch_moments(self._b, int(slot), _dptr(out)), "vfps_batch_moments")
+        return out
+
+    def record_moments(self, slot: int, every: int):
+        """vfps_batch_record_moments."""
+        _check(lib().vfps_batch_record_moments(self._b, int(slot), int(every)), "vfps_batch_record_moments")
+
+    def moment_series(self, slot: int, cap: int = 1 << 20) -> np.ndarray:
+        """The slot's moment records so far: rows (t, <q>, sigma_q, <p>, sigma_p)."""
+        out = np.empty((max(1, cap), 5))
+        k = _I64()
+        _check(lib().vfps_batch_moment_series(self._b, int(slot), _dptr(out), int(cap), ctypes.byref(k)),
+               "vfps_batch_moment_series")
+        return out[:k.value].copy()
+
+    def spectrogram(self, slots, length: int, hop: int, count: int) -> np.ndarray:
+        """(len(slots), count, length/2 + 1) windowed CSR-power spectra, one launch."""
+        sl = (_I32 * len(slots))(*[int(x) for x in slots])
+        out = np.empty((len(slots), count, length // 2 + 1))
+        _check(lib().vfps_batch_spectrogram(self._b, sl, len(slots), int(length), int(hop), int(count), _dptr(out)),
+               "vfps_batch_spectrogram")
         return out
 
     def take(self, slot: int, psi=True, rho=True, power_cap: int = 1 << 22, psi_out=None):

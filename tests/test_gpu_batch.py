@@ -316,3 +316,34 @@ def test_take_into_preallocated_rows_and_series_bound(V):
     with pytest.raises(ValueError):
         b.take(slots[0], psi_out=np.empty((n, n + 1)))
     b.close()
+
+
+def test_bulk_add_and_take_equal_single_calls(V):
+    """vfps_batch_add_many / vfps_batch_take_many move many slots in one copy
+    each way (normalisation and FP32 conversion on the device) and give the
+    same bits as one vfps_batch_add / vfps_batch_take per slot; a bad state
+    anywhere refuses the whole call and adds nothing."""
+    n, spp, steps = 64, 500, 40
+    pts = [(0.3, 2.0), (0.9, 1.0), (1.4, 3.0), (0.6, 0.5), (1.1, 2.5)]
+    psi0 = np.stack([W.blobs(n, 40 + i) for i in range(len(pts))])
+    params = V.Params(n=n, steps_per_period=spp, beta=1e-2)
+    one = V.Batch(len(pts))
+    s1 = [one.add(params, psi0[i], V.IMPEDANCE_PARALLEL_PLATES, Pi, S, nsteps=steps) for i, (S, Pi) in enumerate(pts)]
+    one.run(steps)
+    ref = [one.take(sl) for sl in s1]
+    one.close()
+    many = V.Batch(len(pts) + 2)
+    bad = psi0.copy()
+    bad[3, 5, 5] = np.inf
+    with pytest.raises(V.VfpsError) as e:
+        many.add_many(params, bad, V.IMPEDANCE_PARALLEL_PLATES, [p[1] for p in pts], [p[0] for p in pts], steps)
+    assert e.value.code == V.EINVAL and many.usage()[0] == 0
+    sm = many.add_many(params, psi0, V.IMPEDANCE_PARALLEL_PLATES, [p[1] for p in pts], [p[0] for p in pts], steps)
+    many.run(steps)
+    out = np.empty((len(pts), n, n))
+    power = many.take_many(sm, psi_out=out, power_cap=steps)
+    for i in range(len(pts)):
+        assert np.array_equal(out[i], ref[i]["psi"]), i
+        assert np.array_equal(power[i], ref[i]["power"]), i
+        assert np.array_equal(many.take(sm[i])["psi"], ref[i]["psi"]), i
+    many.close()

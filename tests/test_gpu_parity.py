@@ -179,6 +179,46 @@ def test_state_roundtrip_and_counters(V):
     sim.close()
 
 
+@pytest.mark.parametrize("n,precision,rotation", [(256, 0, 0), (64, 1, 0), (100, 0, 1), (48, 0, 0)])
+def test_checkpoint_resume_is_bitwise(V, n, precision, rotation):
+    """Checkpoint and resume (restart from a previous run, Sec. IV.C; App. B
+    option -i): a run stopped after 37 steps, saved, loaded into a fresh
+    handle of the same parameters and impedance and continued for 29 steps
+    ends with the same bits (state and CSR-power series) as the
+    uninterrupted 66-step run; mismatching parameters or impedance refuse the
+    checkpoint."""
+    params = V.Params(n=n, steps_per_period=500, beta=1e-2, precision=precision, rotation=rotation)
+    psi0 = W.blobs(n, 12)
+
+    def fresh():
+        sim = V.Simulation(params, psi0)
+        sim.set_impedance(V.IMPEDANCE_PARALLEL_PLATES, 2.0, 0.9)
+        return sim
+
+    a = fresh()
+    a.step(66)
+    ref_psi, ref_p = a.get_state(), a.csr_power()
+    a.close()
+    b = fresh()
+    b.step(37)
+    ck = b.save_checkpoint()
+    b.close()
+    c = fresh()
+    c.step(3)  # whatever it held before the load is replaced
+    c.load_checkpoint(ck)
+    assert c.steps_done() == 37
+    c.step(29)
+    assert np.array_equal(c.get_state(), ref_psi)
+    assert np.array_equal(c.csr_power(), ref_p[37:])
+    c.close()
+    other = V.Simulation(params, psi0)
+    other.set_impedance(V.IMPEDANCE_PARALLEL_PLATES, 2.0, 1.0)  # another S_csr
+    with pytest.raises(V.VfpsError) as e:
+        other.load_checkpoint(ck)
+    assert e.value.code == V.EINVAL
+    other.close()
+
+
 def test_invalid_arguments_are_rejected(V):
     for bad in [dict(n=4), dict(n=64, steps_per_period=1), dict(n=64, interp_points=5),
                 dict(n=64, pad_factor=1), dict(n=64, beta=-1.0), dict(n=2049),
