@@ -276,6 +276,7 @@ struct Instance {
     double Pi = 0, S = 0;
     void* dmem = nullptr;
     size_t dbytes = 0;
+    std::shared_ptr<void> arena;  // set when dmem lies in a block shared with other slots
     void* psi[2] = {nullptr, nullptr};
     void* zhat = nullptr;
     void* tw = nullptr;
@@ -401,7 +402,7 @@ void destroy_instance(Instance* I)
 {
     if (!I) return;
     if (I->mring) cudaFree(I->mring);
-    if (I->dmem) cudaFree(I->dmem);
+    if (I->dmem && !I->arena) cudaFree(I->dmem);  // a shared block goes with its last slot
     delete I;
 }
 
@@ -480,6 +481,7 @@ int upload_states_t(Instance* const* inst, int count, const double* src, cudaStr
         src = gauss.data();
     }
     const size_t vb = align_up((size_t)total * 8, kAlign), sb = align_up((size_t)count * 16, kAlign);
+    const size_t pb = align_up((size_t)count * 16 * kStageParts, kAlign);
     const size_t jb = sizeof(StateJob<T>) * (size_t)count;
     std::vector<StateJob<T>> jobs((size_t)count);
     for (int i = 0; i < count; ++i) {
@@ -487,15 +489,21 @@ int upload_states_t(Instance* const* inst, int count, const double* src, cudaStr
         jobs[(size_t)i] = StateJob<T>{{(T*)I.psi[0], (T*)I.psi[1]}, I.st, off[(size_t)i], I.delta * I.delta, I.n, I.ld};
     }
     unsigned char* d = nullptr;
-    CU(cudaMallocAsync((void**)&d, vb + sb + jb, s));
+    CU(cudaMallocAsync((void**)&d, vb + sb + pb + jb, s));
     double* dv = (double*)d;
     double* ds = (double*)(d + vb);
-    StateJob<T>* dj = (StateJob<T>*)(d + vb + sb);
+    double* dp = (double*)(d + vb + sb);
+    StateJob<T>* dj = (StateJob<T>*)(d + vb + sb + pb);
     std::vector<double> sums((size_t)count * 2);
     cudaError_t e = cudaMemcpyAsync(dv, src, (size_t)total * 8, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dj, jobs.data(), jb, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) {
-        stage_sum_kernel<<<count, 256, 0, s>>>(dv, (long long)inst[0]->n * inst[0]->n, ds);
+        stage_sum_kernel<<<dim3(kStageParts, (unsigned)count), 256, 0, s>>>(dv, (long long)inst[0]->n * inst[0]->n,
+                                                                            dp);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        stage_combine_kernel<<<(count + 255) / 256, 256, 0, s>>>(dp, count, ds);
         e = cudaGetLastError();
     }
     // (one grid size per call: stage_sum_kernel strides by the first state's size)
@@ -563,7 +571,9 @@ void cached_impedance(int model, int M, double delta, double Pi, std::vector<std
     }
 }
 
-int upload_impedance(Instance& I, int model, double Pi, double S, const double* table, cudaStream_t s)
+// The instance's impedance table for a model in its element type (buf), and
+// the model, Pi and S_csr recorded in the instance.  Errors: EINVAL.
+int impedance_image(Instance& I, int model, double Pi, double S, const double* table, std::vector<unsigned char>& buf)
 {
     int K = I.M / 2;
     std::vector<std::complex<double>> z;
@@ -582,7 +592,7 @@ int upload_impedance(Instance& I, int model, double Pi, double S, const double* 
     }
     if (!std::isfinite(S)) return VFPS_EINVAL;
     size_t es = elem_size(&I.p);
-    std::vector<unsigned char> buf((size_t)(K + 1) * 2 * es);
+    buf.resize((size_t)(K + 1) * 2 * es);
     for (int k = 0; k <= K; ++k) {
         if (es == 8) {
             reinterpret_cast<double*>(buf.data())[2 * k] = z[k].real();
@@ -592,16 +602,66 @@ int upload_impedance(Instance& I, int model, double Pi, double S, const double* 
             reinterpret_cast<float*>(buf.data())[2 * k + 1] = (float)z[k].imag();
         }
     }
-    CU(cudaMemcpyAsync(I.zhat, buf.data(), buf.size(), cudaMemcpyHostToDevice, s));
-    CU(cudaStreamSynchronize(s));
     I.model = model;
     I.Pi = Pi;
     I.S = S;
     return VFPS_OK;
 }
 
+int upload_impedance(Instance& I, int model, double Pi, double S, const double* table, cudaStream_t s)
+{
+    std::vector<unsigned char> buf;
+    const int rc = impedance_image(I, model, Pi, S, table, buf);
+    if (rc) return rc;
+    CU(cudaMemcpyAsync(I.zhat, buf.data(), buf.size(), cudaMemcpyHostToDevice, s));
+    CU(cudaStreamSynchronize(s));
+    return VFPS_OK;
+}
+
+// An instance's buffers inside its one allocation b (offsets of instance_bytes).
+void set_pointers(Instance& I, unsigned char* b, const size_t* offs)
+{
+    I.psi[0] = b + offs[0];
+    I.psi[1] = b + offs[1];
+    I.zhat = b + offs[2];
+    I.tw = b + offs[3];
+    I.colsum = (double*)(b + offs[4]);
+    I.rho = (double*)(b + offs[5]);
+    I.kick = b + offs[6];
+    I.pring = (double*)(b + offs[7]);
+    I.qring = (double*)(b + offs[8]);
+    I.st = (DevState*)(b + offs[9]);
+    I.ddesc = b + offs[10];
+    I.dtiles = (int2*)(b + offs[11]);
+    I.kickw = b + offs[12];
+    I.mom = (double*)(b + offs[13]);
+    I.dsegs = (int4*)(b + offs[14]);
+}
+
+// Host images of an instance's constant tables, in its own element type:
+// twiddles exp(-2 pi i k/M) (FP64 on the host), and the impedance table of a
+// model (FP64 host table, rounded once).
+void twiddle_table(const Instance& I, std::vector<unsigned char>& buf)
+{
+    const int K = I.M / 2;
+    const size_t es = elem_size(&I.p);
+    buf.resize((size_t)K * 2 * es);
+    for (int k = 0; k < K; ++k) {
+        const double ang = -2.0 * kPi * k / I.M;
+        const double c = std::cos(ang), s = std::sin(ang);
+        if (es == 8) {
+            reinterpret_cast<double*>(buf.data())[2 * k] = c;
+            reinterpret_cast<double*>(buf.data())[2 * k + 1] = s;
+        } else {
+            reinterpret_cast<float*>(buf.data())[2 * k] = (float)c;
+            reinterpret_cast<float*>(buf.data())[2 * k + 1] = (float)s;
+        }
+    }
+}
+
 int create_instance(const vfps_params* p, const double* psi0, int ring, cudaStream_t s, Instance** out,
-                    bool latency = false, bool upload = true)
+                    bool latency = false, bool upload = true, bool tables = true,
+                    std::shared_ptr<void> arena = nullptr, size_t arena_off = 0)
 {
     int rc = check_params(p);
     if (rc) return rc;
@@ -622,43 +682,26 @@ int create_instance(const vfps_params* p, const double* psi0, int ring, cudaStre
     I->phi = 2.0 * kPi / p->steps_per_period;
     size_t offs[15];
     I->dbytes = instance_bytes(p, ring, offs);
-    if (dev_alloc(&I->dmem, I->dbytes) != cudaSuccess) {
-        cudaGetLastError();
-        return VFPS_ENOMEM;
+    if (arena) {  // a slice of a block the caller allocated and cleared
+        I->arena = arena;
+        I->dmem = (unsigned char*)arena.get() + arena_off;
+    } else {
+        if (dev_alloc(&I->dmem, I->dbytes) != cudaSuccess) {
+            cudaGetLastError();
+            return VFPS_ENOMEM;
+        }
+        if (cudaMemsetAsync(I->dmem, 0, I->dbytes, s) != cudaSuccess) return VFPS_ECUDA;
     }
     unsigned char* b = (unsigned char*)I->dmem;
-    if (cudaMemsetAsync(b, 0, I->dbytes, s) != cudaSuccess) return VFPS_ECUDA;
-    I->psi[0] = b + offs[0];
-    I->psi[1] = b + offs[1];
-    I->zhat = b + offs[2];
-    I->tw = b + offs[3];
-    I->colsum = (double*)(b + offs[4]);
-    I->rho = (double*)(b + offs[5]);
-    I->kick = b + offs[6];
-    I->pring = (double*)(b + offs[7]);
-    I->qring = (double*)(b + offs[8]);
-    I->st = (DevState*)(b + offs[9]);
-    I->ddesc = b + offs[10];
-    I->dtiles = (int2*)(b + offs[11]);
-    I->kickw = b + offs[12];
-    I->mom = (double*)(b + offs[13]);
-    I->dsegs = (int4*)(b + offs[14]);
+    set_pointers(*I, b, offs);
+    if (!tables) {  // the caller uploads every table (vfps_batch_add_many)
+        *out = I.release();
+        return VFPS_OK;
+    }
     // twiddles exp(-2 pi i k/M), FP64 on the host
     {
-        int K = I->M / 2;
-        size_t es = elem_size(p);
-        std::vector<unsigned char> buf((size_t)K * 2 * es);
-        for (int k = 0; k < K; ++k) {
-            double ang = -2.0 * kPi * k / I->M;
-            double c = std::cos(ang), s = std::sin(ang);
-            if (es == 8) {
-                reinterpret_cast<double*>(buf.data())[2 * k] = c;
-                reinterpret_cast<double*>(buf.data())[2 * k + 1] = s;
-            } else {
-                reinterpret_cast<float*>(buf.data())[2 * k] = (float)c;
-                reinterpret_cast<float*>(buf.data())[2 * k + 1] = (float)s;
-            }
-        }
+        std::vector<unsigned char> buf;
+        twiddle_table(*I, buf);
         // a copy from pageable memory returns once the data is staged: buf may go
         if (cudaMemcpyAsync(I->tw, buf.data(), buf.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
             return VFPS_ECUDA;
@@ -2316,18 +2359,113 @@ int vfps_batch_add_many(vfps_batch* b, int32_t count, const vfps_params* params,
         for (Instance* I : made) destroy_instance(I);
         return code;
     };
+    // one allocation for all the slots (freed with the last of them)
+    const size_t stride = align_up(instance_bytes(params, kRingDefault / 2, offs), kAlign);
+    void* block = nullptr;
+    if (dev_alloc(&block, stride * (size_t)count) != cudaSuccess) {
+        cudaGetLastError();
+        return VFPS_ENOMEM;
+    }
+    std::shared_ptr<void> arena(block, [](void* q) { cudaFree(q); });
+    CU(cudaMemsetAsync(block, 0, stride * (size_t)count, b->adm));
     for (int i = 0; i < count; ++i) {
         Instance* I = nullptr;
-        rc = create_instance(params, nullptr, kRingDefault / 2, b->adm, &I, false, false);
+        rc = create_instance(params, nullptr, kRingDefault / 2, b->adm, &I, false, false, false, arena,
+                             stride * (size_t)i);
         if (rc) return fail(rc);
         I->target = nsteps;
         made.push_back(I);
     }
-    rc = upload_states(made.data(), count, psi0, b->adm);
-    for (int i = 0; i < count && rc == VFPS_OK; ++i) {
-        rc = upload_impedance(*made[(size_t)i], model, Pi[i], S_csr[i], nullptr, b->adm);
-        if (rc == VFPS_OK) rc = prologue(*made[(size_t)i], b->adm);
+    arena.reset();  // the slots hold it now
+    // every slot's tables in one host block, one copy, one scatter launch:
+    // the twiddles, tile and segment lists and the state word are the same
+    // for all slots (staged once), the impedance and descriptor per slot
+    std::vector<unsigned char> img;
+    std::vector<CopyJob> jobs;
+    auto stage = [&](const void* src, size_t bytes) {
+        const size_t off = align_up(img.size(), 16);
+        img.resize(off + bytes);
+        std::memcpy(img.data() + off, src, bytes);
+        return off;
+    };
+    auto job = [&](size_t off, void* dst, size_t bytes) {
+        jobs.push_back(CopyJob{(const unsigned int*)(uintptr_t)off, (unsigned int*)dst, (long long)(bytes / 4)});
+    };
+    {
+        const Instance& I0 = *made[0];
+        std::vector<unsigned char> tw;
+        twiddle_table(I0, tw);
+        std::vector<int2> t((size_t)I0.ntiles);
+        std::vector<int4> sg((size_t)I0.ntiles);
+        for (int k = 0; k < I0.ntiles; ++k) {
+            t[(size_t)k] = make_int2(0, k * I0.W);
+            sg[(size_t)k] = make_int4(0, k * I0.W, 1, 0);
+        }
+        DevState st{};
+        st.scale = 1.0;
+        const size_t o_tw = stage(tw.data(), tw.size()), o_t = stage(t.data(), sizeof(int2) * t.size());
+        const size_t o_sg = stage(sg.data(), sizeof(int4) * sg.size()), o_st = stage(&st, sizeof(st));
+        std::vector<unsigned char> zb;
+        for (int i = 0; i < count && rc == VFPS_OK; ++i) {
+            Instance& I = *made[(size_t)i];
+            rc = impedance_image(I, model, Pi[i], S_csr[i], nullptr, zb);
+            if (rc) break;
+            if (I.p.precision) fill_desc<double>(I);
+            else fill_desc<float>(I);
+            job(o_tw, I.tw, tw.size());
+            job(o_t, I.dtiles, sizeof(int2) * t.size());
+            job(o_sg, I.dsegs, sizeof(int4) * sg.size());
+            job(o_st, I.st, sizeof(st));
+            job(stage(zb.data(), zb.size()), I.zhat, zb.size());
+            job(stage(I.hdesc, sizeof(Desc<double>)), I.ddesc, sizeof(Desc<double>));
+        }
     }
+    // the prologue of every new slot (profile, wake and kick table of its
+    // start) as one launch: their descriptors and tiles, staged with the rest
+    const size_t dsz = params->precision ? sizeof(Desc<double>) : sizeof(Desc<float>);
+    size_t o_descs = 0, o_tiles = 0;
+    int ptiles = 0;
+    if (rc == VFPS_OK) {
+        o_descs = align_up(img.size(), 256);
+        img.resize(o_descs + dsz * (size_t)count);
+        std::vector<int2> pt;
+        for (int i = 0; i < count; ++i) {
+            std::memcpy(img.data() + o_descs + dsz * (size_t)i, made[(size_t)i]->hdesc, dsz);
+            for (int k = 0; k < made[(size_t)i]->ntiles; ++k) pt.push_back(make_int2(i, k * made[(size_t)i]->W));
+        }
+        ptiles = (int)pt.size();
+        o_tiles = stage(pt.data(), sizeof(int2) * pt.size());
+    }
+    unsigned char* dstage = nullptr;
+    if (rc == VFPS_OK) {
+        const size_t jo = align_up(img.size(), kAlign);
+        unsigned char* d = nullptr;
+        cudaError_t e = cudaMallocAsync((void**)&d, jo + sizeof(CopyJob) * jobs.size(), b->adm);
+        if (e == cudaSuccess) {
+            for (CopyJob& j : jobs) j.src = (const unsigned int*)(d + (uintptr_t)j.src);
+            e = cudaMemcpyAsync(d, img.data(), img.size(), cudaMemcpyHostToDevice, b->adm);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(d + jo, jobs.data(), sizeof(CopyJob) * jobs.size(), cudaMemcpyHostToDevice, b->adm);
+            if (e == cudaSuccess) {
+                scatter_kernel<<<(unsigned)jobs.size(), 128, 0, b->adm>>>((const CopyJob*)(d + jo));
+                e = cudaGetLastError();
+            }
+            dstage = d;
+        }
+        if (e != cudaSuccess) {
+            note_cuda_error(e, "vfps_batch_add_many tables");
+            rc = VFPS_ECUDA;
+        }
+    }
+    if (rc == VFPS_OK) rc = upload_states(made.data(), count, psi0, b->adm);
+    if (rc == VFPS_OK) {
+        Group g = single_group(*made[0]);
+        g.ddescs = dstage + o_descs;
+        g.dtiles = (int2*)(dstage + o_tiles);
+        g.ntiles = g.grid = ptiles;
+        rc = launch_project(g, b->adm);
+    }
+    if (dstage) cudaFreeAsync(dstage, b->adm);
     if (rc == VFPS_OK && (cudaEventRecord(b->adm_ev, b->adm) != cudaSuccess ||
                           cudaStreamWaitEvent(b->stream, b->adm_ev, 0) != cudaSuccess))
         rc = VFPS_ECUDA;

@@ -520,9 +520,11 @@ __device__ __forceinline__ void drift_column(const float* __restrict__ ring, int
 }
 
 // Moment-recording steps only: for the ncols columns from xs that this CTA
-// has just written to out, sum_y p_y psi_c(y) and sum_y p_y^2 psi_c(y) (FP32
-// lane partials, FP64 across lanes) into D.colmom[2x], [2x+1]; p_y = (y - c)
-// Delta.  Warp w takes columns xs+w, xs+w+W, ...
+// has just written to out, sum_y p_y psi_c(y) and sum_y p_y^2 psi_c(y) into
+// D.colmom[2x], [2x+1] (p_y = (y - c) Delta).  FP32 within a column (lane
+// partials, then across lanes -- on this GPU's FP64 pipe, two FP64 shuffle
+// trees per column cost more than the pass itself), FP64 across columns in
+// the finaliser.  Warp w takes columns xs+w, xs+w+W, ...
 __device__ __noinline__ void strip_p_moments(const Desc<float>& D, const float* out, int xs, int ncols, int n, int ld)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -536,15 +538,14 @@ __device__ __noinline__ void strip_p_moments(const Desc<float>& D, const float* 
             a1 += pv;
             a2 = fmaf(p, pv, a2);
         }
-        double s1 = double(a1), s2 = double(a2);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            s1 += __shfl_down_sync(0xffffffffu, s1, o);
-            s2 += __shfl_down_sync(0xffffffffu, s2, o);
+            a1 += __shfl_down_sync(0xffffffffu, a1, o);
+            a2 += __shfl_down_sync(0xffffffffu, a2, o);
         }
         if (lane == 0) {
-            D.colmom[2 * x] = s1;
-            D.colmom[2 * x + 1] = s2;
+            D.colmom[2 * x] = double(a1);
+            D.colmom[2 * x + 1] = double(a2);
         }
     }
 }

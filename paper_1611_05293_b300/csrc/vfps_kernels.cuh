@@ -984,20 +984,27 @@ spectrogram_kernel(const SpecSeries* __restrict__ series, int L, int hop, double
 // Host <-> device state transfers of many simulations at once.
 //
 // Upload: staged FP64 states (host copies in one block) are normalised to
-// charge 1 on the device.  stage_sum_kernel: one CTA per state, FP64 sum of
-// its n*n values in a fixed order (thread t adds t, t+256, ...; then a fixed
-// tree) and whether all are finite: sums[2i], sums[2i+1].
+// charge 1 on the device.  The charge of a state is summed in a fixed order
+// that does not depend on how many states a call uploads: kStageParts
+// consecutive parts of its n*n values, each summed by one CTA (thread t adds
+// t, t+256, ... of its part, then a fixed tree), then the parts in order
+// (stage_combine_kernel).  A part spread over kStageParts CTAs keeps a single
+// upload short (FP64 adds are slow on this GPU).  Whether every value is
+// finite is recorded beside: sums[2i] = charge sum, sums[2i+1] = 1 or 0.
+constexpr int kStageParts = 16;
+
 __global__ void __launch_bounds__(256)
-stage_sum_kernel(const double* __restrict__ src, long long per_state, double* __restrict__ sums)
+stage_sum_kernel(const double* __restrict__ src, long long per_state, double* __restrict__ parts)
 {
     __shared__ double part[256];
     __shared__ int bad;
-    const double* v = src + (size_t)blockIdx.x * per_state;
+    const long long lo = per_state * blockIdx.x / kStageParts, hi = per_state * (blockIdx.x + 1) / kStageParts;
+    const double* v = src + (size_t)blockIdx.y * per_state;
     if (threadIdx.x == 0) bad = 0;
     __syncthreads();
     double acc = 0.0;
     bool fin = true;
-    for (long long i = threadIdx.x; i < per_state; i += 256) {
+    for (long long i = lo + threadIdx.x; i < hi; i += 256) {
         const double x = v[i];
         fin = fin && isfinite(x);
         acc += x;
@@ -1010,9 +1017,25 @@ stage_sum_kernel(const double* __restrict__ src, long long per_state, double* __
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        sums[2 * blockIdx.x] = part[0];
-        sums[2 * blockIdx.x + 1] = bad ? 0.0 : 1.0;
+        double* o = parts + 2 * ((size_t)blockIdx.y * kStageParts + blockIdx.x);
+        o[0] = part[0];
+        o[1] = bad ? 0.0 : 1.0;
     }
+}
+
+__global__ void __launch_bounds__(256)
+stage_combine_kernel(const double* __restrict__ parts, int count, double* __restrict__ sums)
+{
+    const int i = blockIdx.x * 256 + threadIdx.x;
+    if (i >= count) return;
+    const double* p = parts + 2 * (size_t)i * kStageParts;
+    double acc = 0.0, ok = 1.0;
+    for (int k = 0; k < kStageParts; ++k) {
+        acc += p[2 * k];
+        ok = p[2 * k + 1] == 1.0 ? ok : 0.0;
+    }
+    sums[2 * i] = acc;
+    sums[2 * i + 1] = ok;
 }
 
 // One state of a transfer: its device psi (row pitch ld), grid size, and the
@@ -1062,6 +1085,22 @@ stage_load_kernel(double* __restrict__ dst, const StateJob<T>* jobs)
         const int x = (int)(i / j.n), y = (int)(i - (long long)x * j.n);
         dst[j.off + i] = (double)src[(size_t)x * j.ld + y] * scale;
     }
+}
+
+// Scatter of a staged block of small tables (twiddles, impedance, tile and
+// segment lists, state word, descriptor) to their places in many
+// instances' memory: one CTA per piece, 4-byte words (every piece is a
+// multiple of 4 bytes and 4-byte aligned at both ends).
+struct CopyJob {
+    const unsigned int* src;
+    unsigned int* dst;
+    long long words;
+};
+
+__global__ void __launch_bounds__(128) scatter_kernel(const CopyJob* __restrict__ jobs)
+{
+    const CopyJob j = jobs[blockIdx.x];
+    for (long long i = threadIdx.x; i < j.words; i += 128) j.dst[i] = j.src[i];
 }
 
 // Ring entries [lo_i, lo_i + cnt_i) of each state's CSR-power and charge
