@@ -288,6 +288,8 @@ int vfps_batch_add(vfps_batch* b, const vfps_params* params, const double* psi0,
  *         Gaussians); pinned memory makes the copy run at link speed;
  *   model: 0, 1 or 2 for every slot; Pi, S_csr: host, count values each;
  *   slots: host, receives the count slot ids.
+ * The slots share one device allocation, returned when the last of them is
+ * removed (each slot's bytes still leave the budget when it is removed).
  * All or nothing: on any error no slot is added.  Errors: EINVAL (a
  * non-finite value or non-positive charge in any state, bad arguments),
  * EBUSY (free slots or memory budget), ENOMEM, ECUDA. */

@@ -1581,7 +1581,12 @@ int vfps_load_checkpoint(vfps_handle* h, const void* buf, int64_t bytes)
     vfps_checkpoint_head hd;
     std::memcpy(&hd, buf, sizeof(hd));
     const size_t es = elem_size(&I.p);
-    if (std::memcmp(hd.magic, "VFPSCKP1", 8) || std::memcmp(&hd.params, &I.p, sizeof(vfps_params)) ||
+    const vfps_params &a = hd.params, &q = I.p;  // field by field: the struct has padding bytes
+    const bool same = a.n == q.n && a.steps_per_period == q.steps_per_period && a.interp_points == q.interp_points &&
+                      a.clamp == q.clamp && a.fp_derivative == q.fp_derivative && a.pad_factor == q.pad_factor &&
+                      a.precision == q.precision && a.renormalize == q.renormalize && a.rotation == q.rotation &&
+                      a.half_width == q.half_width && a.beta == q.beta;
+    if (std::memcmp(hd.magic, "VFPSCKP1", 8) || !same ||
         hd.model != I.model || hd.Pi != I.Pi || hd.S != I.S || hd.n != I.n || hd.ld != I.ld || hd.M != I.M ||
         hd.es != (int32_t)es || bytes < (int64_t)checkpoint_bytes(I) || hd.st.parity < 0 || hd.st.parity > 1 ||
         hd.st.t < 0)

@@ -347,3 +347,60 @@ def test_bulk_add_and_take_equal_single_calls(V):
         assert np.array_equal(power[i], ref[i]["power"]), i
         assert np.array_equal(many.take(sm[i])["psi"], ref[i]["psi"]), i
     many.close()
+
+
+def test_bulk_edges_and_mixed_precision(V):
+    """vfps_batch_add_many refuses a request larger than the free slots
+    (EBUSY, nothing added); vfps_batch_take_many gathers FP32 and FP64 slots
+    of different grid sizes in one call, each equal to its own take."""
+    p32 = V.Params(n=48, steps_per_period=300, beta=1e-2)
+    p64 = V.Params(n=48, steps_per_period=300, beta=1e-2, precision=1)
+    b = V.Batch(4)
+    with pytest.raises(V.VfpsError) as e:
+        b.add_many(p32, None, V.IMPEDANCE_FREE_SPACE, [0.0] * 5, [0.4] * 5, 10)
+    assert e.value.code == V.EBUSY and b.usage()[0] == 0
+    s32 = b.add_many(p32, None, V.IMPEDANCE_FREE_SPACE, [0.0, 0.0], [0.4, 0.8], 25)
+    s64 = b.add_many(p64, None, V.IMPEDANCE_FREE_SPACE, [0.0], [0.6], 25)
+    b.run(25)
+    slots = s32 + s64
+    out = np.empty((3, 48, 48))
+    power = b.take_many(slots, psi_out=out, power_cap=25)
+    for i, sl in enumerate(slots):
+        r = b.take(sl)
+        assert np.array_equal(out[i], r["psi"]) and np.array_equal(power[i], r["power"]), sl
+    b.close()
+
+
+def test_recording_slot_leaves_the_pair_kernel(V):
+    """With pairing on, a slot that records moments runs in the single-
+    simulation kernel (the pair kernel has no moment pass) and both slots
+    keep the bits of their solo runs."""
+    n, spp = 64, 500
+    params = V.Params(n=n, steps_per_period=spp, beta=1e-2)
+    b = V.Batch(2)
+    b.pairing(True)
+    sa = b.add(params, None, V.IMPEDANCE_PARALLEL_PLATES, 2.0, 0.9, nsteps=40)
+    sb = b.add(params, None, V.IMPEDANCE_PARALLEL_PLATES, 2.0, 1.1, nsteps=40)
+    b.record_moments(sb, 8)
+    b.run(1)
+    assert not any(g["paired"] for g in b.shapes())
+    b.run(39)
+    got = {sa: b.take(sa), sb: b.take(sb)}
+    rec = b.moment_series(sb)
+    b.close()
+    assert rec.shape == (5, 5)
+    for sl, S in ((sa, 0.9), (sb, 1.1)):
+        psi_a, p_a = alone(V, n, spp, S, 2.0, 40, None)
+        assert np.array_equal(got[sl]["psi"], psi_a) and np.array_equal(got[sl]["power"], p_a)
+
+
+def test_spectrogram_rejects_bad_windows(V):
+    sim = V.Simulation(V.Params(n=32, steps_per_period=200, beta=1e-2), None)
+    sim.set_impedance(V.IMPEDANCE_FREE_SPACE, 0.0, 0.5)
+    sim.step(300)
+    for L, hop, count in ((100, 10, 2), (256, 0, 2), (256, 16, 0), (256, 64, 2)):  # not 2^k, hop, count, span
+        with pytest.raises(V.VfpsError) as e:
+            sim.spectrogram(L, hop, count)
+        assert e.value.code == V.EINVAL, (L, hop, count)
+    assert sim.spectrogram(256, 44, 2).shape == (2, 129)
+    sim.close()

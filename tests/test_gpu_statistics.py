@@ -11,6 +11,16 @@ seeded starts; these tests run the CUDA path through the C ABI and compare.
 * C2: one N = 256 simulation, 1000 steps/period, 50 periods, Pi = 2,
   S_csr = 0.9 (above the ~0.74 threshold): mean CSR power over the second
   half and the frequency of its strongest line within 2 %.
+* C5: one N = 1024 simulation, 4000 steps/period, Pi = 1, S_csr = 3 (deep
+  bursting), Gaussian start, against the oracle's same 40 periods: the
+  frequency of the slow bursting line (the strongest below 0.5 cycles per
+  period in periods 20-40, ~0.075: a bursting period of ~13 T_s) within 2 %,
+  the mean CSR power over periods 10-40 within 2 %, and the median
+  fluctuation envelope over periods 20-40 within 10 %.  The run is chaotic
+  from period 2 on and not stationary, so a mean is a statistic only over a
+  window of at least two bursting cycles (periods 10-40: 2.2 cycles; over
+  periods 20-40, 1.5 cycles, the two sides sample different phases of the
+  cycle and differ by 12 %).
 * C3: the 63-point threshold scan (N = 256, S_csr in linspace(0.2, 1.5, 21)
   x Pi in {1, 2, 3}, 1000 steps/period, 20 periods) in one batch, plus a
   duplicate point as an in-batch determinism probe: the threshold per Pi
@@ -114,3 +124,29 @@ def test_c3_threshold_scan_matches_oracle_scan(V):
             m_gpu = P[i][: spp * periods].reshape(periods, spp).mean(axis=1)
             m_ref = np.asarray(pts[i]["period_stats"])[:, 0]
             assert np.max(np.abs(m_gpu - m_ref) / m_ref) < 1e-3, (Pi, pts[i]["S_csr"])
+
+
+def test_c5_large_grid_statistics_match_oracle(V):
+    g = golden("c5")
+    n, spp, beta, periods = g["n"], g["steps_per_period"], g["beta"], g["periods"]
+    sim = V.Simulation(V.Params(n=n, steps_per_period=spp, beta=beta), W.noisy_gaussian(n, g["seed"], 1e-6))
+    sim.set_impedance(V.IMPEDANCE_PARALLEL_PLATES, g["Pi"], g["S_csr"])
+    P = []
+    for _ in range(periods):
+        sim.step(spp)
+        P.append(sim.csr_power())
+    sim.close()
+    P = np.concatenate(P)
+    assert len(P) == spp * periods
+    ref = np.asarray(g["period_stats"])
+    mean_gpu, mean_ref = P[10 * spp:].mean(), ref[10:, 0].mean()
+    env_gpu = np.median(A.fluctuation(P, spp)[20:40])
+    env_ref = np.median(ref[20:40, 1] / ref[20:40, 0])
+    slow_gpu = next(f for f, _ in G.spectrum_lines(P[20 * spp:40 * spp], spp, 10) if f < 0.5)
+    slow_ref = next(f for f, _ in g["periods_20_40"]["lines"] if f < 0.5)
+    print(f"C5: mean P (periods 10-40) {mean_gpu:.6e} vs {mean_ref:.6e}; envelope {env_gpu:.4f} vs {env_ref:.4f}; "
+          f"bursting line {slow_gpu:.5f} vs {slow_ref:.5f} cycles/period")
+    assert A.is_bursting(P, spp, first=20, last=40)
+    assert abs(slow_gpu - slow_ref) <= 0.02 * slow_ref, (slow_gpu, slow_ref)
+    assert abs(mean_gpu - mean_ref) <= 0.02 * mean_ref, (mean_gpu, mean_ref)
+    assert abs(env_gpu - env_ref) <= 0.1 * env_ref, (env_gpu, env_ref)
