@@ -109,8 +109,25 @@ int vfps_set_impedance(vfps_handle* h, int model, double Pi, double S_csr,
                        const double* table_re_im);
 
 /* Advance by nsteps >= 0 time steps (asynchronous on the handle's stream).
- * Errors: EINVAL, ECUDA, ENAN (reported by the next synchronising call). */
+ * A simulation on the FP32 register-blocked kernel whose CTAs, plus one,
+ * fit on the device at once steps in persistent cooperative launches of up
+ * to 256 steps (vfps_step_mode): worker CTAs and one finaliser CTA meet on
+ * two counters of the state word, so the wake transform of one step runs
+ * while the workers load and rotate the next; the results are the same bits
+ * as one launch per step.  Every device wait of such a launch is bounded
+ * (VFPS_SPIN_LIMIT polls, about a second by default); a wait that runs out
+ * ends the launch with status ETIMEOUT, after which the simulation's state
+ * is undefined (destroy the handle; the CUDA context stays usable).
+ * VFPS_PERSISTENT=0 in the environment at vfps_create keeps one launch per
+ * step.
+ * Errors: EINVAL, ECUDA, ENAN and ETIMEOUT (reported by the next
+ * synchronising call). */
 int vfps_step(vfps_handle* h, int64_t nsteps);
+
+/* *persistent = 1 when vfps_step runs this simulation in persistent
+ * launches, 0 when it launches one kernel (or CUDA graph node) per step.
+ * Errors: EINVAL. */
+int vfps_step_mode(vfps_handle* h, int32_t* persistent);
 
 /* rho_out (host, n doubles): profile rho(q_i) = Delta sum_j psi_ij of the
  * current state.  Synchronises.  Errors: EINVAL, ECUDA, ENAN. */

@@ -42,7 +42,12 @@ namespace {
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kRingDefault = 1 << 15;  // CSR-power ring entries per simulation
 constexpr int kGraphSteps = 32;        // launches per captured CUDA graph
+constexpr int kPersistSteps = 256;     // steps per persistent launch (lone simulations)
+// polls of a bounded device wait before it gives up with VFPS_ETIMEOUT (each
+// poll an acquire load and a short sleep: about a second in all)
+constexpr unsigned kSpinLimitDefault = 1u << 21;
 constexpr size_t kAlign = 256;
+constexpr int kInstanceSlots = 16;     // buffers of one instance's allocation
 
 thread_local char g_last_error[256] = "";
 
@@ -285,6 +290,11 @@ struct Instance {
     void* kick = nullptr;
     void* kickw = nullptr;   // FP32: two float4 per column
     double* mom = nullptr;   // moments scratch: 3n column sums, then the 4 results
+    // persistent launches: tagged column-sum words, tagged kick records, step flags
+    unsigned long long* cword = nullptr;
+    unsigned long long* rword = nullptr;
+    unsigned long long* sword = nullptr;
+    unsigned* cflag = nullptr;
     double* pring = nullptr;
     double* qring = nullptr;
     DevState* st = nullptr;
@@ -305,7 +315,16 @@ struct Instance {
     long long mdrained = 0;       // states t <= mdrained are on the host (or not recorded)
     std::vector<double> mw;       // drained records: t, <q>, sigma_q, <p>, sigma_p
     size_t mw_taken = 0;
+    // bounded waits of persistent launches (vfps_create reads both from the
+    // environment: VFPS_SPIN_LIMIT, and the test hook VFPS_FAULT_NO_SIGNAL)
+    unsigned spin_limit = kSpinLimitDefault;
+    int fault_no_signal = 0;
 };
+
+// Persistent launches: tagged 64-bit words (2n column-sum halves, n kick
+// records, a scale per worker CTA -- at most n/2 + 1 of them), then a step
+// flag per worker CTA.
+size_t persist_bytes(int n) { return (size_t)(3 * n + n / 2 + 2) * 8 + (size_t)(n + 2) * 4; }
 
 size_t instance_bytes(const vfps_params* p, int ring, size_t* offs)
 {
@@ -334,6 +353,7 @@ size_t instance_bytes(const vfps_params* p, int ring, size_t* offs)
     take(12, (size_t)n * 32);            // kick table (FP32 path)
     take(13, (size_t)(3 * n + 4) * 8);   // moments scratch
     take(14, sizeof(int4) * (size_t)((n + 1) / 2 + 1));  // FP32-kernel segments (W >= 2)
+    take(15, persist_bytes(n));          // persistent launches: tagged words, step flags
     return align_up(o, kAlign);
 }
 
@@ -353,7 +373,13 @@ void fill_desc(Instance& I)
     d.qring = I.qring;
     d.mring = I.mring;
     d.colmom = I.mom;  // the moments scratch (3n + 4 doubles) holds the 2n column sums
+    d.cword = I.cword;
+    d.rword = I.rword;
+    d.sword = I.sword;
+    d.cflag = I.cflag;
     d.mom_every = I.mring ? I.mom_every : 0;
+    d.spin_limit = I.spin_limit;
+    d.fault_no_signal = I.fault_no_signal;
     d.st = I.st;
     d.n = I.n;
     d.ld = I.ld;
@@ -636,6 +662,10 @@ void set_pointers(Instance& I, unsigned char* b, const size_t* offs)
     I.kickw = b + offs[12];
     I.mom = (double*)(b + offs[13]);
     I.dsegs = (int4*)(b + offs[14]);
+    I.cword = (unsigned long long*)(b + offs[15]);
+    I.rword = I.cword + 2 * (size_t)I.n;
+    I.sword = I.rword + (size_t)I.n;
+    I.cflag = reinterpret_cast<unsigned*>(I.sword + (size_t)I.n / 2 + 2);
 }
 
 // Host images of an instance's constant tables, in its own element type:
@@ -680,7 +710,7 @@ int create_instance(const vfps_params* p, const double* psi0, int ring, cudaStre
     I->ring = ring;
     I->delta = 2.0 * p->half_width / (p->n - 1);
     I->phi = 2.0 * kPi / p->steps_per_period;
-    size_t offs[15];
+    size_t offs[kInstanceSlots];
     I->dbytes = instance_bytes(p, ring, offs);
     if (arena) {  // a slice of a block the caller allocated and cleared
         I->arena = arena;
@@ -902,6 +932,47 @@ int launch_project(const Group& g, cudaStream_t s)
     return VFPS_EINVAL;
 }
 
+// Persistent launches of one lone FP32 simulation (step_persistent_f32), at
+// the widths a lone simulation takes (4 and 8) and the compiled grid sizes;
+// null where there is no such kernel.
+template <int W>
+const void* persist_fn_w(int kr, int n, int rot)
+{
+    if (kr == 8) {
+        if (n == 256)
+            return rot ? (const void*)step_persistent_f32<W, 8, 256, 1> : (const void*)step_persistent_f32<W, 8, 256, 0>;
+        if (n == 1024)
+            return rot ? (const void*)step_persistent_f32<W, 8, 1024, 1>
+                       : (const void*)step_persistent_f32<W, 8, 1024, 0>;
+        return rot ? (const void*)step_persistent_f32<W, 8, 0, 1> : (const void*)step_persistent_f32<W, 8, 0, 0>;
+    }
+    return rot ? (const void*)step_persistent_f32<W, 4, 0, 1> : (const void*)step_persistent_f32<W, 4, 0, 0>;
+}
+
+const void* persist_fn(const Group& g)
+{
+    if (!g.fast || g.pair) return nullptr;
+    if (g.W == 8) return persist_fn_w<8>(g.kr, g.n, g.rot);
+    if (g.W == 4) return persist_fn_w<4>(g.kr, g.n, g.rot);
+    return nullptr;
+}
+
+// K steps of a lone simulation in one cooperative launch: g.grid worker CTAs
+// and one finaliser CTA.  First every tagged word and step flag goes to 0
+// (a launch's own steps are tagged from 1; a launch that timed out leaves
+// them anyhow).
+int launch_persistent(const Group& g, const Instance& I, int K, cudaStream_t s)
+{
+    const void* f = persist_fn(g);
+    if (!f || K <= 0 || g.grid > I.n / 2 + 2) return VFPS_EINVAL;
+    CU(cudaMemsetAsync(I.cword, 0, persist_bytes(I.n), s));
+    const Desc<float>* d = (const Desc<float>*)g.ddescs;
+    const int4* sg = (const int4*)g.dsegs;
+    void* args[3] = {(void*)&d, (void*)&sg, (void*)&K};
+    CU(cudaLaunchCooperativeKernel(f, dim3(g.grid + 1), dim3(g.W * 32), args, g.smem, s));
+    return VFPS_OK;
+}
+
 // Allow every kernel variant the device's full opt-in shared memory (once,
 // before any launch or stream capture).
 template <typename K>
@@ -969,6 +1040,13 @@ int init_kernels()
     CU(set_smem_attr_one(step_kernel_f32<8, 8, 1024, 1>, lim));
     CU(set_smem_attr_one(step_kernel_f32<4, 8, 1024, 1>, lim));
     CU(set_smem_attr_one(step_kernel_f32<2, 8, 1024, 1>, lim));
+    for (int W : {4, 8})
+        for (int kr : {4, 8})
+            for (int n : {256, 1024, 0})
+                for (int rot : {0, 1}) {
+                    const void* f = W == 8 ? persist_fn_w<8>(kr, n, rot) : persist_fn_w<4>(kr, n, rot);
+                    CU(set_smem_attr_one(f, lim));
+                }
     CU(set_smem_attr_one(step_kernel_f32x2<8, 0>, lim));
     CU(set_smem_attr_one(step_kernel_f32x2<4, 0>, lim));
     CU(set_smem_attr_one(step_kernel_f32x2<2, 0>, lim));
@@ -1296,6 +1374,7 @@ struct vfps_handle {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     cudaGraphExec_t graph = nullptr;
+    int persist = -1;  // persistent launches: -1 not decided yet, 0 off, 1 on
 };
 
 extern "C" {
@@ -1354,7 +1433,18 @@ int vfps_create(const vfps_params* params, const double* psi0, void* cuda_stream
         return rc;
     }
     h->I = I;
-    rc = prologue(*I, h->stream);
+    // lone FP32 simulations step in persistent launches unless
+    // VFPS_PERSISTENT=0; the bounded waits of those launches give up after
+    // VFPS_SPIN_LIMIT polls, and VFPS_FAULT_NO_SIGNAL=1 (tests) makes the
+    // finaliser CTA withhold its kick tables so that they do
+    if (const char* e = std::getenv("VFPS_PERSISTENT")) h->persist = (e[0] == '0') ? 0 : -1;
+    if (const char* e = std::getenv("VFPS_SPIN_LIMIT")) {
+        const long long v = std::atoll(e);
+        if (v > 0 && v < (1LL << 31)) I->spin_limit = (unsigned)v;
+    }
+    if (const char* e = std::getenv("VFPS_FAULT_NO_SIGNAL")) I->fault_no_signal = (e[0] == '1');
+    rc = upload_desc(*I, h->stream);
+    if (rc == VFPS_OK) rc = prologue(*I, h->stream);
     if (rc) {
         destroy_instance(I);
         if (h->own_stream) cudaStreamDestroy(h->stream);
@@ -1393,12 +1483,28 @@ static int ensure_graph(vfps_handle* h)
     return VFPS_OK;
 }
 
+// Persistent launches apply when the simulation's kernel has a persistent
+// form and all its CTAs plus the finaliser fit on the device at once.
+static bool use_persistent(vfps_handle* h, const Group& g)
+{
+    if (h->persist < 0) {
+        h->persist = 0;
+        const void* f = persist_fn(g);
+        int per_sm = 0;
+        if (f && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, g.W * 32, g.smem) == cudaSuccess &&
+            (long long)per_sm * num_sms() >= (long long)g.grid + 1)
+            h->persist = 1;
+    }
+    return h->persist == 1;
+}
+
 int vfps_step(vfps_handle* h, int64_t nsteps)
 {
     if (!h || nsteps < 0) return VFPS_EINVAL;
     Range r("vfps_step");
     Instance& I = *h->I;
     Group g = single_group(I);
+    const bool persist = use_persistent(h, g);
     int rc;
     while (nsteps > 0) {
         // keep the ring from overwriting undrained entries
@@ -1409,7 +1515,11 @@ int vfps_step(vfps_handle* h, int64_t nsteps)
             continue;
         }
         long long chunk = std::min<long long>(nsteps, room);
-        if (chunk >= kGraphSteps) {
+        if (persist) {
+            chunk = std::min<long long>(chunk, kPersistSteps);
+            rc = launch_persistent(g, I, (int)chunk, h->stream);
+            if (rc) return rc;
+        } else if (chunk >= kGraphSteps) {
             rc = ensure_graph(h);
             if (rc) return rc;
             long long ng = chunk / kGraphSteps;
@@ -1628,6 +1738,13 @@ int vfps_steps_done(vfps_handle* h, int64_t* steps)
 {
     if (!h || !steps) return VFPS_EINVAL;
     *steps = h->I->steps_queued;
+    return VFPS_OK;
+}
+
+int vfps_step_mode(vfps_handle* h, int32_t* persistent)
+{
+    if (!h || !persistent) return VFPS_EINVAL;
+    *persistent = use_persistent(h, single_group(*h->I)) ? 1 : 0;
     return VFPS_OK;
 }
 
@@ -2209,7 +2326,7 @@ extern "C" {
 int64_t vfps_batch_slot_bytes(const vfps_params* params)
 {
     if (check_params(params)) return -1;
-    size_t offs[15];
+    size_t offs[kInstanceSlots];
     return (int64_t)instance_bytes(params, kRingDefault / 2, offs);
 }
 
@@ -2245,7 +2362,7 @@ int vfps_batch_add(vfps_batch* b, const vfps_params* params, const double* psi0,
             break;
         }
     if (free_slot < 0) return VFPS_EBUSY;
-    size_t offs[15];
+    size_t offs[kInstanceSlots];
     long long need = (long long)instance_bytes(params, kRingDefault / 2, offs);
     if (b->budget > 0 && b->used + need > b->budget) return VFPS_EBUSY;
     size_t fr = 0, tot = 0;
@@ -2345,7 +2462,7 @@ int vfps_batch_add_many(vfps_batch* b, int32_t count, const vfps_params* params,
     for (int i = 0; i < b->max_slots && (int)free_slots.size() < count; ++i)
         if (!b->slots[i]) free_slots.push_back(i);
     if ((int)free_slots.size() < count) return VFPS_EBUSY;
-    size_t offs[15];
+    size_t offs[kInstanceSlots];
     const long long need = (long long)instance_bytes(params, kRingDefault / 2, offs) * count;
     if (b->budget > 0 && b->used + need > b->budget) return VFPS_EBUSY;
     size_t fr = 0, tot = 0;

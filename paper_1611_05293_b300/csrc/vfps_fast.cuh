@@ -550,6 +550,96 @@ __device__ __noinline__ void strip_p_moments(const Desc<float>& D, const float* 
     }
 }
 
+// ----------------------------------------------------------------------------
+// Persistent launches (one lone simulation, K steps per launch; see
+// step_persistent_f32 for the protocol).
+struct PersistStep {
+    int k;          // step of this launch, 0 .. K-1
+    int par;        // psi[par] holds the state this step reads
+    long long t;    // steps done before this one
+};
+
+__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p)
+{
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int ld_volatile_s32(const int* p)
+{
+    int v;
+    asm volatile("ld.volatile.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// One poll step of a bounded wait: false once the wait has to give up (the
+// poll count reached D.spin_limit, or another CTA gave up: status
+// VFPS_ETIMEOUT, checked every 64 polls), after setting that status.  No
+// sleep between polls: each poll is a dependent L2 load, which paces the
+// loop (a sleeping poller noticed a new value microseconds late).
+#ifndef VFPS_POLL_NS
+#define VFPS_POLL_NS 0
+#endif
+__device__ __forceinline__ bool poll_on(const Desc<float>& D, unsigned& polls)
+{
+    ++polls;
+    if (polls >= D.spin_limit || ((polls & 63) == 0 && ld_volatile_s32(&D.st->status) == -4)) {
+        atomicExch(&D.st->status, -4);
+        return false;
+    }
+    if (VFPS_POLL_NS > 0) __nanosleep(VFPS_POLL_NS);
+    return true;
+}
+
+// Bounded wait of one thread for the tagged words p[0 .. NW-1] of launch
+// step tag (loaded together each poll); their values go to out.
+template <int NW>
+__device__ __forceinline__ bool wait_tagged(const Desc<float>& D, const unsigned long long* p, unsigned tag,
+                                            unsigned* out)
+{
+    unsigned polls = 0;
+    for (;;) {
+        unsigned long long w[NW];
+        bool all = true;
+#pragma unroll
+        for (int i = 0; i < NW; ++i) w[i] = ld_tagged(p + i);
+#pragma unroll
+        for (int i = 0; i < NW; ++i) all = all && (unsigned)(w[i] >> 32) == tag;
+        if (all) {
+#pragma unroll
+            for (int i = 0; i < NW; ++i) out[i] = (unsigned)w[i];
+            return true;
+        }
+        if (!poll_on(D, polls)) return false;
+    }
+}
+
+// Bounded wait of a whole CTA until the step flags D.cflag[c0 .. c1] are all
+// >= target (thread i polls flag c0 + i with relaxed loads, sleeping between
+// polls, then fences: acquire).  A thread gives up after D.spin_limit polls,
+// or as soon as another CTA has given up (status VFPS_ETIMEOUT, checked
+// every 64 polls), after setting that status.  Every thread gets the
+// outcome; after a true result the writes that preceded the matching flag
+// releases are visible to all threads of the CTA.
+__device__ __forceinline__ bool cta_wait_flags(const Desc<float>& D, int c0, int c1, unsigned target, int* s_ok)
+{
+    if (threadIdx.x == 0) *s_ok = 1;
+    __syncthreads();
+    for (int c = c0 + (int)threadIdx.x; c <= c1; c += blockDim.x) {
+        unsigned polls = 0;
+        bool ok = true;
+        while (ld_relaxed_u32(D.cflag + c) < target)
+            if (!(ok = poll_on(D, polls))) break;
+        if (!ok) {
+            *s_ok = 0;
+            break;
+        }
+        fence_acq_rel_gpu();
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
 // One strip of the streaming FP32 step: T consecutive W-column tiles of
 // simulation D from column xs.  The strip walks its tiles one by one.  The
 // slab columns live in a ring of R shared-memory slots (R >= 2W + 2h): while
@@ -560,8 +650,20 @@ __device__ __noinline__ void strip_p_moments(const Desc<float>& D, const float* 
 // The column sums of a strip are made visible with one fence per thread
 // before the CTA takes the simulation's ticket; the CTA that takes the last
 // ticket runs the finaliser.
-template <int W, int KR, int NC, int ROT>
-__device__ __forceinline__ void strip_f32(const Desc<float>& D, int xs, int T, unsigned char* smem, int& s_last)
+//
+// PERSIST (step ps->k of a persistent launch): the parity and step count come
+// from ps; the shared-memory prologue (zero padding, FP weights) runs on the
+// launch's first step only.  From the launch's second step on, the kick of a
+// column is not in the table yet when the strip starts: after rotating a
+// column, its warp waits for the column's kick record and the CTA's scale
+// word (lanes 0 and 1, bounded) and builds the kick entry from them (kick_entry, as the finaliser does for the
+// table).  Column sums go out as tagged words the finaliser CTA polls; at
+// the end the CTA sets its step flag instead of taking a ticket.
+// s_last is then the CTA's failure flag.  Returns false when a wait ran out
+// (status set).
+template <int W, int KR, int NC, int ROT, bool PERSIST = false>
+__device__ __forceinline__ bool strip_f32(const Desc<float>& D, int xs, int T, unsigned char* smem, int& s_last,
+                                          const PersistStep* ps = nullptr)
 {
     // NC > 0: the grid size is a compile-time constant (the hot sizes), so
     // loop bounds and pitches fold into the code; ld = n for FP32 then
@@ -586,7 +688,8 @@ __device__ __forceinline__ void strip_f32(const Desc<float>& D, int xs, int T, u
     float* colbcol = reinterpret_cast<float*>(reinterpret_cast<float4*>(gtab + 4 * n) + 8 * W) + warp * PA;
 
     // padding rows of every ring slot and of this warp's psi_a column: zero
-    // for the whole strip
+    // for the whole strip (a persistent launch: for all its steps)
+    if (!PERSIST || ps->k == 0) {
     for (int slot = warp; slot < R; slot += W)
         for (int r = lane; r < RP; r += 32) {
             ring[slot * P + r] = 0.f;
@@ -600,20 +703,25 @@ __device__ __forceinline__ void strip_f32(const Desc<float>& D, int xs, int T, u
 #pragma unroll
         for (int k = 0; k < 4; ++k) gtab[k * n + gi] = fp_weight(D, k, y);
     }
+    }
     // what the previous step wrote (state word, psi, kick table) is read from here on
-    pdl_wait();
-    const int par = D.st->parity;
+    if constexpr (!PERSIST) pdl_wait();
+    const int par = PERSIST ? ps->par : D.st->parity;
+    // kicks from the tagged records (persistent launch, not its first step)
+    const bool recs = PERSIST && ps->k > 0;
+    if (PERSIST && threadIdx.x == 0) s_last = 0;
     const float* __restrict__ in = D.psi[par];
     float* __restrict__ out = D.psi[par ^ 1];
     // a moment-recording step (the finaliser also needs each column's p-moments)
-    const bool mom_now = D.mom_every > 0 && (D.st->t + 1) % D.mom_every == 0;
+    const long long t_step = PERSIST ? ps->t : D.st->t;
+    const bool mom_now = D.mom_every > 0 && (t_step + 1) % D.mom_every == 0;
     // window of tile 0, then the new columns of tile 1
     load_columns<W>(ring, R, P, RP, in, ld, n, xs - h, W + 2 * h);
-    load_kick(kbuf, kickw, xs + warp, n, lane);
+    if (!recs) load_kick(kbuf, kickw, xs + warp, n, lane);
     cp_async_commit();
     if (T > 1) {
         load_columns<W>(ring, R, P, RP, in, ld, n, xs + W + h, W);
-        load_kick(kbuf + 2 * W, kickw, xs + W + warp, n, lane);
+        if (!recs) load_kick(kbuf + 2 * W, kickw, xs + W + warp, n, lane);
     }
     cp_async_commit();
 
@@ -683,10 +791,30 @@ __device__ __forceinline__ void strip_f32(const Desc<float>& D, int xs, int T, u
             __syncwarp();
             kcol = colbcol;
         }
-        if (active) {
+        bool kick_ok = true;
+        float4 kw = make_float4(0.f, 0.f, 0.f, 0.f);
+        int s = 0;
+        if (active && recs) {
+            // the kick of column x and the pending scale of this step: the
+            // finaliser CTA's records (lane 0 and lane 1 wait)
+            unsigned r = 0;
+            bool ok = true;
+            if (lane < 2) ok = wait_tagged<1>(D, lane == 0 ? D.rword + x : D.sword + blockIdx.x, (unsigned)ps->k, &r);
+            const unsigned rk = __shfl_sync(0xffffffffu, r, 0), rs = __shfl_sync(0xffffffffu, r, 1);
+            kick_ok = __shfl_sync(0xffffffffu, (int)ok, 0) && __shfl_sync(0xffffffffu, (int)ok, 1);
+            if (kick_ok) {
+                const KickEntry e = kick_entry(__uint_as_float(rk), __uint_as_float(rs));
+                kw = e.w;
+                s = e.s;
+            } else if (lane == 0) {
+                s_last = 1;
+            }
+        } else if (active) {
             const float4* kj = kbuf + 2 * W * (j & 3);
-            const float4 kw = kj[0];
-            const int s = __float_as_int(kj[1].x);
+            kw = kj[0];
+            s = __float_as_int(kj[1].x);
+        }
+        if (active && kick_ok) {
             float* dst = out + (size_t)x * ld;
             float lsum = 0.f;
             if (s >= -4 && s <= 4) {
@@ -730,12 +858,25 @@ __device__ __forceinline__ void strip_f32(const Desc<float>& D, int xs, int T, u
             double csum = double(lsum);  // FP32 lane partials, FP64 across lanes
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) csum += __shfl_down_sync(0xffffffffu, csum, o);
-            if (lane == 0) colsum[x] = csum;
+            if (lane == 0) {
+                if constexpr (PERSIST) {
+                    // the two tagged words (low, high half) the finaliser CTA polls
+                    const unsigned long long b = (unsigned long long)__double_as_longlong(csum);
+                    st_tagged(D.cword + 2 * (size_t)x, (unsigned)b, (unsigned)ps->k + 1u);
+                    st_tagged(D.cword + 2 * (size_t)x + 1, (unsigned)(b >> 32), (unsigned)ps->k + 1u);
+                } else {
+                    colsum[x] = csum;
+                }
+            }
         }
         __syncthreads();  // the ring slots of columns xs+jW-h .. xs+jW+W-h-1 are free
+        if (PERSIST && s_last) {  // a kick record never came
+            cp_async_wait_0();
+            return false;
+        }
         if (j + 2 < T) {
             load_columns<W>(ring, R, P, RP, in, ld, n, xs + (j + 2) * W + h, W);
-            load_kick(kbuf + 2 * W * ((j + 2) & 3), kickw, xs + (j + 2) * W + warp, n, lane);
+            if (!recs) load_kick(kbuf + 2 * W * ((j + 2) & 3), kickw, xs + (j + 2) * W + warp, n, lane);
         }
         cp_async_commit();
     }
@@ -744,8 +885,17 @@ __device__ __forceinline__ void strip_f32(const Desc<float>& D, int xs, int T, u
     // after the loop (every tile ended with a barrier, so all are written),
     // keeping the hot loop free of the extra work
     if (mom_now) strip_p_moments(D, out, xs, T * W, n, ld);
-    __threadfence();  // this thread's column sums, before the ticket
+    // this thread's columns and column sums, before the ticket (persistent:
+    // before the arrival count)
+    if constexpr (PERSIST) fence_acq_rel_gpu();
+    else __threadfence();
     __syncthreads();
+    if constexpr (PERSIST) {
+        // this CTA has written its columns of step k (its flag: k + 1)
+        if (threadIdx.x == 0) asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(D.cflag + blockIdx.x),
+                                           "r"((unsigned)ps->k + 1u) : "memory");
+        return true;
+    }
 #ifdef VFPS_DEBUG
     if (threadIdx.x == 0 && s_dbg_site) D.st->status = -100 - s_dbg_site;
 #endif
@@ -758,6 +908,7 @@ __device__ __forceinline__ void strip_f32(const Desc<float>& D, int xs, int T, u
         __threadfence();
         finalise<float>(D, smem, 1);
     }
+    return true;
 }
 
 // Streaming FP32 step.  CTA b walks its segments segs[b*spc .. b*spc+spc-1]
@@ -787,6 +938,89 @@ step_kernel_f32(const Desc<float>* __restrict__ descs, const int4* __restrict__ 
         if (sg.z <= 0) break;
         if (i > 0) __syncthreads();  // shared memory of the previous strip (or its finaliser) is free
         strip_f32<W, KR, NC, ROT>(descs[sg.x], sg.y, sg.z, smem, s_last);
+    }
+}
+
+// Persistent step of one lone simulation: K steps in one cooperative launch
+// (all CTAs resident).  CTAs 0 .. G-2 are workers, one strip each of T tiles
+// (segs, as for step_kernel_f32 with one segment per CTA, all of one length);
+// CTA G-1 is the finaliser.  Before the launch the host sets every worker's
+// step flag and every tagged word (column sums, kick records) to 0.
+//  * Worker b, step k: wait until the workers whose columns its window reads
+//    (columns xs - h .. xs + W T + h - 1) have finished step k-1 (flags >=
+//    k: those columns of psi_k are written, and those CTAs no longer read
+//    the columns this step overwrites -- the windows are symmetric); load
+//    and rotate; for k > 0 wait for the column's kick record and the CTA's
+//    scale word tagged k; kick, damp and diffuse; write the column sums
+//    (two words each, tagged k+1); fence; flag k+1.
+//  * Finaliser, step k: take each column sum as soon as both its words carry
+//    tag k+1; on moment-recording steps also wait for every worker's flag (the
+//    p-moment sums); run the finaliser arithmetic of the ticketed kernel
+//    (finalise_compute: charge, scale, transforms, wake, power, series, step
+//    count, parity), which also writes the kick records tagged k+1.
+// The tagged words need no fence: only the step flags, which publish psi,
+// are released with one (off the critical path while a worker rotates).
+// So the transform of step k runs while the workers load and rotate step
+// k+1, with the same arithmetic in the same order as K launches of
+// step_kernel_f32; the twiddles and impedance stay in shared memory for the
+// whole launch.  Every wait is bounded (spin_limit polls) and gives up with
+// status VFPS_ETIMEOUT; the other CTAs then give up within 64 polls.
+template <int W, int KR, int NC, int ROT>
+__global__ void __launch_bounds__(W * 32, 1)
+step_persistent_f32(const Desc<float>* __restrict__ descs, const int4* __restrict__ segs, int K)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_flag, s_fail;
+    // the descriptor, in shared memory for the whole launch: the waits' fences
+    // and asm memory clobbers would otherwise make every later field read a
+    // fresh global load, after an acquire an L2 round trip
+    __shared__ __align__(16) Desc<float> sD;
+    {
+        const int* src = reinterpret_cast<const int*>(descs);
+        int* dst = reinterpret_cast<int*>(&sD);
+        for (int i = threadIdx.x; i < (int)(sizeof(Desc<float>) / 4); i += blockDim.x) dst[i] = src[i];
+        __syncthreads();
+    }
+    const Desc<float>& D = sD;
+    const int nwork = gridDim.x - 1;
+    // parity and step count when the launch starts (the finaliser changes
+    // both only after every worker has written its step-0 columns)
+    const int par0 = D.st->parity;
+    const long long t0 = D.st->t;
+    if (blockIdx.x == gridDim.x - 1) {
+        const int n = D.n;
+        const FinSmem<float> L(smem, n, D.M / 2);
+        finalise_load<float>(D, smem, true, false);
+        for (int k = 0; k < K; ++k) {
+            if (threadIdx.x == 0) s_fail = 0;
+            __syncthreads();
+            for (int x = threadIdx.x; x < n; x += blockDim.x) {
+                unsigned v[2];
+                if (!wait_tagged<2>(D, D.cword + 2 * (size_t)x, (unsigned)k + 1u, v)) {
+                    s_fail = 1;
+                    break;
+                }
+                L.cs[x] = __longlong_as_double((long long)(((unsigned long long)v[1] << 32) | v[0]));
+            }
+            __syncthreads();
+            if (s_fail) return;
+            const bool mom_now = D.mom_every > 0 && D.mring && (t0 + k + 1) % D.mom_every == 0;
+            if (mom_now && !cta_wait_flags(D, 0, nwork - 1, (unsigned)k + 1u, &s_flag)) return;
+            finalise_compute<float>(D, smem, 1, D.fault_no_signal ? 0u : (unsigned)(k + 1), nwork);
+        }
+        return;
+    }
+    const int4 sg = segs[blockIdx.x];
+    // workers whose columns this strip's window reads (strips of W sg.z columns)
+    const int span = W * sg.z, h = D.h;
+    const int c0 = max(0, (sg.y - h) / span), c1 = min(nwork - 1, (sg.y + span + h - 1) / span);
+    PersistStep ps;
+    for (int k = 0; k < K; ++k) {
+        if (k > 0 && !cta_wait_flags(D, c0, c1, (unsigned)k, &s_flag)) return;
+        ps.k = k;
+        ps.par = par0 ^ (k & 1);
+        ps.t = t0 + k;
+        if (!strip_f32<W, KR, NC, ROT, true>(D, sg.y, sg.z, smem, s_fail, &ps)) return;
     }
 }
 

@@ -57,7 +57,6 @@ struct DevState {
     unsigned int ticket; // CTAs of the current step that have finished
     int parity;          // psi[parity] holds the current state
     int status;          // 0 or a negative VFPS_E* code
-    int pad;
 };
 
 template <typename T>
@@ -73,8 +72,17 @@ struct Desc {
     double* qring;
     double* mring;                     // moments ring (4 doubles per step), or null
     double* colmom;                    // 2n: per column sum p psi and sum p^2 psi (moment steps)
+    // persistent launches (see step_persistent_f32): tagged words -- 2n for
+    // the column sums (low, high half), n kick records, a scale per worker
+    // CTA -- and a step flag per worker CTA
+    unsigned long long* cword;
+    unsigned long long* rword;
+    unsigned long long* sword;
+    unsigned* cflag;
     DevState* st;
     int mom_every;                     // record moments of psi_t when t % mom_every == 0 (0: off)
+    unsigned spin_limit;               // persistent launches: polls of a wait before VFPS_ETIMEOUT
+    int fault_no_signal;               // test hook: the finaliser CTA never publishes (waits run out)
     int n, ld, M, logM;
     int ring_mask, renorm, clamp, h;  // h: column halo of the staged slab
     int ntiles;                        // CTAs per step of this instance
@@ -265,6 +273,44 @@ template <typename T2> __device__ __forceinline__ T2 cmulc(T2 a, T2 b)  // a * c
     return {a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y};
 }
 
+// Kick-table entry of a column whose p-shift for the next step is k cells,
+// with the pending renormalisation factor sf folded into the weights:
+// psi_b(y) = sum_j w_j psi_a(y + s - 1 + j) (cubic, source y - k), s =
+// floor(-k).  Both the finaliser and the persistent workers (which rebuild
+// the entry from k and sf) compute it here.
+struct KickEntry {
+    float4 w;
+    int s;
+};
+__device__ __forceinline__ KickEntry kick_entry(float k, float sf)
+{
+    const float ks = -k, fk = floorf(ks);
+    float w[4];
+    lagrange_w<float, 4>(ks - fk, w);
+    return {make_float4(sf * w[0], sf * w[1], sf * w[2], sf * w[3]), int(fk)};
+}
+
+// Tagged words of persistent launches: 64 bits, a 32-bit value in the low
+// half and the launch step it belongs to (0: none yet) in the high half,
+// stored and loaded as one (relaxed, GPU scope: single-copy atomic), so that
+// a reader that sees the tag it waits for also sees that step's value -- no
+// fence and no reset between steps.
+__device__ __forceinline__ void st_tagged(unsigned long long* p, unsigned v, unsigned tag)
+{
+    const unsigned long long w = ((unsigned long long)tag << 32) | v;
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(w) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_tagged(const unsigned long long* p)
+{
+    unsigned long long w;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(w) : "l"(p) : "memory");
+    return w;
+}
+// Acquire-release fence at GPU scope: with a relaxed store after it, a
+// release; with a relaxed load before it, an acquire (lighter than
+// __threadfence, which is sequentially consistent).
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
 // ----------------------------------------------------------------------------
 // Finaliser: from the column sums of the state just written, compute the
 // charge, the pending scale, the profile rho, its zero-padded M-point
@@ -289,11 +335,16 @@ template <typename T2> __device__ __forceinline__ T2 cmulc(T2 a, T2 b)  // a * c
 // Shared memory (bytes) for FFT length M and n columns: two H-point complex
 // buffers, twiddles (H) and impedance (H+1) complex values, the n column
 // sums and H/2+1 power terms as doubles, and a reduction area.
+// Groups of the finaliser's FP64 sums (sum_groups): for count values, the
+// number of 256-value groups.
+__host__ __device__ inline int sum_groups(int count) { return (count + 255) >> 8; }
+
 __host__ __device__ inline size_t finalise_smem(int M, int n, int nt, int complex_bytes)
 {
     (void)nt;
     const size_t H = (size_t)M / 2;
-    return (4 * H + 2) * complex_bytes + (size_t)((n + 1) & ~1) * 8 + (H / 2 + 2) * 8 + 64;
+    const int G = sum_groups(n > (int)H / 2 + 1 ? n : (int)H / 2 + 1);
+    return (4 * H + 2) * complex_bytes + (size_t)((n + 1) & ~1) * 8 + (H / 2 + 2) * 8 + (12 + 2 * (size_t)G) * 8;
 }
 
 template <typename T2, bool INV>
@@ -544,42 +595,78 @@ __device__ __forceinline__ void moment_sums_warp(const double* cs, const double*
     }
 }
 
+// Shared-memory layout of the finaliser.
 template <typename T>
-__device__ void finalise(const Desc<T>& D, unsigned char* smem, int is_step)
+struct FinSmem {
+    using T2 = typename C2<T>::type;
+    T2 *bufA, *bufB, *tw, *zh;
+    double *cs, *pterm, *red;
+    __device__ FinSmem(unsigned char* smem, int n, int H)
+    {
+        bufA = reinterpret_cast<T2*>(smem);
+        bufB = bufA + H;
+        tw = bufB + H;
+        zh = tw + H;
+        cs = reinterpret_cast<double*>(zh + H + 2);  // n column sums
+        pterm = cs + ((n + 1) & ~1);                 // H/2+1 power terms
+        red = pterm + H / 2 + 2;
+    }
+};
+
+// One round of asynchronous copies into the finaliser's shared memory: the
+// twiddles and impedance (tables), the column sums (written by the other
+// CTAs of this step; .cg keeps L1 out of the way), or both.
+template <typename T>
+__device__ __forceinline__ void finalise_load(const Desc<T>& D, unsigned char* smem, bool tables, bool colsums)
+{
+    using T2 = typename C2<T>::type;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int n = D.n, H = D.M / 2;
+    const FinSmem<T> L(smem, n, H);
+    constexpr int CB = sizeof(T2);
+    const char* gtw = reinterpret_cast<const char*>(D.tw);
+    const char* gzh = reinterpret_cast<const char*>(D.zhat);
+    const char* gcs = reinterpret_cast<const char*>(D.colsum);
+    const int ntw = H * CB / 16, zbytes = (H + 1) * CB, nzh = (zbytes + 15) / 16;
+    const int cbytes = n * 8, ncs = (cbytes + 15) / 16;
+    if (tables) {
+        for (int i = tid; i < ntw; i += nt) cp_async16(reinterpret_cast<char*>(L.tw) + 16 * i, gtw + 16 * i, 16);
+        for (int i = tid; i < nzh; i += nt)
+            cp_async16(reinterpret_cast<char*>(L.zh) + 16 * i, gzh + 16 * i, min(16, zbytes - 16 * i));
+    }
+    if (colsums)
+        for (int i = tid; i < ncs; i += nt)
+            cp_async16(reinterpret_cast<char*>(L.cs) + 16 * i, gcs + 16 * i, min(16, cbytes - 16 * i));
+    cp_async_commit();
+    cp_async_wait_0();
+    __syncthreads();
+}
+
+// The finaliser's arithmetic, from the column sums, twiddles and impedance
+// in shared memory.  gen > 0 (persistent launches): also the kick records of
+// the launch's step gen, tagged words D.rword[x] = (kick of column x, gen)
+// and D.sword[b] = (pending scale, gen) for each worker CTA b < nscale,
+// written before the rest of the table.
+template <typename T>
+__device__ void finalise_compute(const Desc<T>& D, unsigned char* smem, int is_step, unsigned gen = 0,
+                                 int nscale = 0)
 {
     using T2 = typename C2<T>::type;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int n = D.n, M = D.M, H = M / 2;
-    T2* bufA = reinterpret_cast<T2*>(smem);
-    T2* bufB = bufA + H;
-    T2* tw = bufB + H;
-    T2* zh = tw + H;
-    double* cs = reinterpret_cast<double*>(zh + H + 2);  // n column sums
-    double* pterm = cs + ((n + 1) & ~1);                 // H/2+1 power terms
-    double* red = pterm + H / 2 + 2;
+    const FinSmem<T> L(smem, n, H);
+    T2* bufA = L.bufA;
+    T2* bufB = L.bufB;
+    T2* tw = L.tw;
+    T2* zh = L.zh;
+    double* cs = L.cs;
+    double* pterm = L.pterm;
+    double* red = L.red;
 
     // the step counter, read early (its latency overlaps the transforms)
     // (every thread reads it: the moment steps below depend on it, and thread
     // 0 only advances it after the last barrier)
     const long long t_now = D.st->t;
-    // one round of asynchronous copies: twiddles, impedance, column sums
-    // (written by the other CTAs of this step; .cg keeps L1 out of the way)
-    {
-        constexpr int CB = sizeof(T2);
-        const char* gtw = reinterpret_cast<const char*>(D.tw);
-        const char* gzh = reinterpret_cast<const char*>(D.zhat);
-        const char* gcs = reinterpret_cast<const char*>(D.colsum);
-        const int ntw = H * CB / 16, zbytes = (H + 1) * CB, nzh = (zbytes + 15) / 16;
-        const int cbytes = n * 8, ncs = (cbytes + 15) / 16;
-        for (int i = tid; i < ntw; i += nt) cp_async16(reinterpret_cast<char*>(tw) + 16 * i, gtw + 16 * i, 16);
-        for (int i = tid; i < nzh; i += nt)
-            cp_async16(reinterpret_cast<char*>(zh) + 16 * i, gzh + 16 * i, min(16, zbytes - 16 * i));
-        for (int i = tid; i < ncs; i += nt)
-            cp_async16(reinterpret_cast<char*>(cs) + 16 * i, gcs + 16 * i, min(16, cbytes - 16 * i));
-        cp_async_commit();
-        cp_async_wait_0();
-        __syncthreads();
-    }
     // transform input z_j = cs_2j + i cs_2j+1 (zero-padded), in T
     for (int j = tid; j < H; j += nt) {
         const int x = 2 * j;
@@ -587,64 +674,100 @@ __device__ void finalise(const Desc<T>& D, unsigned char* smem, int is_step)
     }
     __syncthreads();
 
-    // forward transform on all warps but the last, which meanwhile sums the
-    // charge Q = Delta^2 sum cs into red[0] in FP64 (FP64 adds are slow on the
-    // B300: the sum takes longer than a transform pass, so it runs beside
-    // the whole transform rather than inside one pass; a one-warp block runs
-    // the two in turn)
-    const int sum_warp = (nt >> 5) - 1, nfft = nt >= 64 ? nt - 32 : nt;
-    const bool fft_thread = nt < 64 || (tid >> 5) != sum_warp, sum_thread = (tid >> 5) == sum_warp;
+    // forward transform on the first warps while the last nsum warps sum the
+    // charge Q = Delta^2 sum cs in FP64 (FP64 adds are slow on the B300: a
+    // sum takes longer than a transform pass, so it runs beside the whole
+    // transform rather than inside one pass; a one-warp block runs the two in
+    // turn).  Each FP64 sum has a structure fixed by its length alone: groups
+    // of 256 consecutive values, each summed in the order of warp_fixed_sum,
+    // then the group sums added in order -- the sum warps take the groups in
+    // turn, so the bits do not depend on how many there are.
+    const int nw = nt >> 5, wid = tid >> 5;
+    const int Gc = sum_groups(n), Gp = sum_groups(H / 2 + 1);
+    const int nsum = nw == 1 ? 1 : max(1, min(max(Gc, Gp), nw / 2));
+    const int sw = nw == 1 ? 0 : wid - (nw - nsum);  // index among the sum warps, < 0 for the others
+    const bool sum_thread = sw >= 0, fft_thread = nw == 1 || sw < 0;
+    const int nfft = nw == 1 ? nt : nt - 32 * nsum;
+    double* gsum_c = red + 12;      // Gc group sums of the charge
+    double* gsum_p = gsum_c + Gc;   // Gp group sums of the power terms
     T2* Z = fft_result<T2>(bufB, bufA, bufB, H);
     if (fft_thread) fft_h_part<T, false>(bufB, bufA, bufB, tw, H, nfft);
     // (a moment-recording step also forms the moment sums there)
     const bool mom_now = is_step && D.mom_every > 0 && D.mring && (t_now + 1) % D.mom_every == 0;
     if (sum_thread) {
-        const double sum = warp_fixed_sum<double>(cs, n);
-        if ((tid & 31) == 0) red[0] = sum;
-        if (mom_now) moment_sums_warp(cs, D.colmom, n, D.delta, red);
+        for (int g = sw; g < Gc; g += nsum) {
+            const double sum = warp_fixed_sum<double>(cs + 256 * g, min(256, n - 256 * g));
+            if ((tid & 31) == 0) gsum_c[g] = sum;
+        }
+        if (nsum > 1) asm volatile("bar.sync 2, %0;" ::"r"(32 * nsum) : "memory");
+        if (tid == 32 * (nw - nsum)) {
+            // the charge, pending scale and profile factors, once, on the
+            // first sum warp while the transform runs (an FP64 division takes
+            // long on this GPU; every thread reads the results after the barrier)
+            double c = gsum_c[0];
+            for (int g = 1; g < Gc; ++g) c += gsum_c[g];
+            const double q = D.delta * D.delta * c;
+            const bool b = !(q > 0.0) || !isfinite(q);
+            const double s1 = (D.renorm && !b) ? 1.0 / q : 1.0;
+            red[0] = c;
+            red[8] = q;
+            red[9] = s1;
+            red[10] = s1 * D.delta;
+        }
+        if (mom_now && sw == 0) moment_sums_warp(cs, D.colmom, n, D.delta, red);
     }
     __syncthreads();
-    const double Q = D.delta * D.delta * red[0];
+    const double csum = red[0];
+    const double Q = red[8];
     const bool bad = !(Q > 0.0) || !isfinite(Q);
-    const double s_new = (D.renorm && !bad) ? 1.0 / Q : 1.0;
-    const double sd = s_new * D.delta;        // rho_x = sd * cs_x
+    const double s_new = red[9];
+    const double sd = red[10];                // rho_x = sd * cs_x
     const T sk = T(sd * D.delta);             // rho~_k = Delta * DFT(rho)_k = sk * X_k
 
     wake_pair_pass<T>(Z, tw, zh, H, sk, pterm, tid, nt);
     __syncthreads();
 
-    // inverse transform likewise, beside the FP64 sum of the power terms into
-    // red[1]
+    // inverse transform likewise, beside the FP64 sum of the power terms
     T2* const Zo = Z == bufA ? bufB : bufA;
     T2* y = fft_result<T2>(Z, Zo, Z, H);
     if (fft_thread) fft_h_part<T, true>(Z, Zo, Z, tw, H, nfft);
     if (sum_thread) {
-        const double sum = warp_fixed_sum<double>(pterm, H / 2 + 1);
-        if ((tid & 31) == 0) red[1] = sum;
+        for (int g = sw; g < Gp; g += nsum) {
+            const double sum = warp_fixed_sum<double>(pterm + 256 * g, min(256, H / 2 + 1 - 256 * g));
+            if ((tid & 31) == 0) gsum_p[g] = sum;
+        }
     }
     __syncthreads();
     const T kpv = T(D.kick_per_v * D.dkappa);
+    if constexpr (sizeof(T) == 4) {
+        if (gen) {
+            for (int x = tid; x < n; x += nt) {
+                const T2 v = y[x >> 1];
+                st_tagged(D.rword + x, __float_as_uint(kpv * ((x & 1) ? v.y : v.x)), gen);
+            }
+            const unsigned sfb = __float_as_uint(float(s_new));
+            for (int b = tid; b < nscale; b += nt) st_tagged(D.sword + b, sfb, gen);
+        }
+    }
     for (int x = tid; x < n; x += nt) {
         const T2 v = y[x >> 1];
         const T k = kpv * ((x & 1) ? v.y : v.x);
         D.kick[x] = k;
         D.rho[x] = sd * cs[x];
         if constexpr (sizeof(T) == 4) {
-            // psi_b(y) = sum_k w_k psi_a(y + s - 1 + k): source y - kick, s = floor(-kick)
-            const float ks = -k, fk = floorf(ks);
-            float w[4];
-            lagrange_w<float, 4>(ks - fk, w);
-            const float sf = float(s_new);
-            D.kickw[2 * x] = make_float4(sf * w[0], sf * w[1], sf * w[2], sf * w[3]);
-            D.kickw[2 * x + 1] = make_float4(__int_as_float(int(fk)), 0.f, 0.f, 0.f);
+            const KickEntry e = kick_entry(k, float(s_new));
+            D.kickw[2 * x] = e.w;
+            D.kickw[2 * x + 1] = make_float4(__int_as_float(e.s), 0.f, 0.f, 0.f);
         }
     }
     if (tid == 0) {
-        const double P = D.dkappa * red[1];
+        double psum = gsum_p[0];
+        for (int g = 1; g < Gp; ++g) psum += gsum_p[g];
+        const double P = D.dkappa * psum;
         DevState* st = D.st;
         const long long t = t_now;
         if (mom_now) {  // bunch length and energy spread of the new state (Sec. IV)
-            const double s0 = red[0], mq = red[2] / s0, mp = red[4] / s0;
+            const double s0 = csum, mq = red[2] / s0, mp = red[4] / s0;
             double* m = D.mring + 4 * ((t + 1) & D.ring_mask);
             m[0] = mq;
             m[1] = sqrt(fmax(red[3] / s0 - mq * mq, 0.0));
@@ -664,6 +787,13 @@ __device__ void finalise(const Desc<T>& D, unsigned char* smem, int is_step)
         if (bad || !isfinite(P)) st->status = -5;
         st->ticket = 0u;
     }
+}
+
+template <typename T>
+__device__ void finalise(const Desc<T>& D, unsigned char* smem, int is_step)
+{
+    finalise_load<T>(D, smem, true, true);
+    finalise_compute<T>(D, smem, is_step, 0u);
 }
 
 // ----------------------------------------------------------------------------

@@ -23,7 +23,7 @@ IMPEDANCE_NONE, IMPEDANCE_FREE_SPACE, IMPEDANCE_PARALLEL_PLATES, IMPEDANCE_TABLE
 EXPORTS = [
     "vfps_params_default", "vfps_create", "vfps_set_impedance", "vfps_step", "vfps_profile",
     "vfps_csr_power", "vfps_charge_series", "vfps_get_state", "vfps_set_state",
-    "vfps_steps_done", "vfps_destroy", "vfps_strerror", "vfps_last_cuda_error", "vfps_impedance_table",
+    "vfps_steps_done", "vfps_step_mode", "vfps_destroy", "vfps_strerror", "vfps_last_cuda_error", "vfps_impedance_table",
     "vfps_batch_create", "vfps_batch_add", "vfps_batch_slot_bytes", "vfps_batch_run",
     "vfps_batch_poll", "vfps_batch_take", "vfps_batch_remove", "vfps_batch_usage",
     "vfps_batch_destroy", "vfps_step_static", "vfps_batch_launches_per_step",
@@ -116,6 +116,7 @@ def lib() -> ctypes.CDLL:
         "vfps_get_state": (ctypes.c_int, [_VP, _D]),
         "vfps_set_state": (ctypes.c_int, [_VP, _D]),
         "vfps_steps_done": (ctypes.c_int, [_VP, ctypes.POINTER(_I64)]),
+        "vfps_step_mode": (ctypes.c_int, [_VP, ctypes.POINTER(_I32)]),
         "vfps_destroy": (ctypes.c_int, [_VP]),
         "vfps_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "vfps_last_cuda_error": (ctypes.c_char_p, []),
@@ -312,6 +313,13 @@ class Simulation:
         k = _I64()
         _check(lib().vfps_steps_done(self._h, ctypes.byref(k)), "vfps_steps_done")
         return k.value
+
+    @property
+    def persistent(self) -> bool:
+        """True when step() runs this simulation in persistent launches."""
+        on = _I32()
+        _check(lib().vfps_step_mode(self._h, ctypes.byref(on)), "vfps_step_mode")
+        return bool(on.value)
 
     def close(self):
         if getattr(self, "_h", None):
