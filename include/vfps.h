@@ -267,10 +267,9 @@ int vfps_impedance_table(int model, int32_t n, double half_width, int32_t pad_fa
  * Only precision = 0.  Limits: n <= 1024 and FFT length <= 4096; larger
  * requests return VFPS_EINVAL with the reason in vfps_last_cuda_error().
  * Scratch lives in a fixed device array of about 80 KB inside the library
- * image (held by every GPU that loads the library until exit).  It is looked
- * up on the first call on each device: make that first call before any
- * stream capture.  All calls share that array; calls whose work overlaps on
- * the GPU (other streams or host threads) race on it.  Host-side tables
+ * image (held by every GPU that loads the library until exit), looked up on
+ * the first call on each device.  All calls share that array; calls whose
+ * work overlaps on the GPU (other streams or host threads) race on it.  Host-side tables
  * (impedance, twiddles) use ordinary host memory. */
 int vfps_step_static(const vfps_params* params, int model, double Pi, double S_csr,
                      const float* psi_in, float* psi_out, double* power_out, void* cuda_stream);
