@@ -482,6 +482,14 @@ void unit_gaussian(const Instance& I, double* g)
         }
 }
 
+// CTAs per state of the staging kernels (one row or more each): about four
+// per SM over the whole transfer, at least 4 per state and at most n.
+int stage_rows(int n, int count)
+{
+    const int want = 4 * num_sms() / std::max(1, count);
+    return std::min(n, std::max(4, want));
+}
+
 // Host states -> normalised device states of `count` instances of one
 // precision: one copy of all of them to the device, FP64 charge sums there
 // (stage_sum_kernel), a check that every value is finite and every charge
@@ -543,8 +551,7 @@ int upload_states_t(Instance* const* inst, int count, const double* src, cudaStr
     for (int i = 0; i < count && rc == VFPS_OK; ++i)
         if (!(sums[2 * (size_t)i + 1] == 1.0) || !(sums[2 * (size_t)i] > 0.0)) rc = VFPS_EINVAL;
     if (rc == VFPS_OK) {
-        int rows = 1;
-        while (rows < 64 && (long long)rows * 256 * 16 < (long long)inst[0]->n * inst[0]->ld) rows <<= 1;
+        const int rows = stage_rows(inst[0]->n, count);
         stage_store_kernel<T><<<dim3((unsigned)rows, (unsigned)count), 256, 0, s>>>(dv, ds, dj);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -2620,8 +2627,7 @@ int take_states_t(std::vector<Instance*>& inst, const std::vector<long long>& of
     if (jobs.empty()) return VFPS_OK;
     StateJob<T>* dj = (StateJob<T>*)(d + job_off);
     CU(cudaMemcpyAsync(dj, jobs.data(), sizeof(StateJob<T>) * jobs.size(), cudaMemcpyHostToDevice, s));
-    int rows = 1;
-    while (rows < 64 && (long long)rows * 256 * 16 < (long long)jobs[0].n * jobs[0].n) rows <<= 1;
+    const int rows = stage_rows(jobs[0].n, (int)jobs.size());
     stage_load_kernel<T><<<dim3((unsigned)rows, (unsigned)jobs.size()), 256, 0, s>>>((double*)d, dj);
     CU(cudaGetLastError());
     return VFPS_OK;

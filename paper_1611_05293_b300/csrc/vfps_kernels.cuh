@@ -1180,29 +1180,34 @@ struct StateJob {
 };
 
 // Upload: psi[parity] = (T)(staged * inv), inv = 1/(Delta^2 sum), rows padded
-// with zeros to ld; the state's pending scale becomes 1.  Grid (row blocks,
-// states).
+// with zeros to ld; the state's pending scale becomes 1.  Grid (CTAs per
+// state, states): CTA b takes rows b, b + gridDim.x, ...; the factor is
+// formed once per CTA (an FP64 division is slow on this GPU).
 template <typename T>
 __global__ void __launch_bounds__(256)
 stage_store_kernel(const double* __restrict__ src, const double* __restrict__ sums, const StateJob<T>* jobs)
 {
+    __shared__ double s_inv;
     const StateJob<T> j = jobs[blockIdx.y];
-    const double inv = 1.0 / (j.delta2 * sums[2 * blockIdx.y]);
+    if (threadIdx.x == 0) s_inv = 1.0 / (j.delta2 * sums[2 * blockIdx.y]);
     T* dst = j.psi[j.st->parity];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         j.st->scale = 1.0;
         j.st->ticket = 0u;
     }
-    const long long cells = (long long)j.n * j.ld;
-    for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < cells; i += (long long)gridDim.x * 256) {
-        const int x = (int)(i / j.ld), y = (int)(i - (long long)x * j.ld);
-        dst[i] = y < j.n ? (T)(src[j.off + (long long)x * j.n + y] * inv) : T(0);
+    __syncthreads();
+    const double inv = s_inv;
+    for (int x = blockIdx.x; x < j.n; x += gridDim.x) {
+        const double* row = src + j.off + (long long)x * j.n;
+        T* out = dst + (size_t)x * j.ld;
+        for (int y = threadIdx.x; y < j.ld; y += blockDim.x) out[y] = y < j.n ? (T)(row[y] * inv) : T(0);
     }
 }
 
 // Download: staged[off + x n + y] = (double)psi[parity][x][y] * scale (the
 // stored state with its pending renormalisation applied, as a single
-// vfps_get_state computes it).  Grid (row blocks, states).
+// vfps_get_state computes it).  Grid (CTAs per state, states), rows as in
+// stage_store_kernel.
 template <typename T>
 __global__ void __launch_bounds__(256)
 stage_load_kernel(double* __restrict__ dst, const StateJob<T>* jobs)
@@ -1210,10 +1215,10 @@ stage_load_kernel(double* __restrict__ dst, const StateJob<T>* jobs)
     const StateJob<T> j = jobs[blockIdx.y];
     const T* src = j.psi[j.st->parity];
     const double scale = j.st->scale;
-    const long long cells = (long long)j.n * j.n;
-    for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < cells; i += (long long)gridDim.x * 256) {
-        const int x = (int)(i / j.n), y = (int)(i - (long long)x * j.n);
-        dst[j.off + i] = (double)src[(size_t)x * j.ld + y] * scale;
+    for (int x = blockIdx.x; x < j.n; x += gridDim.x) {
+        const T* row = src + (size_t)x * j.ld;
+        double* out = dst + j.off + (long long)x * j.n;
+        for (int y = threadIdx.x; y < j.n; y += blockDim.x) out[y] = (double)row[y] * scale;
     }
 }
 
