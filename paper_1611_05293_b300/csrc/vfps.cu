@@ -168,8 +168,8 @@ bool fast_eligible(const vfps_params* p)
 {
     // the Manhattan drift's x-node may step by at most one per 4-row block:
     // h = 2 sin(pi/steps) < 1/3
-    return p->precision == 0 && p->interp_points == 4 && p->clamp == 0 && (p->n % 4) == 0 &&
-           (p->rotation == 0 || p->steps_per_period >= 20);
+    return p->precision == 0 && p->interp_points >= 2 && p->interp_points <= 4 && p->clamp == 0 &&
+           (p->n % 4) == 0 && (p->rotation == 0 || p->steps_per_period >= 20);
 }
 
 // Rows per lane of the FP32 kernel's kick/FP blocks: 8 where n allows.
@@ -187,7 +187,8 @@ size_t fast_smem(const vfps_params* p, int W)
 // then stay inside the kPairRP padding pair-rows of a ring column).
 bool pair_eligible(const vfps_params* p)
 {
-    return fast_eligible(p) && p->rotation == 0 && (p->n % 32) == 0 && halo_for(p) <= 12;
+    return fast_eligible(p) && p->interp_points == 4 && p->rotation == 0 && (p->n % 32) == 0 &&
+           halo_for(p) <= 12;
 }
 
 size_t pair_smem(const vfps_params* p, int W)
@@ -261,7 +262,9 @@ int choose_width(const vfps_params* p, int* fast = nullptr, bool latency = false
 {
     if (fast) *fast = 0;
     if (fast_eligible(p)) {
-        const int W = pick_width(p, true, latency);
+        // N_I = 2 and 3 have one FP32-kernel width, W = 4
+        const int W = p->interp_points == 4 ? pick_width(p, true, latency)
+                      : ((long long)fast_smem(p, 4) <= device_smem_limit() - 1024 ? 4 : 0);
         if (W) {
             if (fast) *fast = 1;
             return W;
@@ -378,6 +381,7 @@ void fill_desc(Instance& I)
     d.sword = I.sword;
     d.cflag = I.cflag;
     d.mom_every = I.mring ? I.mom_every : 0;
+    d.ni = I.p.interp_points;
     d.spin_limit = I.spin_limit;
     d.fault_no_signal = I.fault_no_signal;
     d.st = I.st;
@@ -857,14 +861,14 @@ int launch_step_ni(const Group& g, cudaStream_t s)
     return VFPS_EINVAL;
 }
 
-template <int W, int KR, int NC>
+template <int W, int KR, int NC, int NI = 4>
 int launch_fast_k(const Group& g, cudaStream_t s)
 {
     if (g.rot)
-        CU(launch_pdl(step_kernel_f32<W, KR, NC, 1>, g.grid, W * 32, g.smem, s, (const Desc<float>*)g.ddescs,
+        CU(launch_pdl(step_kernel_f32<W, KR, NC, 1, NI>, g.grid, W * 32, g.smem, s, (const Desc<float>*)g.ddescs,
                       (const int4*)g.dsegs, g.spc));
     else
-        CU(launch_pdl(step_kernel_f32<W, KR, NC, 0>, g.grid, W * 32, g.smem, s, (const Desc<float>*)g.ddescs,
+        CU(launch_pdl(step_kernel_f32<W, KR, NC, 0, NI>, g.grid, W * 32, g.smem, s, (const Desc<float>*)g.ddescs,
                       (const int4*)g.dsegs, g.spc));
     return VFPS_OK;
 }
@@ -890,6 +894,10 @@ int launch_pair_t(const Group& g, cudaStream_t s)
 template <int W>
 int launch_fast_t(const Group& g, cudaStream_t s)
 {
+    if (g.ni != 4) {  // N_I = 2, 3: the order comes from the descriptor, W = 4 only
+        if constexpr (W == 4) return g.kr == 8 ? launch_fast_k<4, 8, 0, 0>(g, s) : launch_fast_k<4, 4, 0, 0>(g, s);
+        return VFPS_EINVAL;
+    }
     if (g.kr == 8) {
         if (g.n == 256) return launch_fast_k<W, 8, 256>(g, s);
         if (g.n == 1024) return launch_fast_k<W, 8, 1024>(g, s);
@@ -958,7 +966,7 @@ const void* persist_fn_w(int kr, int n, int rot)
 
 const void* persist_fn(const Group& g)
 {
-    if (!g.fast || g.pair) return nullptr;
+    if (!g.fast || g.pair || g.ni != 4) return nullptr;
     if (g.W == 8) return persist_fn_w<8>(g.kr, g.n, g.rot);
     if (g.W == 4) return persist_fn_w<4>(g.kr, g.n, g.rot);
     return nullptr;
@@ -1054,6 +1062,10 @@ int init_kernels()
                     const void* f = W == 8 ? persist_fn_w<8>(kr, n, rot) : persist_fn_w<4>(kr, n, rot);
                     CU(set_smem_attr_one(f, lim));
                 }
+    CU(set_smem_attr_one(step_kernel_f32<4, 8, 0, 0, 0>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<4, 8, 0, 1, 0>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<4, 4, 0, 0, 0>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<4, 4, 0, 1, 0>, lim));
     CU(set_smem_attr_one(step_kernel_f32x2<8, 0>, lim));
     CU(set_smem_attr_one(step_kernel_f32x2<4, 0>, lim));
     CU(set_smem_attr_one(step_kernel_f32x2<2, 0>, lim));
@@ -1856,6 +1868,11 @@ int blocks_per_sm(K kernel, int threads, size_t smem)
 template <int W>
 int fast_blocks_t(const Group& g, size_t smem)
 {
+    if (g.ni != 4) {
+        if (g.kr == 8)
+            return blocks_per_sm(g.rot ? step_kernel_f32<4, 8, 0, 1, 0> : step_kernel_f32<4, 8, 0, 0, 0>, 128, smem);
+        return blocks_per_sm(g.rot ? step_kernel_f32<4, 4, 0, 1, 0> : step_kernel_f32<4, 4, 0, 0, 0>, 128, smem);
+    }
     if (g.pair) {
         if (g.n == 256) return blocks_per_sm(step_kernel_f32x2<W, 256>, W * 32, smem);
         if (g.n == 1024) return blocks_per_sm(step_kernel_f32x2<W, 1024>, W * 32, smem);
@@ -2020,6 +2037,7 @@ bool tuned_choice(const std::tuple<int, int, int, int, int, int>& key, std::pair
 bool pin_fits(const Group& g, int W, int tps)
 {
     const long long lim = device_smem_limit() - 1024;
+    if (g.ni != 4 && W != 4) return false;
     for (const Instance* I : g.members)
         if ((long long)member_smem(g, I, W) > lim) return false;
     return tps == -1 || (tps >= 1 && ((g.n + W - 1) / W) % tps == 0);
@@ -2030,6 +2048,7 @@ std::vector<std::pair<int, int>> tune_candidates(const Group& g)
     std::vector<std::pair<int, int>> c;
     const long long lim = device_smem_limit() - 1024;
     for (int W : {8, 4, 2}) {
+        if (g.ni != 4 && W != 4) continue;
         bool fits = true;
         for (const Instance* I : g.members) fits = fits && (long long)member_smem(g, I, W) <= lim;
         if (!fits) continue;
@@ -2212,7 +2231,8 @@ int rebuild_groups(vfps_batch* b)
             const int cnt = (int)kv.members.size();
             int bucket = 1;
             while (bucket < cnt) bucket <<= 1;
-            g.tune_key = std::make_tuple(I0->n, g.prec, g.rot + 2 * g.pair, I0->p.steps_per_period, bucket, I0->W);
+            g.tune_key = std::make_tuple(I0->n, g.prec, g.rot + 2 * g.pair + 4 * g.ni, I0->p.steps_per_period,
+                                         bucket, I0->W);
             std::pair<int, int> best;
             if (b->pin_W && pin_fits(g, b->pin_W, b->pin_tps)) {
                 W = b->pin_W;

@@ -85,6 +85,29 @@ __device__ __forceinline__ void lagrange2(float2 t, float2 w[4])
     w[3] = __ffma2_rn(m, f2(-0.5f, -0.5f), f2(-w[0].x, -w[0].y));
 }
 
+// lagrange2 for N_I nodes in the cubic 4-slot layout (lagrange_w4_rt): NI = 4
+// is the compile-time cubic, NI = 0 takes the order (2 or 3) from ni; each
+// half of a pair as the scalar weights are.
+template <int NI>
+__device__ __forceinline__ void lagrange2_ni(float2 t, float2 w[4], int ni)
+{
+    if constexpr (NI == 4) {
+        lagrange2(t, w);
+    } else {
+        float a[4], b[4];
+        lagrange_w4_rt(t.x, a, ni);
+        lagrange_w4_rt(t.y, b, ni);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) w[k] = f2(a[k], b[k]);
+    }
+}
+template <int NI>
+__device__ __forceinline__ void lagrange_w4(float t, float w[4], int ni)
+{
+    if constexpr (NI == 4) lagrange_w<float, 4>(t, w);
+    else lagrange_w4_rt(t, w, ni);
+}
+
 // Fokker-Planck weight g_k(y) of tap k (rows y-1 .. y+2) with the identity
 // folded into the centre tap, in one fixed order of operations (the FP32
 // kernels all build their tables with it).
@@ -106,16 +129,16 @@ __device__ __forceinline__ float fp_apply(float g0, float g1, float g2, float g3
 // columns (ring slots slot0.., row offset rowoff) whose first row is O rows
 // above the first stencil row of output 0.  tx, ty hold the node fractions
 // of rows (0,1) and (2,3) as pairs (packed weight arithmetic).
-template <int O>
+template <int O, int NI>
 __device__ __forceinline__ void rotate_block(const float* __restrict__ ring, int slot0, int R, int P, int rowoff,
                                              float2 tx01, float2 tx23, float2 ty01, float2 ty23, bool e1,
-                                             bool e2, bool e3, float out[4])
+                                             bool e2, bool e3, float out[4], int ni)
 {
     float2 wy01[4], wy23[4], wx01[4], wx23[4];
-    lagrange2(ty01, wy01);
-    lagrange2(ty23, wy23);
-    lagrange2(tx01, wx01);
-    lagrange2(tx23, wx23);
+    lagrange2_ni<NI>(ty01, wy01, ni);
+    lagrange2_ni<NI>(ty23, wy23, ni);
+    lagrange2_ni<NI>(tx01, wx01, ni);
+    lagrange2_ni<NI>(tx23, wx23, ni);
     const float wy[4][4] = {{wy01[0].x, wy01[1].x, wy01[2].x, wy01[3].x},
                             {wy01[0].y, wy01[1].y, wy01[2].y, wy01[3].y},
                             {wy23[0].x, wy23[1].x, wy23[2].x, wy23[3].x},
@@ -157,15 +180,15 @@ __device__ __forceinline__ void rotate_block(const float* __restrict__ ring, int
 // rows is row 0's, so only window columns 1..4 take part and the x-weights
 // need no selection (same operations as rotate_block for such a block, whose
 // column-0 terms are zeros).
-template <int O>
+template <int O, int NI>
 __device__ __forceinline__ void rotate_block4(const float* __restrict__ ring, int slot0, int R, int P, int rowoff,
-                                              float2 tx01, float2 tx23, float2 ty01, float2 ty23, float out[4])
+                                              float2 tx01, float2 tx23, float2 ty01, float2 ty23, float out[4], int ni)
 {
     float2 wy01[4], wy23[4], wx01[4], wx23[4];
-    lagrange2(ty01, wy01);
-    lagrange2(ty23, wy23);
-    lagrange2(tx01, wx01);
-    lagrange2(tx23, wx23);
+    lagrange2_ni<NI>(ty01, wy01, ni);
+    lagrange2_ni<NI>(ty23, wy23, ni);
+    lagrange2_ni<NI>(tx01, wx01, ni);
+    lagrange2_ni<NI>(tx23, wx23, ni);
     float2 acc01, acc23;
 #pragma unroll
     for (int a = 1; a < 5; ++a) {
@@ -322,8 +345,9 @@ __device__ __forceinline__ float kick_fp_column(const float* __restrict__ colcol
 // Source node (mx, my) and cubic weights of cell (x, y) of the rotation, in
 // one fixed order of operations; false when the source lies more than one
 // cell outside the grid (the cell is then 0).
+template <int NI>
 __device__ __forceinline__ bool cell_weights(int x, int y, int n, float cm1, float sn, float c, int* mx, int* my,
-                                             float wx[4], float wy[4])
+                                             float wx[4], float wy[4], int ni)
 {
     const float xc = float(x) - c, yc = float(y) - c;
     const float dx = fmaf(-sn, yc, cm1 * xc);
@@ -332,19 +356,20 @@ __device__ __forceinline__ bool cell_weights(int x, int y, int n, float cm1, flo
     *mx = x + int(fx);
     *my = y + int(fy);
     if (*mx <= -2 || *mx >= n || *my <= -2 || *my >= n) return false;
-    lagrange_w<float, 4>(dx - fx, wx);
-    lagrange_w<float, 4>(dy - fy, wy);
+    lagrange_w4<NI>(dx - fx, wx, ni);
+    lagrange_w4<NI>(dy - fy, wy, ni);
     return true;
 }
 
 // Rotation of one cell from the column ring (general path), with slab
 // column col stored in ring slot col & (R-1).
+template <int NI>
 __device__ __forceinline__ float rotate_cell_ring(const float* __restrict__ ring, int R, int P, int RP, int x, int y,
-                                                  int n, float cm1, float sn, float c)
+                                                  int n, float cm1, float sn, float c, int ni)
 {
     int mx, my;
     float wx[4], wy[4];
-    if (!cell_weights(x, y, n, cm1, sn, c, &mx, &my, wx, wy)) return 0.f;
+    if (!cell_weights<NI>(x, y, n, cm1, sn, c, &mx, &my, wx, wy, ni)) return 0.f;
     float acc = 0.f;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
@@ -412,10 +437,10 @@ __device__ __forceinline__ void load_kick(float4* dst, const float4* __restrict_
 // y-node offset FY is the same on every row (window alignment O = A & 3,
 // A = FY - 1 + RP) and the x-node steps back by at most one inside a block
 // of four rows (sin phi < 1/3).
-template <int O, int KR>
+template <int O, int KR, int NI>
 __device__ __forceinline__ void rotate_column(const float* __restrict__ ring, int R, int P, int RP, int A,
                                               float* __restrict__ colcol, int HC, int x, int n, int lane, float xc,
-                                              float c, float sn, float cm1, int FY)
+                                              float c, float sn, float cm1, int FY, int ni)
 {
     const float2 msn2 = f2(-sn, -sn), cm12 = f2(cm1, cm1);
     const float2 snxc = f2(sn * xc, sn * xc), cmxc = f2(cm1 * xc, cm1 * xc);
@@ -444,10 +469,10 @@ __device__ __forceinline__ void rotate_column(const float* __restrict__ ring, in
         const bool anyback = __any_sync(0xffffffffu, live && fx3 < fx0);
         if (!live) continue;
         if (anyback)
-            rotate_block<O>(ring, (mx0 - 2) & (R - 1), R, P, y0 + A - O, tx01, tx23, ty01, ty23, fx1 < fx0,
-                            fx2 < fx0, fx3 < fx0, r);
+            rotate_block<O, NI>(ring, (mx0 - 2) & (R - 1), R, P, y0 + A - O, tx01, tx23, ty01, ty23, fx1 < fx0,
+                                fx2 < fx0, fx3 < fx0, r, ni);
         else
-            rotate_block4<O>(ring, (mx0 - 2) & (R - 1), R, P, y0 + A - O, tx01, tx23, ty01, ty23, r);
+            rotate_block4<O, NI>(ring, (mx0 - 2) & (R - 1), R, P, y0 + A - O, tx01, tx23, ty01, ty23, r, ni);
         // sources more than one cell outside the grid give 0
         if (!((mx0 >= 0) && (mx0 <= n - 1) && (y0 + FY >= -1) && (y0 + 3 + FY <= n - 1))) {
             const float fxk[4] = {fx0, fx1, fx2, fx3};
@@ -468,10 +493,10 @@ __device__ __forceinline__ void rotate_column(const float* __restrict__ ring, in
 // and pass; their x-node steps down by at most one inside the block (h <
 // 1/3), so one 5-column window of the ring (one LDS.128 per column) with a
 // 5-column weight vector covers the block, as in the 2-D rotation.
-template <int KR>
+template <int KR, int NI>
 __device__ __forceinline__ void drift_column(const float* __restrict__ ring, int R, int P, int RP,
                                              float* __restrict__ colcol, int HC, int x, int n, int lane, float c,
-                                             float hm)
+                                             float hm, int ni)
 {
     const int lbase = cola_lane_base<KR>(lane, HC);
 #pragma unroll 1
@@ -482,8 +507,8 @@ __device__ __forceinline__ void drift_column(const float* __restrict__ ring, int
         const float d0 = -hm * yc0, d1 = -hm * (yc0 + 1.f), d2 = -hm * (yc0 + 2.f), d3 = -hm * (yc0 + 3.f);
         const float fx0 = floorf(d0), fx1 = floorf(d1), fx2 = floorf(d2), fx3 = floorf(d3);
         float2 w01[4], w23[4];
-        lagrange2(f2(d0 - fx0, d1 - fx1), w01);
-        lagrange2(f2(d2 - fx2, d3 - fx3), w23);
+        lagrange2_ni<NI>(f2(d0 - fx0, d1 - fx1), w01, ni);
+        lagrange2_ni<NI>(f2(d2 - fx2, d3 - fx3), w23, ni);
         const float wx[4][4] = {{w01[0].x, w01[1].x, w01[2].x, w01[3].x},
                                 {w01[0].y, w01[1].y, w01[2].y, w01[3].y},
                                 {w23[0].x, w23[1].x, w23[2].x, w23[3].x},
@@ -661,7 +686,7 @@ __device__ __forceinline__ bool cta_wait_flags(const Desc<float>& D, int c0, int
 // the end the CTA sets its step flag instead of taking a ticket.
 // s_last is then the CTA's failure flag.  Returns false when a wait ran out
 // (status set).
-template <int W, int KR, int NC, int ROT, bool PERSIST = false>
+template <int W, int KR, int NC, int ROT, bool PERSIST = false, int NI = 4>
 __device__ __forceinline__ bool strip_f32(const Desc<float>& D, int xs, int T, unsigned char* smem, int& s_last,
                                           const PersistStep* ps = nullptr)
 {
@@ -685,6 +710,7 @@ __device__ __forceinline__ bool strip_f32(const Desc<float>& D, int xs, int T, u
     float4* kbuf = reinterpret_cast<float4*>(gtab + 4 * n) + 2 * warp;  // stage k: kbuf + 2 W k
     constexpr int rot = ROT;            // 1: Manhattan rotation (every instance of the launch)
     const float hm = D.hm;
+    const int ni = NI == 4 ? 4 : D.ni;  // interpolation points (NI = 0: from the descriptor)
     float* colbcol = reinterpret_cast<float*>(reinterpret_cast<float4*>(gtab + 4 * n) + 8 * W) + warp * PA;
 
     // padding rows of every ring slot and of this warp's psi_a column: zero
@@ -731,7 +757,7 @@ __device__ __forceinline__ bool strip_f32(const Desc<float>& D, int xs, int T, u
         cp_async_wait_1();
         __syncthreads();
         if (active && rot) {
-            drift_column<KR>(ring, R, P, RP, colcol, HC, x, n, lane, c, hm);
+            drift_column<KR, NI>(ring, R, P, RP, colcol, HC, x, n, lane, c, hm, ni);
         } else if (active) {
             const float xc = float(x) - c;
             // dy is linear along the column: floor(dy) is the same on every row
@@ -742,14 +768,14 @@ __device__ __forceinline__ bool strip_f32(const Desc<float>& D, int xs, int T, u
                 const int FY = int(fy_top);
                 const int A = FY - 1 + RP;
                 switch (A & 3) {
-                case 0: rotate_column<0, KR>(ring, R, P, RP, A, colcol, HC, x, n, lane, xc, c, sn, cm1, FY); break;
-                case 1: rotate_column<1, KR>(ring, R, P, RP, A, colcol, HC, x, n, lane, xc, c, sn, cm1, FY); break;
-                case 2: rotate_column<2, KR>(ring, R, P, RP, A, colcol, HC, x, n, lane, xc, c, sn, cm1, FY); break;
-                default: rotate_column<3, KR>(ring, R, P, RP, A, colcol, HC, x, n, lane, xc, c, sn, cm1, FY); break;
+                case 0: rotate_column<0, KR, NI>(ring, R, P, RP, A, colcol, HC, x, n, lane, xc, c, sn, cm1, FY, ni); break;
+                case 1: rotate_column<1, KR, NI>(ring, R, P, RP, A, colcol, HC, x, n, lane, xc, c, sn, cm1, FY, ni); break;
+                case 2: rotate_column<2, KR, NI>(ring, R, P, RP, A, colcol, HC, x, n, lane, xc, c, sn, cm1, FY, ni); break;
+                default: rotate_column<3, KR, NI>(ring, R, P, RP, A, colcol, HC, x, n, lane, xc, c, sn, cm1, FY, ni); break;
                 }
             } else {
                 for (int y = lane; y < n; y += 32)
-                    colcol[split_idx<KR>(kColPad + y, HC)] = rotate_cell_ring(ring, R, P, RP, x, y, n, cm1, sn, c);
+                    colcol[split_idx<KR>(kColPad + y, HC)] = rotate_cell_ring<NI>(ring, R, P, RP, x, y, n, cm1, sn, c, ni);
             }
         }
         __syncwarp();
@@ -760,7 +786,7 @@ __device__ __forceinline__ bool strip_f32(const Desc<float>& D, int xs, int T, u
             const float ts = hm * (float(x) - c), fk = floorf(ts);
             const int sr = int(fk);
             float wr[4];
-            lagrange_w<float, 4>(ts - fk, wr);
+            lagrange_w4<NI>(ts - fk, wr, ni);
             const float4 w4 = make_float4(wr[0], wr[1], wr[2], wr[3]);
             if (sr >= -4 && sr <= 4) {
                 const int A2 = sr - 2 + kColPad;
@@ -803,7 +829,7 @@ __device__ __forceinline__ bool strip_f32(const Desc<float>& D, int xs, int T, u
             const unsigned rk = __shfl_sync(0xffffffffu, r, 0), rs = __shfl_sync(0xffffffffu, r, 1);
             kick_ok = __shfl_sync(0xffffffffu, (int)ok, 0) && __shfl_sync(0xffffffffu, (int)ok, 1);
             if (kick_ok) {
-                const KickEntry e = kick_entry(__uint_as_float(rk), __uint_as_float(rs));
+                const KickEntry e = kick_entry(__uint_as_float(rk), __uint_as_float(rs), ni);
                 kw = e.w;
                 s = e.s;
             } else if (lane == 0) {
@@ -922,7 +948,7 @@ __device__ __forceinline__ bool strip_f32(const Desc<float>& D, int xs, int T, u
 #define VFPS_FAST_WARPS_PER_SM 32
 #endif
 
-template <int W, int KR, int NC, int ROT>
+template <int W, int KR, int NC, int ROT, int NI = 4>
 __global__ void __launch_bounds__(W * 32, VFPS_FAST_WARPS_PER_SM / W)
 step_kernel_f32(const Desc<float>* __restrict__ descs, const int4* __restrict__ segs, int spc)
 {
@@ -937,7 +963,7 @@ step_kernel_f32(const Desc<float>* __restrict__ descs, const int4* __restrict__ 
         const int4 sg = segs[blockIdx.x * spc + i];
         if (sg.z <= 0) break;
         if (i > 0) __syncthreads();  // shared memory of the previous strip (or its finaliser) is free
-        strip_f32<W, KR, NC, ROT>(descs[sg.x], sg.y, sg.z, smem, s_last);
+        strip_f32<W, KR, NC, ROT, false, NI>(descs[sg.x], sg.y, sg.z, smem, s_last);
     }
 }
 

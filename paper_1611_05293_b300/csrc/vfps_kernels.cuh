@@ -81,6 +81,7 @@ struct Desc {
     unsigned* cflag;
     DevState* st;
     int mom_every;                     // record moments of psi_t when t % mom_every == 0 (0: off)
+    int ni;                            // interpolation points N_I (2, 3, 4)
     unsigned spin_limit;               // persistent launches: polls of a wait before VFPS_ETIMEOUT
     int fault_no_signal;               // test hook: the finaliser CTA never publishes (waits run out)
     int n, ld, M, logM;
@@ -114,6 +115,32 @@ __device__ __forceinline__ void lagrange_w(T t, T* w)
     } else {                          // nodes 0, 1
         w[0] = T(1) - t;
         w[1] = t;
+    }
+}
+
+// Lagrange weights of N_I = 2, 3 or 4 nodes (ni) in the 4-slot layout of the
+// cubic stencil, nodes -1, 0, 1, 2 relative to floor: N_I = 3 takes nodes
+// -1..1 and leaves slot 3 zero, N_I = 2 nodes 0..1 with slots 0 and 3 zero
+// (the node sets of lagrange_w), so one window and one stencil serve every
+// order (FP32 kernels).
+__device__ __forceinline__ void lagrange_w4_rt(float t, float w[4], int ni)
+{
+    if (ni == 3) {
+        float v[3];
+        lagrange_w<float, 3>(t, v);
+        w[0] = v[0];
+        w[1] = v[1];
+        w[2] = v[2];
+        w[3] = 0.f;
+    } else if (ni == 2) {
+        float v[2];
+        lagrange_w<float, 2>(t, v);
+        w[0] = 0.f;
+        w[1] = v[0];
+        w[2] = v[1];
+        w[3] = 0.f;
+    } else {
+        lagrange_w<float, 4>(t, w);
     }
 }
 
@@ -275,18 +302,18 @@ template <typename T2> __device__ __forceinline__ T2 cmulc(T2 a, T2 b)  // a * c
 
 // Kick-table entry of a column whose p-shift for the next step is k cells,
 // with the pending renormalisation factor sf folded into the weights:
-// psi_b(y) = sum_j w_j psi_a(y + s - 1 + j) (cubic, source y - k), s =
-// floor(-k).  Both the finaliser and the persistent workers (which rebuild
+// psi_b(y) = sum_j w_j psi_a(y + s - 1 + j) (N_I = ni nodes in the cubic
+// layout, source y - k), s = floor(-k).  Both the finaliser and the persistent workers (which rebuild
 // the entry from k and sf) compute it here.
 struct KickEntry {
     float4 w;
     int s;
 };
-__device__ __forceinline__ KickEntry kick_entry(float k, float sf)
+__device__ __forceinline__ KickEntry kick_entry(float k, float sf, int ni)
 {
     const float ks = -k, fk = floorf(ks);
     float w[4];
-    lagrange_w<float, 4>(ks - fk, w);
+    lagrange_w4_rt(ks - fk, w, ni);
     return {make_float4(sf * w[0], sf * w[1], sf * w[2], sf * w[3]), int(fk)};
 }
 
@@ -755,7 +782,7 @@ __device__ void finalise_compute(const Desc<T>& D, unsigned char* smem, int is_s
         D.kick[x] = k;
         D.rho[x] = sd * cs[x];
         if constexpr (sizeof(T) == 4) {
-            const KickEntry e = kick_entry(k, float(s_new));
+            const KickEntry e = kick_entry(k, float(s_new), D.ni);
             D.kickw[2 * x] = e.w;
             D.kickw[2 * x + 1] = make_float4(__int_as_float(e.s), 0.f, 0.f, 0.f);
         }

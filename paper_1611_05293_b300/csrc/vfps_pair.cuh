@@ -106,7 +106,7 @@ __device__ __forceinline__ float2 rotate_cell_pair(const unsigned char* __restri
 {
     int mx, my;
     float wx[4], wy[4];
-    if (!cell_weights(x, y, n, cm1, sn, c, &mx, &my, wx, wy)) return f2(0.f, 0.f);
+    if (!cell_weights<4>(x, y, n, cm1, sn, c, &mx, &my, wx, wy, 4)) return f2(0.f, 0.f);
     float2 acc = f2(0.f, 0.f);
 #pragma unroll
     for (int a = 0; a < 4; ++a) {

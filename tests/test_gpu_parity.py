@@ -53,6 +53,11 @@ CASES = [
     (33, "random", 2, 1.0, 1.3, {"rotation": 1, "interp_points": 3}),
     (48, "blobs", 2, 3.0, 1.5, {"rotation": 1, "clamp": 1}),
     (256, "blobs", 2, 2.0, 0.9, {"rotation": 1}),
+    # N_I = 2, 3 on grids the FP32 register-blocked kernel takes (n % 4 == 0)
+    (64, "blobs", 2, 2.0, 0.9, {"interp_points": 2}),
+    (256, "blobs", 2, 2.0, 0.9, {"interp_points": 3}),
+    (68, "random", 2, 1.0, 1.3, {"rotation": 1, "interp_points": 3}),
+    (48, "blobs", 2, 2.0, 0.9, {"rotation": 1, "interp_points": 2}),
 ]
 
 
@@ -80,6 +85,23 @@ def test_one_step_matches_oracle(V, precision, tol, n, kind, model, Pi, S, extra
     assert abs(Q[0] - Q0) <= tol * abs(Q0)
     rho1, _ = O.project(op, ref1)
     assert rel_linf(sim.profile(), rho1) < tol
+    sim.close()
+
+
+@pytest.mark.parametrize("ni,rotation", [(3, 0), (2, 0), (3, 1)])
+def test_lower_order_fp32_run_matches_oracle(V, ni, rotation):
+    """N_I = 3 and 2 in the FP32 register-blocked kernel (their weights in the
+    cubic 4-slot layout, reading 3): 200 steps of N=64 at 200 steps/period,
+    wake on, against the FP64 oracle."""
+    n, spp, steps = 64, 200, 200
+    psi0 = W.blobs(n, 5)
+    sim, op, zr, zi = make(V, n, 0, spp=spp, beta=0.05, model=2, Pi=2.0, S=0.6, psi=psi0,
+                           interp_points=ni, rotation=rotation)
+    ref, Pref, _ = O.run(op, zr, zi, O.normalize(op, psi0), steps)
+    sim.step(steps)
+    assert rel_linf(sim.get_state(), ref) < 1e-4
+    P = sim.csr_power()
+    assert np.max(np.abs(P - Pref)) <= 1e-3 * np.max(np.abs(Pref))
     sim.close()
 
 
