@@ -168,8 +168,8 @@ bool fast_eligible(const vfps_params* p)
 {
     // the Manhattan drift's x-node may step by at most one per 4-row block:
     // h = 2 sin(pi/steps) < 1/3
-    return p->precision == 0 && p->interp_points >= 2 && p->interp_points <= 4 && p->clamp == 0 &&
-           (p->n % 4) == 0 && (p->rotation == 0 || p->steps_per_period >= 20);
+    return p->precision == 0 && p->interp_points >= 2 && p->interp_points <= 4 && (p->n % 4) == 0 &&
+           (p->rotation == 0 || p->steps_per_period >= 20);
 }
 
 // Rows per lane of the FP32 kernel's kick/FP blocks: 8 where n allows.
@@ -187,7 +187,7 @@ size_t fast_smem(const vfps_params* p, int W)
 // then stay inside the kPairRP padding pair-rows of a ring column).
 bool pair_eligible(const vfps_params* p)
 {
-    return fast_eligible(p) && p->interp_points == 4 && p->rotation == 0 && (p->n % 32) == 0 &&
+    return fast_eligible(p) && p->interp_points == 4 && !p->clamp && p->rotation == 0 && (p->n % 32) == 0 &&
            halo_for(p) <= 12;
 }
 
@@ -262,8 +262,8 @@ int choose_width(const vfps_params* p, int* fast = nullptr, bool latency = false
 {
     if (fast) *fast = 0;
     if (fast_eligible(p)) {
-        // N_I = 2 and 3 have one FP32-kernel width, W = 4
-        const int W = p->interp_points == 4 ? pick_width(p, true, latency)
+        // N_I = 2, 3 and clamping have one FP32-kernel width, W = 4
+        const int W = (p->interp_points == 4 && !p->clamp) ? pick_width(p, true, latency)
                       : ((long long)fast_smem(p, 4) <= device_smem_limit() - 1024 ? 4 : 0);
         if (W) {
             if (fast) *fast = 1;
@@ -778,6 +778,7 @@ int create_instance(const vfps_params* p, const double* psi0, int ring, cudaStre
 // launch per step.  The tile table lists (instance, first column) per CTA.
 struct Group {
     int prec = 0, ni = 4, W = 8, fast = 0;
+    int var = 0;  // FP32 kernel instance: 0 cubic, 1 N_I = 2 or 3 (from the descriptor), 2 clamped
     int tps = 1;  // FP32 streaming kernel: consecutive tiles per CTA
     int kr = 4;   // FP32 streaming kernel: rows per lane of the kick/FP blocks
     int n = 0;    // grid size shared by the group's instances
@@ -894,8 +895,11 @@ int launch_pair_t(const Group& g, cudaStream_t s)
 template <int W>
 int launch_fast_t(const Group& g, cudaStream_t s)
 {
-    if (g.ni != 4) {  // N_I = 2, 3: the order comes from the descriptor, W = 4 only
-        if constexpr (W == 4) return g.kr == 8 ? launch_fast_k<4, 8, 0, 0>(g, s) : launch_fast_k<4, 4, 0, 0>(g, s);
+    if (g.var) {  // N_I = 2, 3 (NI = 0) or clamping (NI = 1): W = 4 only
+        if constexpr (W == 4) {
+            if (g.var == 2) return g.kr == 8 ? launch_fast_k<4, 8, 0, 1>(g, s) : launch_fast_k<4, 4, 0, 1>(g, s);
+            return g.kr == 8 ? launch_fast_k<4, 8, 0, 0>(g, s) : launch_fast_k<4, 4, 0, 0>(g, s);
+        }
         return VFPS_EINVAL;
     }
     if (g.kr == 8) {
@@ -966,7 +970,7 @@ const void* persist_fn_w(int kr, int n, int rot)
 
 const void* persist_fn(const Group& g)
 {
-    if (!g.fast || g.pair || g.ni != 4) return nullptr;
+    if (!g.fast || g.pair || g.var) return nullptr;
     if (g.W == 8) return persist_fn_w<8>(g.kr, g.n, g.rot);
     if (g.W == 4) return persist_fn_w<4>(g.kr, g.n, g.rot);
     return nullptr;
@@ -1066,6 +1070,10 @@ int init_kernels()
     CU(set_smem_attr_one(step_kernel_f32<4, 8, 0, 1, 0>, lim));
     CU(set_smem_attr_one(step_kernel_f32<4, 4, 0, 0, 0>, lim));
     CU(set_smem_attr_one(step_kernel_f32<4, 4, 0, 1, 0>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<4, 8, 0, 0, 1>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<4, 8, 0, 1, 1>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<4, 4, 0, 0, 1>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<4, 4, 0, 1, 1>, lim));
     CU(set_smem_attr_one(step_kernel_f32x2<8, 0>, lim));
     CU(set_smem_attr_one(step_kernel_f32x2<4, 0>, lim));
     CU(set_smem_attr_one(step_kernel_f32x2<2, 0>, lim));
@@ -1091,6 +1099,7 @@ Group single_group(const Instance& I)
     Group g;
     g.prec = I.p.precision;
     g.ni = I.p.interp_points;
+    g.var = !I.fast ? 0 : (I.p.clamp ? 2 : (I.p.interp_points != 4 ? 1 : 0));
     g.W = I.W;
     g.fast = I.fast;
     g.kr = fast_kr(I.p.n);
@@ -1868,7 +1877,12 @@ int blocks_per_sm(K kernel, int threads, size_t smem)
 template <int W>
 int fast_blocks_t(const Group& g, size_t smem)
 {
-    if (g.ni != 4) {
+    if (g.var == 2) {
+        if (g.kr == 8)
+            return blocks_per_sm(g.rot ? step_kernel_f32<4, 8, 0, 1, 1> : step_kernel_f32<4, 8, 0, 0, 1>, 128, smem);
+        return blocks_per_sm(g.rot ? step_kernel_f32<4, 4, 0, 1, 1> : step_kernel_f32<4, 4, 0, 0, 1>, 128, smem);
+    }
+    if (g.var) {
         if (g.kr == 8)
             return blocks_per_sm(g.rot ? step_kernel_f32<4, 8, 0, 1, 0> : step_kernel_f32<4, 8, 0, 0, 0>, 128, smem);
         return blocks_per_sm(g.rot ? step_kernel_f32<4, 4, 0, 1, 0> : step_kernel_f32<4, 4, 0, 0, 0>, 128, smem);
@@ -2037,7 +2051,7 @@ bool tuned_choice(const std::tuple<int, int, int, int, int, int>& key, std::pair
 bool pin_fits(const Group& g, int W, int tps)
 {
     const long long lim = device_smem_limit() - 1024;
-    if (g.ni != 4 && W != 4) return false;
+    if (g.var && W != 4) return false;
     for (const Instance* I : g.members)
         if ((long long)member_smem(g, I, W) > lim) return false;
     return tps == -1 || (tps >= 1 && ((g.n + W - 1) / W) % tps == 0);
@@ -2048,7 +2062,7 @@ std::vector<std::pair<int, int>> tune_candidates(const Group& g)
     std::vector<std::pair<int, int>> c;
     const long long lim = device_smem_limit() - 1024;
     for (int W : {8, 4, 2}) {
-        if (g.ni != 4 && W != 4) continue;
+        if (g.var && W != 4) continue;
         bool fits = true;
         for (const Instance* I : g.members) fits = fits && (long long)member_smem(g, I, W) <= lim;
         if (!fits) continue;
@@ -2097,7 +2111,8 @@ int rebuild_groups(vfps_batch* b)
     std::map<std::tuple<int, int, int, int>, std::vector<Instance*>> by_key;
     for (Instance* I : b->slots)
         if (I && remaining(I) > 0)
-            by_key[{I->p.precision, (I->p.interp_points * 2 + I->fast) * 2 + I->p.rotation, I->W, I->n}].push_back(I);
+            by_key[{I->p.precision, ((I->p.interp_points * 2 + I->p.clamp) * 2 + I->fast) * 2 + I->p.rotation, I->W,
+                    I->n}].push_back(I);
     std::vector<GroupPlan> cls;
     auto add_halves = [&](const std::tuple<int, int, int, int>& key, int pair, const std::vector<Instance*>& m) {
         // large groups in two halves (a pair group splits between pairs)
@@ -2186,8 +2201,9 @@ int rebuild_groups(vfps_batch* b)
     for (auto& kv : cls) {
         Group g;
         g.prec = std::get<0>(kv.key);
-        g.ni = std::get<1>(kv.key) / 4;
+        g.ni = std::get<1>(kv.key) / 8;
         g.fast = (std::get<1>(kv.key) >> 1) & 1;
+        g.var = !g.fast ? 0 : (((std::get<1>(kv.key) >> 2) & 1) ? 2 : (g.ni != 4 ? 1 : 0));
         g.pair = kv.pair;
         g.stream = b->pool[gi];
         g.t0 = b->timers[2 * gi];
@@ -2231,7 +2247,8 @@ int rebuild_groups(vfps_batch* b)
             const int cnt = (int)kv.members.size();
             int bucket = 1;
             while (bucket < cnt) bucket <<= 1;
-            g.tune_key = std::make_tuple(I0->n, g.prec, g.rot + 2 * g.pair + 4 * g.ni, I0->p.steps_per_period,
+            g.tune_key = std::make_tuple(I0->n, g.prec, g.rot + 2 * g.pair + 4 * g.ni + 32 * g.var,
+                                         I0->p.steps_per_period,
                                          bucket, I0->W);
             std::pair<int, int> best;
             if (b->pin_W && pin_fits(g, b->pin_W, b->pin_tps)) {
@@ -3125,6 +3142,7 @@ extern "C" int vfps_step_static(const vfps_params* params, int model, double Pi,
     g.ni = params->interp_points;
     g.W = W;
     g.fast = fast;
+    g.var = !fast ? 0 : (params->clamp ? 2 : (params->interp_points != 4 ? 1 : 0));
     g.kr = fast_kr(params->n);
     g.n = params->n;
     g.rot = params->rotation;

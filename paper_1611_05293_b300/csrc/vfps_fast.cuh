@@ -1,8 +1,12 @@
-// vfps_fast.cuh -- FP32 step kernel for the hot configuration (cubic
-// interpolation, no clamp, n a multiple of 4), written to issue few
-// instructions per cell.  Same arithmetic as step_kernel<float, 4, W>:
-// rotation (2-D cubic Lagrange, Sec. III.A-B), kick along p, Fokker-Planck
-// step (Eq. cubic diff), column sums, and the same last-CTA finaliser.
+// vfps_fast.cuh -- FP32 step kernel for grids with n a multiple of 4, written
+// to issue few instructions per cell: rotation (2-D Lagrange, Sec. III.A-B),
+// kick along p, Fokker-Planck step (Eq. cubic diff), column sums, and the
+// same last-CTA finaliser as step_kernel.  The hot configuration (cubic
+// interpolation, no clamp) is its own instance (NI = 4); N_I = 2 and 3 read
+// the order from the descriptor (NI = 0: their nodes fit the cubic 4-slot
+// layout with zero weights); clamping (Eq. clamping), at any order, is the
+// NI = 1 instance: each interpolated value is restricted to its nearest
+// nodes, which the same windows hold.
 //
 // Work of one lane: blocks of consecutive rows of its warp's column x.
 //  * Rotation, four rows y0..y0+3.  Along a column the source point moves
@@ -86,8 +90,8 @@ __device__ __forceinline__ void lagrange2(float2 t, float2 w[4])
 }
 
 // lagrange2 for N_I nodes in the cubic 4-slot layout (lagrange_w4_rt): NI = 4
-// is the compile-time cubic, NI = 0 takes the order (2 or 3) from ni; each
-// half of a pair as the scalar weights are.
+// is the compile-time cubic, NI = 0 and 1 take the order from ni; each half
+// of a pair as the scalar weights are.
 template <int NI>
 __device__ __forceinline__ void lagrange2_ni(float2 t, float2 w[4], int ni)
 {
@@ -107,6 +111,9 @@ __device__ __forceinline__ void lagrange_w4(float t, float w[4], int ni)
     if constexpr (NI == 4) lagrange_w<float, 4>(t, w);
     else lagrange_w4_rt(t, w, ni);
 }
+
+// v restricted to [min(lo), max(hi)] of its nearest nodes (reading 4).
+__device__ __forceinline__ float clamp_to(float v, float lo, float hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
 // Fokker-Planck weight g_k(y) of tap k (rows y-1 .. y+2) with the identity
 // folded into the centre tap, in one fixed order of operations (the FP32
@@ -132,8 +139,11 @@ __device__ __forceinline__ float fp_apply(float g0, float g1, float g2, float g3
 template <int O, int NI>
 __device__ __forceinline__ void rotate_block(const float* __restrict__ ring, int slot0, int R, int P, int rowoff,
                                              float2 tx01, float2 tx23, float2 ty01, float2 ty23, bool e1,
-                                             bool e2, bool e3, float out[4], int ni)
+                                             bool e2, bool e3, float out[4], int ni, bool clamp)
 {
+    // (NI = 1, clamped: the 2 x 2 nearest nodes of output k are window
+    // columns 2 - e_k, 3 - e_k, rows O + k + 1, O + k + 2)
+    float lo[4] = {3.4e38f, 3.4e38f, 3.4e38f, 3.4e38f}, hi[4] = {-3.4e38f, -3.4e38f, -3.4e38f, -3.4e38f};
     float2 wy01[4], wy23[4], wx01[4], wx23[4];
     lagrange2_ni<NI>(ty01, wy01, ni);
     lagrange2_ni<NI>(ty23, wy23, ni);
@@ -166,6 +176,12 @@ __device__ __forceinline__ void rotate_block(const float* __restrict__ ring, int
             v = fmaf(wy[k][2], win[O + k + 2], v);
             r[k] = fmaf(wy[k][3], win[O + k + 3], v);
             wa[k] = e[k] ? ((a <= 3) ? wx[k][a] : 0.f) : ((a >= 1) ? wx[k][a - 1] : 0.f);
+            if constexpr (NI == 1) {
+                if (clamp && (a == 2 - int(e[k]) || a == 3 - int(e[k]))) {
+                    lo[k] = fminf(lo[k], fminf(win[O + k + 1], win[O + k + 2]));
+                    hi[k] = fmaxf(hi[k], fmaxf(win[O + k + 1], win[O + k + 2]));
+                }
+            }
         }
         acc01 = __ffma2_rn(f2(wa[0], wa[1]), f2(r[0], r[1]), acc01);
         acc23 = __ffma2_rn(f2(wa[2], wa[3]), f2(r[2], r[3]), acc23);
@@ -174,6 +190,11 @@ __device__ __forceinline__ void rotate_block(const float* __restrict__ ring, int
     out[1] = acc01.y;
     out[2] = acc23.x;
     out[3] = acc23.y;
+    if constexpr (NI == 1) {
+        if (clamp)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) out[k] = clamp_to(out[k], lo[k], hi[k]);
+    }
 }
 
 // rotate_block when no row of the block steps back: the x-node of all four
@@ -182,8 +203,10 @@ __device__ __forceinline__ void rotate_block(const float* __restrict__ ring, int
 // column-0 terms are zeros).
 template <int O, int NI>
 __device__ __forceinline__ void rotate_block4(const float* __restrict__ ring, int slot0, int R, int P, int rowoff,
-                                              float2 tx01, float2 tx23, float2 ty01, float2 ty23, float out[4], int ni)
+                                              float2 tx01, float2 tx23, float2 ty01, float2 ty23, float out[4], int ni,
+                                              bool clamp)
 {
+    float lo[4] = {3.4e38f, 3.4e38f, 3.4e38f, 3.4e38f}, hi[4] = {-3.4e38f, -3.4e38f, -3.4e38f, -3.4e38f};
     float2 wy01[4], wy23[4], wx01[4], wx23[4];
     lagrange2_ni<NI>(ty01, wy01, ni);
     lagrange2_ni<NI>(ty23, wy23, ni);
@@ -206,6 +229,14 @@ __device__ __forceinline__ void rotate_block4(const float* __restrict__ ring, in
             r23 = __ffma2_rn(wy23[b], f2(win[O + b + 2], win[O + b + 3]), r23);
         }
         const float r[4] = {r01.x, r01.y, r23.x, r23.y};
+        if constexpr (NI == 1) {
+            if (clamp && (a == 2 || a == 3))
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    lo[k] = fminf(lo[k], fminf(win[O + k + 1], win[O + k + 2]));
+                    hi[k] = fmaxf(hi[k], fmaxf(win[O + k + 1], win[O + k + 2]));
+                }
+        }
         if (a == 1) {
             acc01 = __fmul2_rn(wx01[0], f2(r[0], r[1]));
             acc23 = __fmul2_rn(wx23[0], f2(r[2], r[3]));
@@ -218,6 +249,11 @@ __device__ __forceinline__ void rotate_block4(const float* __restrict__ ring, in
     out[1] = acc01.y;
     out[2] = acc23.x;
     out[3] = acc23.y;
+    if constexpr (NI == 1) {
+        if (clamp)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) out[k] = clamp_to(out[k], lo[k], hi[k]);
+    }
 }
 
 // Offset of the psi_a column row kColPad + yb + 4 lane (start of a
@@ -245,14 +281,15 @@ __device__ __forceinline__ int cola_block_off(int yb)
 // the FP weights g_k(y) as four rows of n (split layout for KR = 8), with
 // the identity folded into the centre tap: psi_c(y) = sum_k g_k(y) psi_b(y-1+k).
 // SMALL: s is -1 or 0 (kicks under one cell), where the edge test reduces to
-// the rows just outside the grid.
+// the rows just outside the grid.  NI = 1 (clamped): each psi_b value is
+// restricted to its two nearest nodes (times csf).
 //
 // FP = false (the RF kick of the Manhattan rotation): only the shift, psi_b of
 // the lane's own rows goes to the psi_a-layout column dst (shared memory).
-template <int O2, int PAR, int KR, bool SMALL, bool FP = true>
+template <int O2, int PAR, int KR, bool SMALL, bool FP = true, int NI = 4>
 __device__ __forceinline__ float kick_fp_column(const float* __restrict__ colcol, int HC,
                                                 const float* __restrict__ g, float* __restrict__ dst, int n, int s,
-                                                int A2, float4 w, int lane)
+                                                int A2, float4 w, int lane, bool clamp = false, float csf = 1.f)
 {
     constexpr int NB = KR + 3;                  // psi_b rows y0-1 .. y0+KR+1
     constexpr int NV = (O2 + NB + 3 + 3) / 4;   // float4 reads of the window
@@ -300,6 +337,15 @@ __device__ __forceinline__ float kick_fp_column(const float* __restrict__ colcol
             v = fmaf(w.y, win[O2 + j + 1], v);
             v = fmaf(w.z, win[O2 + j + 2], v);
             b[j] = fmaf(w.w, win[O2 + j + 3], v);
+        }
+        if constexpr (NI == 1) {
+            // clamped: between its two nearest nodes, window rows O2 + j + 1, + 2
+            // (times csf, the pending scale that the weights carry)
+            if (clamp)
+#pragma unroll
+                for (int j = 0; j < NB; ++j)
+                    b[j] = clamp_to(b[j], csf * fminf(win[O2 + j + 1], win[O2 + j + 2]),
+                                    csf * fmaxf(win[O2 + j + 1], win[O2 + j + 2]));
         }
         if constexpr (SMALL) {
             // s in {-1, 0}: every on-grid row has its source within one cell
@@ -365,7 +411,7 @@ __device__ __forceinline__ bool cell_weights(int x, int y, int n, float cm1, flo
 // column col stored in ring slot col & (R-1).
 template <int NI>
 __device__ __forceinline__ float rotate_cell_ring(const float* __restrict__ ring, int R, int P, int RP, int x, int y,
-                                                  int n, float cm1, float sn, float c, int ni)
+                                                  int n, float cm1, float sn, float c, int ni, bool clamp)
 {
     int mx, my;
     float wx[4], wy[4];
@@ -378,6 +424,14 @@ __device__ __forceinline__ float rotate_cell_ring(const float* __restrict__ ring
 #pragma unroll
         for (int b = 0; b < 4; ++b) r = fmaf(wy[b], col[b], r);
         acc = fmaf(wx[a], r, acc);
+    }
+    if constexpr (NI == 1) {
+        if (clamp) {  // the 2 x 2 nearest nodes (mx, my) .. (mx + 1, my + 1)
+            const float* c0 = ring + (mx & (R - 1)) * P + my + RP;
+            const float* c1 = ring + ((mx + 1) & (R - 1)) * P + my + RP;
+            acc = clamp_to(acc, fminf(fminf(c0[0], c0[1]), fminf(c1[0], c1[1])),
+                           fmaxf(fmaxf(c0[0], c0[1]), fmaxf(c1[0], c1[1])));
+        }
     }
     return acc;
 }
@@ -440,7 +494,7 @@ __device__ __forceinline__ void load_kick(float4* dst, const float4* __restrict_
 template <int O, int KR, int NI>
 __device__ __forceinline__ void rotate_column(const float* __restrict__ ring, int R, int P, int RP, int A,
                                               float* __restrict__ colcol, int HC, int x, int n, int lane, float xc,
-                                              float c, float sn, float cm1, int FY, int ni)
+                                              float c, float sn, float cm1, int FY, int ni, bool clamp)
 {
     const float2 msn2 = f2(-sn, -sn), cm12 = f2(cm1, cm1);
     const float2 snxc = f2(sn * xc, sn * xc), cmxc = f2(cm1 * xc, cm1 * xc);
@@ -470,9 +524,9 @@ __device__ __forceinline__ void rotate_column(const float* __restrict__ ring, in
         if (!live) continue;
         if (anyback)
             rotate_block<O, NI>(ring, (mx0 - 2) & (R - 1), R, P, y0 + A - O, tx01, tx23, ty01, ty23, fx1 < fx0,
-                                fx2 < fx0, fx3 < fx0, r, ni);
+                                fx2 < fx0, fx3 < fx0, r, ni, clamp);
         else
-            rotate_block4<O, NI>(ring, (mx0 - 2) & (R - 1), R, P, y0 + A - O, tx01, tx23, ty01, ty23, r, ni);
+            rotate_block4<O, NI>(ring, (mx0 - 2) & (R - 1), R, P, y0 + A - O, tx01, tx23, ty01, ty23, r, ni, clamp);
         // sources more than one cell outside the grid give 0
         if (!((mx0 >= 0) && (mx0 <= n - 1) && (y0 + FY >= -1) && (y0 + 3 + FY <= n - 1))) {
             const float fxk[4] = {fx0, fx1, fx2, fx3};
@@ -496,7 +550,7 @@ __device__ __forceinline__ void rotate_column(const float* __restrict__ ring, in
 template <int KR, int NI>
 __device__ __forceinline__ void drift_column(const float* __restrict__ ring, int R, int P, int RP,
                                              float* __restrict__ colcol, int HC, int x, int n, int lane, float c,
-                                             float hm, int ni)
+                                             float hm, int ni, bool clamp)
 {
     const int lbase = cola_lane_base<KR>(lane, HC);
 #pragma unroll 1
@@ -517,6 +571,7 @@ __device__ __forceinline__ void drift_column(const float* __restrict__ ring, int
         const int mx0 = x + int(fx0);
         const int slot0 = (mx0 - 2) & (R - 1);  // window columns mx0-2 .. mx0+2
         float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        float lo[4] = {3.4e38f, 3.4e38f, 3.4e38f, 3.4e38f}, hi[4] = {-3.4e38f, -3.4e38f, -3.4e38f, -3.4e38f};
 #pragma unroll
         for (int a = 0; a < 5; ++a) {
             const float4 q = VFPS_GUARD(RP + y0 + 4 <= P && slot0 >= 0 && slot0 < R, 3)
@@ -527,7 +582,18 @@ __device__ __forceinline__ void drift_column(const float* __restrict__ ring, int
             for (int k = 0; k < 4; ++k) {
                 const float wa = e[k] ? ((a <= 3) ? wx[k][a] : 0.f) : ((a >= 1) ? wx[k][a - 1] : 0.f);
                 acc[k] = fmaf(wa, v[k], acc[k]);
+                if constexpr (NI == 1) {  // nearest nodes: window columns 2 - e_k, 3 - e_k
+                    if (clamp && (a == 2 - int(e[k]) || a == 3 - int(e[k]))) {
+                        lo[k] = fminf(lo[k], v[k]);
+                        hi[k] = fmaxf(hi[k], v[k]);
+                    }
+                }
             }
+        }
+        if constexpr (NI == 1) {
+            if (clamp)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) acc[k] = clamp_to(acc[k], lo[k], hi[k]);
         }
         // sources more than one cell outside the grid give 0
         if (!(mx0 >= 0 && mx0 <= n - 1)) {
@@ -711,6 +777,7 @@ __device__ __forceinline__ bool strip_f32(const Desc<float>& D, int xs, int T, u
     constexpr int rot = ROT;            // 1: Manhattan rotation (every instance of the launch)
     const float hm = D.hm;
     const int ni = NI == 4 ? 4 : D.ni;  // interpolation points (NI = 0: from the descriptor)
+    const bool clamp = NI == 1;  // clamped interpolation (the NI = 1 instance)
     float* colbcol = reinterpret_cast<float*>(reinterpret_cast<float4*>(gtab + 4 * n) + 8 * W) + warp * PA;
 
     // padding rows of every ring slot and of this warp's psi_a column: zero
@@ -757,7 +824,7 @@ __device__ __forceinline__ bool strip_f32(const Desc<float>& D, int xs, int T, u
         cp_async_wait_1();
         __syncthreads();
         if (active && rot) {
-            drift_column<KR, NI>(ring, R, P, RP, colcol, HC, x, n, lane, c, hm, ni);
+            drift_column<KR, NI>(ring, R, P, RP, colcol, HC, x, n, lane, c, hm, ni, clamp);
         } else if (active) {
             const float xc = float(x) - c;
             // dy is linear along the column: floor(dy) is the same on every row
@@ -768,14 +835,14 @@ __device__ __forceinline__ bool strip_f32(const Desc<float>& D, int xs, int T, u
                 const int FY = int(fy_top);
                 const int A = FY - 1 + RP;
                 switch (A & 3) {
-                case 0: rotate_column<0, KR, NI>(ring, R, P, RP, A, colcol, HC, x, n, lane, xc, c, sn, cm1, FY, ni); break;
-                case 1: rotate_column<1, KR, NI>(ring, R, P, RP, A, colcol, HC, x, n, lane, xc, c, sn, cm1, FY, ni); break;
-                case 2: rotate_column<2, KR, NI>(ring, R, P, RP, A, colcol, HC, x, n, lane, xc, c, sn, cm1, FY, ni); break;
-                default: rotate_column<3, KR, NI>(ring, R, P, RP, A, colcol, HC, x, n, lane, xc, c, sn, cm1, FY, ni); break;
+                case 0: rotate_column<0, KR, NI>(ring, R, P, RP, A, colcol, HC, x, n, lane, xc, c, sn, cm1, FY, ni, clamp); break;
+                case 1: rotate_column<1, KR, NI>(ring, R, P, RP, A, colcol, HC, x, n, lane, xc, c, sn, cm1, FY, ni, clamp); break;
+                case 2: rotate_column<2, KR, NI>(ring, R, P, RP, A, colcol, HC, x, n, lane, xc, c, sn, cm1, FY, ni, clamp); break;
+                default: rotate_column<3, KR, NI>(ring, R, P, RP, A, colcol, HC, x, n, lane, xc, c, sn, cm1, FY, ni, clamp); break;
                 }
             } else {
                 for (int y = lane; y < n; y += 32)
-                    colcol[split_idx<KR>(kColPad + y, HC)] = rotate_cell_ring<NI>(ring, R, P, RP, x, y, n, cm1, sn, c, ni);
+                    colcol[split_idx<KR>(kColPad + y, HC)] = rotate_cell_ring<NI>(ring, R, P, RP, x, y, n, cm1, sn, c, ni, clamp);
             }
         }
         __syncwarp();
@@ -791,14 +858,14 @@ __device__ __forceinline__ bool strip_f32(const Desc<float>& D, int xs, int T, u
             if (sr >= -4 && sr <= 4) {
                 const int A2 = sr - 2 + kColPad;
                 switch (KR == 8 ? (A2 & 7) : (A2 & 3)) {
-                case 0: kick_fp_column<0, 0, KR, false, false>(colcol, HC, gtab, colbcol, n, sr, A2, w4, lane); break;
-                case 1: kick_fp_column<1, 0, KR, false, false>(colcol, HC, gtab, colbcol, n, sr, A2, w4, lane); break;
-                case 2: kick_fp_column<2, 0, KR, false, false>(colcol, HC, gtab, colbcol, n, sr, A2, w4, lane); break;
-                case 3: kick_fp_column<3, 0, KR, false, false>(colcol, HC, gtab, colbcol, n, sr, A2, w4, lane); break;
-                case 4: kick_fp_column<0, 1, KR, false, false>(colcol, HC, gtab, colbcol, n, sr, A2, w4, lane); break;
-                case 5: kick_fp_column<1, 1, KR, KR == 8, false>(colcol, HC, gtab, colbcol, n, sr, A2, w4, lane); break;
-                case 6: kick_fp_column<2, 1, KR, KR == 8, false>(colcol, HC, gtab, colbcol, n, sr, A2, w4, lane); break;
-                default: kick_fp_column<3, 1, KR, false, false>(colcol, HC, gtab, colbcol, n, sr, A2, w4, lane); break;
+                case 0: kick_fp_column<0, 0, KR, false, false, NI>(colcol, HC, gtab, colbcol, n, sr, A2, w4, lane, clamp); break;
+                case 1: kick_fp_column<1, 0, KR, false, false, NI>(colcol, HC, gtab, colbcol, n, sr, A2, w4, lane, clamp); break;
+                case 2: kick_fp_column<2, 0, KR, false, false, NI>(colcol, HC, gtab, colbcol, n, sr, A2, w4, lane, clamp); break;
+                case 3: kick_fp_column<3, 0, KR, false, false, NI>(colcol, HC, gtab, colbcol, n, sr, A2, w4, lane, clamp); break;
+                case 4: kick_fp_column<0, 1, KR, false, false, NI>(colcol, HC, gtab, colbcol, n, sr, A2, w4, lane, clamp); break;
+                case 5: kick_fp_column<1, 1, KR, KR == 8, false, NI>(colcol, HC, gtab, colbcol, n, sr, A2, w4, lane, clamp); break;
+                case 6: kick_fp_column<2, 1, KR, KR == 8, false, NI>(colcol, HC, gtab, colbcol, n, sr, A2, w4, lane, clamp); break;
+                default: kick_fp_column<3, 1, KR, false, false, NI>(colcol, HC, gtab, colbcol, n, sr, A2, w4, lane, clamp); break;
                 }
             } else {
                 for (int y = lane; y < n; y += 32) {
@@ -810,6 +877,11 @@ __device__ __forceinline__ bool strip_f32(const Desc<float>& D, int xs, int T, u
                             const int rr = m - 1 + k;
                             if (rr >= 0 && rr < n) v += wr[k] * colcol[split_idx<KR>(kColPad + rr, HC)];
                         }
+                        if (clamp) {
+                            const float a0 = m >= 0 ? colcol[split_idx<KR>(kColPad + m, HC)] : 0.f;
+                            const float a1 = m + 1 < n ? colcol[split_idx<KR>(kColPad + m + 1, HC)] : 0.f;
+                            v = clamp_to(v, fminf(a0, a1), fmaxf(a0, a1));
+                        }
                     }
                     colbcol[split_idx<KR>(kColPad + y, HC)] = v;
                 }
@@ -820,6 +892,7 @@ __device__ __forceinline__ bool strip_f32(const Desc<float>& D, int xs, int T, u
         bool kick_ok = true;
         float4 kw = make_float4(0.f, 0.f, 0.f, 0.f);
         int s = 0;
+        float csf = 1.f;  // the pending scale in the weights (clamp bounds)
         if (active && recs) {
             // the kick of column x and the pending scale of this step: the
             // finaliser CTA's records (lane 0 and lane 1 wait)
@@ -832,6 +905,7 @@ __device__ __forceinline__ bool strip_f32(const Desc<float>& D, int xs, int T, u
                 const KickEntry e = kick_entry(__uint_as_float(rk), __uint_as_float(rs), ni);
                 kw = e.w;
                 s = e.s;
+                csf = __uint_as_float(rs);
             } else if (lane == 0) {
                 s_last = 1;
             }
@@ -839,6 +913,7 @@ __device__ __forceinline__ bool strip_f32(const Desc<float>& D, int xs, int T, u
             const float4* kj = kbuf + 2 * W * (j & 3);
             kw = kj[0];
             s = __float_as_int(kj[1].x);
+            csf = kj[1].y;
         }
         if (active && kick_ok) {
             float* dst = out + (size_t)x * ld;
@@ -847,14 +922,14 @@ __device__ __forceinline__ bool strip_f32(const Desc<float>& D, int xs, int T, u
                 const int A2 = s - 2 + kColPad;  // column index of row y0+s-2, minus y0
                 // A2 = s + 14 with |s| <= 4: (A2 & 7) = 5 and 6 are s = -1 and 0 only
                 switch (KR == 8 ? (A2 & 7) : (A2 & 3)) {
-                case 0: lsum = kick_fp_column<0, 0, KR, false>(kcol, HC, gtab, dst, n, s, A2, kw, lane); break;
-                case 1: lsum = kick_fp_column<1, 0, KR, false>(kcol, HC, gtab, dst, n, s, A2, kw, lane); break;
-                case 2: lsum = kick_fp_column<2, 0, KR, false>(kcol, HC, gtab, dst, n, s, A2, kw, lane); break;
-                case 3: lsum = kick_fp_column<3, 0, KR, false>(kcol, HC, gtab, dst, n, s, A2, kw, lane); break;
-                case 4: lsum = kick_fp_column<0, 1, KR, false>(kcol, HC, gtab, dst, n, s, A2, kw, lane); break;
-                case 5: lsum = kick_fp_column<1, 1, KR, KR == 8>(kcol, HC, gtab, dst, n, s, A2, kw, lane); break;
-                case 6: lsum = kick_fp_column<2, 1, KR, KR == 8>(kcol, HC, gtab, dst, n, s, A2, kw, lane); break;
-                default: lsum = kick_fp_column<3, 1, KR, false>(kcol, HC, gtab, dst, n, s, A2, kw, lane); break;
+                case 0: lsum = kick_fp_column<0, 0, KR, false, true, NI>(kcol, HC, gtab, dst, n, s, A2, kw, lane, clamp, csf); break;
+                case 1: lsum = kick_fp_column<1, 0, KR, false, true, NI>(kcol, HC, gtab, dst, n, s, A2, kw, lane, clamp, csf); break;
+                case 2: lsum = kick_fp_column<2, 0, KR, false, true, NI>(kcol, HC, gtab, dst, n, s, A2, kw, lane, clamp, csf); break;
+                case 3: lsum = kick_fp_column<3, 0, KR, false, true, NI>(kcol, HC, gtab, dst, n, s, A2, kw, lane, clamp, csf); break;
+                case 4: lsum = kick_fp_column<0, 1, KR, false, true, NI>(kcol, HC, gtab, dst, n, s, A2, kw, lane, clamp, csf); break;
+                case 5: lsum = kick_fp_column<1, 1, KR, KR == 8, true, NI>(kcol, HC, gtab, dst, n, s, A2, kw, lane, clamp, csf); break;
+                case 6: lsum = kick_fp_column<2, 1, KR, KR == 8, true, NI>(kcol, HC, gtab, dst, n, s, A2, kw, lane, clamp, csf); break;
+                default: lsum = kick_fp_column<3, 1, KR, false, true, NI>(kcol, HC, gtab, dst, n, s, A2, kw, lane, clamp, csf); break;
                 }
             } else {
                 // large kick: plain per-row evaluation with bounds
@@ -871,6 +946,11 @@ __device__ __forceinline__ bool strip_f32(const Desc<float>& D, int xs, int T, u
                             for (int k = 0; k < 4; ++k) {
                                 const int rr = mm - 1 + k;
                                 if (rr >= 0 && rr < n) v = fmaf(w[k], kcol[split_idx<KR>(kColPad + rr, HC)], v);
+                            }
+                            if (clamp) {
+                                const float a0 = mm >= 0 ? kcol[split_idx<KR>(kColPad + mm, HC)] : 0.f;
+                                const float a1 = mm + 1 < n ? kcol[split_idx<KR>(kColPad + mm + 1, HC)] : 0.f;
+                                v = clamp_to(v, csf * fminf(a0, a1), csf * fmaxf(a0, a1));
                             }
                         }
                         b[d] = v;

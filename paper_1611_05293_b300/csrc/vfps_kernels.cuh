@@ -16,7 +16,8 @@
 //   kick     n T, p-shift of column x in grid cells for the next step
 //   kickw    2n float4 (FP32 instances): per column x, [2x] the cubic weights
 //            of that shift times the pending scale, [2x+1].x the node shift
-//            floor(-kick) as int bits
+//            floor(-kick) as int bits, [2x+1].y the pending scale (the clamp
+//            bounds of a clamped kick)
 //   pring    ring of CSR powers, pring[t] = P(psi_t)
 //   qring    ring of charges before renormalisation, qring[t] = Q of step t
 //   mring    (optional) ring of bunch moments, mring[4t..4t+3] = <q>, sigma_q,
@@ -784,7 +785,7 @@ __device__ void finalise_compute(const Desc<T>& D, unsigned char* smem, int is_s
         if constexpr (sizeof(T) == 4) {
             const KickEntry e = kick_entry(k, float(s_new), D.ni);
             D.kickw[2 * x] = e.w;
-            D.kickw[2 * x + 1] = make_float4(__int_as_float(e.s), 0.f, 0.f, 0.f);
+            D.kickw[2 * x + 1] = make_float4(__int_as_float(e.s), float(s_new), 0.f, 0.f);
         }
     }
     if (tid == 0) {

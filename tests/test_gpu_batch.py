@@ -36,20 +36,22 @@ def alone(V, n, spp, S, Pi, nsteps, psi0, beta=1e-2):
 
 
 def test_lower_order_slots_equal_solo_runs_bitwise(V):
-    """N_I = 2, 3 and 4 slots of several grid sizes and both rotations in one
-    batch (launch groups by interpolation order): each equals its solo run."""
-    mix = [(64, 500, 0.9, 2.0, 150, 3, 0), (128, 700, 1.2, 1.0, 120, 3, 0), (64, 500, 0.9, 2.0, 150, 4, 0),
-           (96, 600, 0.7, 2.0, 90, 2, 0), (64, 400, 0.8, 2.0, 110, 3, 1)]
+    """N_I = 2, 3 and 4 slots, clamped and not, of several grid sizes and both
+    rotations in one batch (launch groups by interpolation order and clamp):
+    each equals its solo run."""
+    mix = [(64, 500, 0.9, 2.0, 150, 3, 0, 0), (128, 700, 1.2, 1.0, 120, 3, 0, 0), (64, 500, 0.9, 2.0, 150, 4, 0, 0),
+           (96, 600, 0.7, 2.0, 90, 2, 0, 0), (64, 400, 0.8, 2.0, 110, 3, 1, 0), (64, 500, 0.9, 2.0, 150, 4, 0, 1),
+           (64, 400, 0.8, 2.0, 110, 3, 1, 1)]
     b = V.Batch(len(mix))
     slots = []
-    for i, (n, spp, S, Pi, ns, ni, rot) in enumerate(mix):
-        slots.append(b.add(V.Params(n=n, steps_per_period=spp, beta=1e-2, interp_points=ni, rotation=rot),
+    for i, (n, spp, S, Pi, ns, ni, rot, cl) in enumerate(mix):
+        slots.append(b.add(V.Params(n=n, steps_per_period=spp, beta=1e-2, interp_points=ni, rotation=rot, clamp=cl),
                            W.blobs(n, 300 + i), V.IMPEDANCE_PARALLEL_PLATES, Pi, S, nsteps=ns))
     b.run(10_000)
     res = [b.take(s) for s in slots]
     b.close()
-    for i, (n, spp, S, Pi, ns, ni, rot) in enumerate(mix):
-        sim = V.Simulation(V.Params(n=n, steps_per_period=spp, beta=1e-2, interp_points=ni, rotation=rot),
+    for i, (n, spp, S, Pi, ns, ni, rot, cl) in enumerate(mix):
+        sim = V.Simulation(V.Params(n=n, steps_per_period=spp, beta=1e-2, interp_points=ni, rotation=rot, clamp=cl),
                            W.blobs(n, 300 + i))
         sim.set_impedance(V.IMPEDANCE_PARALLEL_PLATES, Pi, S)
         sim.step(ns)

@@ -88,15 +88,17 @@ def test_one_step_matches_oracle(V, precision, tol, n, kind, model, Pi, S, extra
     sim.close()
 
 
-@pytest.mark.parametrize("ni,rotation", [(3, 0), (2, 0), (3, 1)])
-def test_lower_order_fp32_run_matches_oracle(V, ni, rotation):
-    """N_I = 3 and 2 in the FP32 register-blocked kernel (their weights in the
-    cubic 4-slot layout, reading 3): 200 steps of N=64 at 200 steps/period,
-    wake on, against the FP64 oracle."""
+@pytest.mark.parametrize("ni,rotation,clamp", [(3, 0, 0), (2, 0, 0), (3, 1, 0), (4, 0, 1), (3, 0, 1), (4, 1, 1),
+                                                (2, 1, 1)])
+def test_variant_fp32_run_matches_oracle(V, ni, rotation, clamp):
+    """N_I = 3 and 2 and clamping in the FP32 register-blocked kernel (weights
+    in the cubic 4-slot layout, reading 3; bounds from the nearest nodes,
+    reading 4): 200 steps of N=64 at 200 steps/period, wake on, against the
+    FP64 oracle."""
     n, spp, steps = 64, 200, 200
     psi0 = W.blobs(n, 5)
     sim, op, zr, zi = make(V, n, 0, spp=spp, beta=0.05, model=2, Pi=2.0, S=0.6, psi=psi0,
-                           interp_points=ni, rotation=rotation)
+                           interp_points=ni, rotation=rotation, clamp=clamp)
     ref, Pref, _ = O.run(op, zr, zi, O.normalize(op, psi0), steps)
     sim.step(steps)
     assert rel_linf(sim.get_state(), ref) < 1e-4
