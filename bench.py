@@ -328,13 +328,36 @@ def c3_scan_64(V, torch, stream, warmup, steps=100):
             "l2": "flushed before every timed step"}
 
 
-GRAPH_STEPS = 32  # a lone simulation replays CUDA graphs of this many steps
+GRAPH_STEPS = 32  # batches replay CUDA graphs of this many steps; timed step counts are whole graphs
 
 
 def solo_warmup(sim, warmup):
-    """Warm-up of a lone simulation: at least two graph replays, so that the
-    graph is captured and instantiated before the timed region."""
+    """Warm-up of a lone simulation before its timed region (it steps in
+    persistent launches, or in CUDA graphs of GRAPH_STEPS steps where those do
+    not apply): at least 2 GRAPH_STEPS steps."""
     sim.step(max(warmup, 2 * GRAPH_STEPS))
+
+
+def c3_n1024_64(V, torch, stream, warmup, steps=64):
+    """A 64-instance copy of the scan at N=1024 (4000 steps/period): its state
+    (2 x 268 MB) exceeds L2, so the batched step is timed back to back for a
+    pure-HBM number."""
+    calibrate(V, torch, stream, 64, n=1024, spp=4000, steps=256)
+    b = build_batch(V, 64, 1024, 4000, 1e-2, stream)
+    b.run(max(warmup, 2 * GRAPH_STEPS))
+    torch.cuda.synchronize()
+    head_start(torch, stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.run(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dt = e0.elapsed_time(e1) / 1e3
+    b.close()
+    cells = 64 * 1024 * 1024
+    return {"value": cells * steps / dt, "unit": "cell-updates/s", "ms_per_step": 1e3 * dt / steps,
+            "roofline_frac": 8.0 * cells / (dt / steps) / 1e9 / measured_peaks()[0],
+            "workload": "64 x N=1024 scan, 4000 steps/period, state larger than L2"}
 
 
 def c5_single(V, torch, stream, warmup, steps=512):
@@ -645,6 +668,7 @@ def main():
     if not args.no_extra:
         line["c3_scan_64"] = c3_scan_64(V, torch, stream, args.warmup)
         line["c5_n1024"] = c5_single(V, torch, stream, args.warmup)
+        line["c3_n1024_64"] = c3_n1024_64(V, torch, stream, args.warmup)
         line["manhattan_scan"] = manhattan_scan(V, torch, stream, args.warmup)
         line["m6_rotation_n512"] = m6_rotation(V, torch, stream, args.warmup)
         line["moments_cost"] = moments_cost(V, torch, stream, args.warmup)
