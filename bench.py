@@ -342,7 +342,7 @@ def c3_n1024_64(V, torch, stream, warmup, steps=64):
     """A 64-instance copy of the scan at N=1024 (4000 steps/period): its state
     (2 x 268 MB) exceeds L2, so the batched step is timed back to back for a
     pure-HBM number."""
-    calibrate(V, torch, stream, 64, n=1024, spp=4000, steps=256)
+    calibrate(V, torch, stream, 64, n=1024, spp=4000, steps=1024)  # ~21 candidate shapes of 32 steps
     b = build_batch(V, 64, 1024, 4000, 1e-2, stream)
     b.run(max(warmup, 2 * GRAPH_STEPS))
     torch.cuda.synchronize()

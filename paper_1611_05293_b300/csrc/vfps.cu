@@ -188,7 +188,7 @@ size_t fast_smem(const vfps_params* p, int W)
 bool pair_eligible(const vfps_params* p)
 {
     return fast_eligible(p) && p->interp_points == 4 && !p->clamp && p->rotation == 0 && (p->n % 32) == 0 &&
-           halo_for(p) <= 12;
+           p->n < 1024 && halo_for(p) <= 12;
 }
 
 size_t pair_smem(const vfps_params* p, int W)
@@ -866,11 +866,11 @@ template <int W, int KR, int NC, int NI = 4>
 int launch_fast_k(const Group& g, cudaStream_t s)
 {
     if (g.rot)
-        CU(launch_pdl(step_kernel_f32<W, KR, NC, 1, NI>, g.grid, W * 32, g.smem, s, (const Desc<float>*)g.ddescs,
-                      (const int4*)g.dsegs, g.spc));
+        CU(launch_pdl(step_kernel_f32<W, KR, NC, 1, NI>, g.grid, fast_threads(W, NC), g.smem, s,
+                      (const Desc<float>*)g.ddescs, (const int4*)g.dsegs, g.spc));
     else
-        CU(launch_pdl(step_kernel_f32<W, KR, NC, 0, NI>, g.grid, W * 32, g.smem, s, (const Desc<float>*)g.ddescs,
-                      (const int4*)g.dsegs, g.spc));
+        CU(launch_pdl(step_kernel_f32<W, KR, NC, 0, NI>, g.grid, fast_threads(W, NC), g.smem, s,
+                      (const Desc<float>*)g.ddescs, (const int4*)g.dsegs, g.spc));
     return VFPS_OK;
 }
 
@@ -976,6 +976,19 @@ const void* persist_fn(const Group& g)
     return nullptr;
 }
 
+// Threads per CTA of an FP32 group's kernel (the N = 1024 instance has two
+// warps per column).
+int group_threads(const Group& g)
+{
+    return g.W * 32 * ((g.fast && !g.pair && !g.var && g.kr == 8 && g.n == 1024) ? 2 : 1);
+}
+
+// Threads per CTA of a group's persistent kernel.
+int persist_group_threads(const Group& g)
+{
+    return g.W * 32 * ((g.kr == 8 && g.n == 1024) ? kPersistRS : 1);
+}
+
 // K steps of a lone simulation in one cooperative launch: g.grid worker CTAs
 // and one finaliser CTA.  First every tagged word and step flag goes to 0
 // (a launch's own steps are tagged from 1; a launch that timed out leaves
@@ -988,7 +1001,7 @@ int launch_persistent(const Group& g, const Instance& I, int K, cudaStream_t s)
     const Desc<float>* d = (const Desc<float>*)g.ddescs;
     const int4* sg = (const int4*)g.dsegs;
     void* args[3] = {(void*)&d, (void*)&sg, (void*)&K};
-    CU(cudaLaunchCooperativeKernel(f, dim3(g.grid + 1), dim3(g.W * 32), args, g.smem, s));
+    CU(cudaLaunchCooperativeKernel(f, dim3(g.grid + 1), dim3(persist_group_threads(g)), args, g.smem, s));
     return VFPS_OK;
 }
 
@@ -1519,7 +1532,8 @@ static bool use_persistent(vfps_handle* h, const Group& g)
         h->persist = 0;
         const void* f = persist_fn(g);
         int per_sm = 0;
-        if (f && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, g.W * 32, g.smem) == cudaSuccess &&
+        if (f && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, persist_group_threads(g), g.smem) ==
+                     cudaSuccess &&
             (long long)per_sm * num_sms() >= (long long)g.grid + 1)
             h->persist = 1;
     }
@@ -1896,8 +1910,8 @@ int fast_blocks_t(const Group& g, size_t smem)
         if (g.n == 256)
             return blocks_per_sm(g.rot ? step_kernel_f32<W, 8, 256, 1> : step_kernel_f32<W, 8, 256, 0>, W * 32, smem);
         if (g.n == 1024)
-            return blocks_per_sm(g.rot ? step_kernel_f32<W, 8, 1024, 1> : step_kernel_f32<W, 8, 1024, 0>, W * 32,
-                                 smem);
+            return blocks_per_sm(g.rot ? step_kernel_f32<W, 8, 1024, 1> : step_kernel_f32<W, 8, 1024, 0>,
+                                 fast_threads(W, 1024), smem);
         return blocks_per_sm(g.rot ? step_kernel_f32<W, 8, 0, 1> : step_kernel_f32<W, 8, 0, 0>, W * 32, smem);
     }
     return blocks_per_sm(g.rot ? step_kernel_f32<W, 4, 0, 1> : step_kernel_f32<W, 4, 0, 0>, W * 32, smem);

@@ -280,8 +280,9 @@ __device__ __forceinline__ int cola_block_off(int yb)
 // column's kick weights (pending scale included), s its node shift; g holds
 // the FP weights g_k(y) as four rows of n (split layout for KR = 8), with
 // the identity folded into the centre tap: psi_c(y) = sum_k g_k(y) psi_b(y-1+k).
-// SMALL: s is -1 or 0 (kicks under one cell), where the edge test reduces to
-// the rows just outside the grid.  NI = 1 (clamped): each psi_b value is
+// Rows ylo .. yhi - 1 (block-aligned: multiples of 32 KR, yhi = n or such a
+// multiple).  SMALL: s is -1 or 0 (kicks under one cell), where the edge test
+// reduces to the rows just outside the grid.  NI = 1 (clamped): each psi_b value is
 // restricted to its two nearest nodes (times csf).
 //
 // FP = false (the RF kick of the Manhattan rotation): only the shift, psi_b of
@@ -289,7 +290,7 @@ __device__ __forceinline__ int cola_block_off(int yb)
 template <int O2, int PAR, int KR, bool SMALL, bool FP = true, int NI = 4>
 __device__ __forceinline__ float kick_fp_column(const float* __restrict__ colcol, int HC,
                                                 const float* __restrict__ g, float* __restrict__ dst, int n, int s,
-                                                int A2, float4 w, int lane, bool clamp = false, float csf = 1.f)
+                                                int A2, float4 w, int lane, bool clamp, float csf, int ylo, int yhi)
 {
     constexpr int NB = KR + 3;                  // psi_b rows y0-1 .. y0+KR+1
     constexpr int NV = (O2 + NB + 3 + 3) / 4;   // float4 reads of the window
@@ -297,7 +298,7 @@ __device__ __forceinline__ float kick_fp_column(const float* __restrict__ colcol
     const int lo = max(0, -1 - s), hi = min(n - 1, n - 1 - s);
     float lsum = 0.f;
 #pragma unroll
-    for (int yb = 0; yb < n; yb += 32 * KR) {
+    for (int yb = ylo; yb < yhi; yb += 32 * KR) {
         const int y0 = yb + KR * lane;
         if ((n % (32 * KR)) && y0 >= n) break;
         float win[4 * NV];
@@ -468,13 +469,14 @@ __host__ __device__ inline int ring_slots(int W, int h)
 }
 
 // Shared memory of the FP32 streaming kernel: ring, psi_a columns, FP
-// weights, a 4-stage buffer of the tiles' kick-table entries, and for the
-// Manhattan rotation a second set of columns (the RF-kicked psi).
+// weights, a 4-stage buffer of the tiles' kick-table entries, for the
+// Manhattan rotation a second set of columns (the RF-kicked psi), and for
+// n >= 1024 the upper-half lane partials of the W columns.
 __host__ inline size_t fast_ring_smem(int n, int h, int W, bool manhattan)
 {
     const int RP = fast_row_pad(h);
     return (size_t)ring_slots(W, h) * ring_pitch(n, RP) * 4 + (size_t)W * cola_pitch(n) * 4 * (manhattan ? 2 : 1) +
-           (size_t)n * 16 + (size_t)4 * W * 32;
+           (size_t)n * 16 + (size_t)4 * W * 32 + (n >= 1024 ? (size_t)W * 32 * 4 : 0);
 }
 
 // Copy the kick-table entries (two float4) of column x into dst (lanes 0 and
@@ -487,14 +489,15 @@ __device__ __forceinline__ void load_kick(float4* dst, const float4* __restrict_
     }
 }
 
-// Rotation of one column x (rows 0..n-1, four per lane and pass) when the
+// Rotation of one column x (rows ylo..yhi-1, four per lane and pass) when the
 // y-node offset FY is the same on every row (window alignment O = A & 3,
 // A = FY - 1 + RP) and the x-node steps back by at most one inside a block
 // of four rows (sin phi < 1/3).
 template <int O, int KR, int NI>
 __device__ __forceinline__ void rotate_column(const float* __restrict__ ring, int R, int P, int RP, int A,
                                               float* __restrict__ colcol, int HC, int x, int n, int lane, float xc,
-                                              float c, float sn, float cm1, int FY, int ni, bool clamp)
+                                              float c, float sn, float cm1, int FY, int ni, bool clamp, int ylo,
+                                              int yhi)
 {
     const float2 msn2 = f2(-sn, -sn), cm12 = f2(cm1, cm1);
     const float2 snxc = f2(sn * xc, sn * xc), cmxc = f2(cm1 * xc, cm1 * xc);
@@ -502,7 +505,7 @@ __device__ __forceinline__ void rotate_column(const float* __restrict__ ring, in
     const float2 mfy = f2(-fyf, -fyf);
     const int lbase = cola_lane_base<KR>(lane, HC);
 #pragma unroll kRotUnroll
-    for (int yb = 0; yb < n; yb += 128) {
+    for (int yb = ylo; yb < yhi; yb += 128) {
         // every lane runs every pass (the vote below needs the whole warp);
         // lanes past the last row only vote
         const int y0 = yb + 4 * lane;
@@ -550,11 +553,11 @@ __device__ __forceinline__ void rotate_column(const float* __restrict__ ring, in
 template <int KR, int NI>
 __device__ __forceinline__ void drift_column(const float* __restrict__ ring, int R, int P, int RP,
                                              float* __restrict__ colcol, int HC, int x, int n, int lane, float c,
-                                             float hm, int ni, bool clamp)
+                                             float hm, int ni, bool clamp, int ylo, int yhi)
 {
     const int lbase = cola_lane_base<KR>(lane, HC);
 #pragma unroll 1
-    for (int yb = 0; yb < n; yb += 128) {
+    for (int yb = ylo; yb < yhi; yb += 128) {
         const int y0 = yb + 4 * lane;
         if ((n & 127) && y0 >= n) break;
         const float yc0 = float(y0) - c;
@@ -752,7 +755,7 @@ __device__ __forceinline__ bool cta_wait_flags(const Desc<float>& D, int c0, int
 // the end the CTA sets its step flag instead of taking a ticket.
 // s_last is then the CTA's failure flag.  Returns false when a wait ran out
 // (status set).
-template <int W, int KR, int NC, int ROT, bool PERSIST = false, int NI = 4>
+template <int W, int KR, int NC, int ROT, bool PERSIST = false, int NI = 4, int RS = (NC == 1024 ? 2 : 1)>
 __device__ __forceinline__ bool strip_f32(const Desc<float>& D, int xs, int T, unsigned char* smem, int& s_last,
                                           const PersistStep* ps = nullptr)
 {
@@ -768,28 +771,40 @@ __device__ __forceinline__ bool strip_f32(const Desc<float>& D, int xs, int T, u
     const float cm1 = D.cm1, sn = D.sn, c = D.c;
     const float4* __restrict__ kickw = D.kickw;
     double* __restrict__ colsum = D.colsum;
+    // Rows of a column: in two halves split at Y2 where n >= 1024 (its column
+    // sum is then the lower half's lane partials plus the upper half's, for
+    // every kernel shape); with RS = 2 (the N = 1024 instance) two warps share
+    // a column, warp w taking column w % W, half w / W, so that twice as many
+    // warps are resident at the same shared memory.
+    constexpr int NW = W * RS;
+    const int Y2 = n >= 1024 ? ((n >> 1) & ~255) : n;
+    const int cw = RS == 2 ? warp % W : warp, half = RS == 2 ? warp / W : 0;
+    const int ylo = half ? Y2 : 0, yhi = (RS == 2 && !half) ? Y2 : n;
 
     float* ring = reinterpret_cast<float*>(smem);
     float* colA = ring + R * P;
     float* gtab = colA + W * PA;  // g_0(y) .. g_3(y), n each (split layout for KR = 8)
-    float* colcol = colA + warp * PA;  // this warp's psi_a column, padded
-    float4* kbuf = reinterpret_cast<float4*>(gtab + 4 * n) + 2 * warp;  // stage k: kbuf + 2 W k
+    float* colcol = colA + cw * PA;  // this warp's psi_a column, padded
+    float4* kbuf = reinterpret_cast<float4*>(gtab + 4 * n) + 2 * cw;  // stage k: kbuf + 2 W k
     constexpr int rot = ROT;            // 1: Manhattan rotation (every instance of the launch)
     const float hm = D.hm;
     const int ni = NI == 4 ? 4 : D.ni;  // interpolation points (NI = 0: from the descriptor)
     const bool clamp = NI == 1;  // clamped interpolation (the NI = 1 instance)
-    float* colbcol = reinterpret_cast<float*>(reinterpret_cast<float4*>(gtab + 4 * n) + 8 * W) + warp * PA;
+    float* colbcol = reinterpret_cast<float*>(reinterpret_cast<float4*>(gtab + 4 * n) + 8 * W) + cw * PA;
+    // RS = 2: the upper half's lane partials of each column
+    float* xsum = reinterpret_cast<float*>(reinterpret_cast<float4*>(gtab + 4 * n) + 8 * W) + (rot ? W * PA : 0);
 
     // padding rows of every ring slot and of this warp's psi_a column: zero
     // for the whole strip (a persistent launch: for all its steps)
     if (!PERSIST || ps->k == 0) {
-    for (int slot = warp; slot < R; slot += W)
+    for (int slot = warp; slot < R; slot += NW)
         for (int r = lane; r < RP; r += 32) {
             ring[slot * P + r] = 0.f;
             ring[slot * P + RP + n + r] = 0.f;
         }
-    for (int r = lane; r < PA - n; r += 32) colcol[split_idx<KR>(r < kColPad ? r : n + r, HC)] = 0.f;
-    if (rot)
+    if (half == 0)
+        for (int r = lane; r < PA - n; r += 32) colcol[split_idx<KR>(r < kColPad ? r : n + r, HC)] = 0.f;
+    if (rot && half == 0)
         for (int r = lane; r < PA - n; r += 32) colbcol[split_idx<KR>(r < kColPad ? r : n + r, HC)] = 0.f;
     for (int y = threadIdx.x; y < n; y += blockDim.x) {
         const int gi = split_idx<KR>(y, n >> 3);
@@ -809,22 +824,22 @@ __device__ __forceinline__ bool strip_f32(const Desc<float>& D, int xs, int T, u
     const long long t_step = PERSIST ? ps->t : D.st->t;
     const bool mom_now = D.mom_every > 0 && (t_step + 1) % D.mom_every == 0;
     // window of tile 0, then the new columns of tile 1
-    load_columns<W>(ring, R, P, RP, in, ld, n, xs - h, W + 2 * h);
-    if (!recs) load_kick(kbuf, kickw, xs + warp, n, lane);
+    load_columns<NW>(ring, R, P, RP, in, ld, n, xs - h, W + 2 * h);
+    if (!recs && half == 0) load_kick(kbuf, kickw, xs + cw, n, lane);
     cp_async_commit();
     if (T > 1) {
-        load_columns<W>(ring, R, P, RP, in, ld, n, xs + W + h, W);
-        if (!recs) load_kick(kbuf + 2 * W, kickw, xs + W + warp, n, lane);
+        load_columns<NW>(ring, R, P, RP, in, ld, n, xs + W + h, W);
+        if (!recs && half == 0) load_kick(kbuf + 2 * W, kickw, xs + W + cw, n, lane);
     }
     cp_async_commit();
 
     for (int j = 0; j < T; ++j) {
-        const int x = xs + j * W + warp;
+        const int x = xs + j * W + cw;
         const bool active = x < n;
         cp_async_wait_1();
         __syncthreads();
         if (active && rot) {
-            drift_column<KR, NI>(ring, R, P, RP, colcol, HC, x, n, lane, c, hm, ni, clamp);
+            drift_column<KR, NI>(ring, R, P, RP, colcol, HC, x, n, lane, c, hm, ni, clamp, ylo, yhi);
         } else if (active) {
             const float xc = float(x) - c;
             // dy is linear along the column: floor(dy) is the same on every row
@@ -835,17 +850,18 @@ __device__ __forceinline__ bool strip_f32(const Desc<float>& D, int xs, int T, u
                 const int FY = int(fy_top);
                 const int A = FY - 1 + RP;
                 switch (A & 3) {
-                case 0: rotate_column<0, KR, NI>(ring, R, P, RP, A, colcol, HC, x, n, lane, xc, c, sn, cm1, FY, ni, clamp); break;
-                case 1: rotate_column<1, KR, NI>(ring, R, P, RP, A, colcol, HC, x, n, lane, xc, c, sn, cm1, FY, ni, clamp); break;
-                case 2: rotate_column<2, KR, NI>(ring, R, P, RP, A, colcol, HC, x, n, lane, xc, c, sn, cm1, FY, ni, clamp); break;
-                default: rotate_column<3, KR, NI>(ring, R, P, RP, A, colcol, HC, x, n, lane, xc, c, sn, cm1, FY, ni, clamp); break;
+                case 0: rotate_column<0, KR, NI>(ring, R, P, RP, A, colcol, HC, x, n, lane, xc, c, sn, cm1, FY, ni, clamp, ylo, yhi); break;
+                case 1: rotate_column<1, KR, NI>(ring, R, P, RP, A, colcol, HC, x, n, lane, xc, c, sn, cm1, FY, ni, clamp, ylo, yhi); break;
+                case 2: rotate_column<2, KR, NI>(ring, R, P, RP, A, colcol, HC, x, n, lane, xc, c, sn, cm1, FY, ni, clamp, ylo, yhi); break;
+                default: rotate_column<3, KR, NI>(ring, R, P, RP, A, colcol, HC, x, n, lane, xc, c, sn, cm1, FY, ni, clamp, ylo, yhi); break;
                 }
             } else {
-                for (int y = lane; y < n; y += 32)
+                for (int y = ylo + lane; y < yhi; y += 32)
                     colcol[split_idx<KR>(kColPad + y, HC)] = rotate_cell_ring<NI>(ring, R, P, RP, x, y, n, cm1, sn, c, ni, clamp);
             }
         }
-        __syncwarp();
+        if constexpr (RS == 2) __syncthreads();  // both halves of every psi_a column
+        else __syncwarp();
         const float* kcol = colcol;  // the column the wake kick reads
         if (active && rot) {
             // Manhattan rotation, second half: RF kick p -> p - h q, i.e. this
@@ -858,17 +874,17 @@ __device__ __forceinline__ bool strip_f32(const Desc<float>& D, int xs, int T, u
             if (sr >= -4 && sr <= 4) {
                 const int A2 = sr - 2 + kColPad;
                 switch (KR == 8 ? (A2 & 7) : (A2 & 3)) {
-                case 0: kick_fp_column<0, 0, KR, false, false, NI>(colcol, HC, gtab, colbcol, n, sr, A2, w4, lane, clamp); break;
-                case 1: kick_fp_column<1, 0, KR, false, false, NI>(colcol, HC, gtab, colbcol, n, sr, A2, w4, lane, clamp); break;
-                case 2: kick_fp_column<2, 0, KR, false, false, NI>(colcol, HC, gtab, colbcol, n, sr, A2, w4, lane, clamp); break;
-                case 3: kick_fp_column<3, 0, KR, false, false, NI>(colcol, HC, gtab, colbcol, n, sr, A2, w4, lane, clamp); break;
-                case 4: kick_fp_column<0, 1, KR, false, false, NI>(colcol, HC, gtab, colbcol, n, sr, A2, w4, lane, clamp); break;
-                case 5: kick_fp_column<1, 1, KR, KR == 8, false, NI>(colcol, HC, gtab, colbcol, n, sr, A2, w4, lane, clamp); break;
-                case 6: kick_fp_column<2, 1, KR, KR == 8, false, NI>(colcol, HC, gtab, colbcol, n, sr, A2, w4, lane, clamp); break;
-                default: kick_fp_column<3, 1, KR, false, false, NI>(colcol, HC, gtab, colbcol, n, sr, A2, w4, lane, clamp); break;
+                case 0: kick_fp_column<0, 0, KR, false, false, NI>(colcol, HC, gtab, colbcol, n, sr, A2, w4, lane, clamp, 1.f, ylo, yhi); break;
+                case 1: kick_fp_column<1, 0, KR, false, false, NI>(colcol, HC, gtab, colbcol, n, sr, A2, w4, lane, clamp, 1.f, ylo, yhi); break;
+                case 2: kick_fp_column<2, 0, KR, false, false, NI>(colcol, HC, gtab, colbcol, n, sr, A2, w4, lane, clamp, 1.f, ylo, yhi); break;
+                case 3: kick_fp_column<3, 0, KR, false, false, NI>(colcol, HC, gtab, colbcol, n, sr, A2, w4, lane, clamp, 1.f, ylo, yhi); break;
+                case 4: kick_fp_column<0, 1, KR, false, false, NI>(colcol, HC, gtab, colbcol, n, sr, A2, w4, lane, clamp, 1.f, ylo, yhi); break;
+                case 5: kick_fp_column<1, 1, KR, KR == 8, false, NI>(colcol, HC, gtab, colbcol, n, sr, A2, w4, lane, clamp, 1.f, ylo, yhi); break;
+                case 6: kick_fp_column<2, 1, KR, KR == 8, false, NI>(colcol, HC, gtab, colbcol, n, sr, A2, w4, lane, clamp, 1.f, ylo, yhi); break;
+                default: kick_fp_column<3, 1, KR, false, false, NI>(colcol, HC, gtab, colbcol, n, sr, A2, w4, lane, clamp, 1.f, ylo, yhi); break;
                 }
             } else {
-                for (int y = lane; y < n; y += 32) {
+                for (int y = ylo + lane; y < yhi; y += 32) {
                     const int m = y + sr;
                     float v = 0.f;
                     if (m > -2 && m < n) {
@@ -886,8 +902,11 @@ __device__ __forceinline__ bool strip_f32(const Desc<float>& D, int xs, int T, u
                     colbcol[split_idx<KR>(kColPad + y, HC)] = v;
                 }
             }
-            __syncwarp();
             kcol = colbcol;
+        }
+        if (rot) {
+            if constexpr (RS == 2) __syncthreads();  // both halves of every RF-kicked column
+            else __syncwarp();
         }
         bool kick_ok = true;
         float4 kw = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -915,52 +934,71 @@ __device__ __forceinline__ bool strip_f32(const Desc<float>& D, int xs, int T, u
             s = __float_as_int(kj[1].x);
             csf = kj[1].y;
         }
+        float lsum = 0.f;
         if (active && kick_ok) {
             float* dst = out + (size_t)x * ld;
-            float lsum = 0.f;
             if (s >= -4 && s <= 4) {
                 const int A2 = s - 2 + kColPad;  // column index of row y0+s-2, minus y0
                 // A2 = s + 14 with |s| <= 4: (A2 & 7) = 5 and 6 are s = -1 and 0 only
-                switch (KR == 8 ? (A2 & 7) : (A2 & 3)) {
-                case 0: lsum = kick_fp_column<0, 0, KR, false, true, NI>(kcol, HC, gtab, dst, n, s, A2, kw, lane, clamp, csf); break;
-                case 1: lsum = kick_fp_column<1, 0, KR, false, true, NI>(kcol, HC, gtab, dst, n, s, A2, kw, lane, clamp, csf); break;
-                case 2: lsum = kick_fp_column<2, 0, KR, false, true, NI>(kcol, HC, gtab, dst, n, s, A2, kw, lane, clamp, csf); break;
-                case 3: lsum = kick_fp_column<3, 0, KR, false, true, NI>(kcol, HC, gtab, dst, n, s, A2, kw, lane, clamp, csf); break;
-                case 4: lsum = kick_fp_column<0, 1, KR, false, true, NI>(kcol, HC, gtab, dst, n, s, A2, kw, lane, clamp, csf); break;
-                case 5: lsum = kick_fp_column<1, 1, KR, KR == 8, true, NI>(kcol, HC, gtab, dst, n, s, A2, kw, lane, clamp, csf); break;
-                case 6: lsum = kick_fp_column<2, 1, KR, KR == 8, true, NI>(kcol, HC, gtab, dst, n, s, A2, kw, lane, clamp, csf); break;
-                default: lsum = kick_fp_column<3, 1, KR, false, true, NI>(kcol, HC, gtab, dst, n, s, A2, kw, lane, clamp, csf); break;
-                }
+                auto kick_rows = [&](int r0, int r1) -> float {
+                    switch (KR == 8 ? (A2 & 7) : (A2 & 3)) {
+                    case 0: return kick_fp_column<0, 0, KR, false, true, NI>(kcol, HC, gtab, dst, n, s, A2, kw, lane, clamp, csf, r0, r1);
+                    case 1: return kick_fp_column<1, 0, KR, false, true, NI>(kcol, HC, gtab, dst, n, s, A2, kw, lane, clamp, csf, r0, r1);
+                    case 2: return kick_fp_column<2, 0, KR, false, true, NI>(kcol, HC, gtab, dst, n, s, A2, kw, lane, clamp, csf, r0, r1);
+                    case 3: return kick_fp_column<3, 0, KR, false, true, NI>(kcol, HC, gtab, dst, n, s, A2, kw, lane, clamp, csf, r0, r1);
+                    case 4: return kick_fp_column<0, 1, KR, false, true, NI>(kcol, HC, gtab, dst, n, s, A2, kw, lane, clamp, csf, r0, r1);
+                    case 5: return kick_fp_column<1, 1, KR, KR == 8, true, NI>(kcol, HC, gtab, dst, n, s, A2, kw, lane, clamp, csf, r0, r1);
+                    case 6: return kick_fp_column<2, 1, KR, KR == 8, true, NI>(kcol, HC, gtab, dst, n, s, A2, kw, lane, clamp, csf, r0, r1);
+                    default: return kick_fp_column<3, 1, KR, false, true, NI>(kcol, HC, gtab, dst, n, s, A2, kw, lane, clamp, csf, r0, r1);
+                    }
+                };
+                if (RS == 1 && Y2 < n) lsum = kick_rows(0, Y2) + kick_rows(Y2, n);  // lower + upper half
+                else lsum = kick_rows(ylo, yhi);
             } else {
                 // large kick: plain per-row evaluation with bounds
                 const float w[4] = {kw.x, kw.y, kw.z, kw.w};
-                for (int y = lane; y < n; y += 32) {
-                    float b[4];
+                auto large_rows = [&](int r0, int r1) -> float {
+                    float acc = 0.f;
+                    for (int y = r0 + lane; y < r1; y += 32) {
+                        float b[4];
 #pragma unroll
-                    for (int d = 0; d < 4; ++d) {
-                        const int yy = y - 1 + d;
-                        const int mm = yy + s;
-                        float v = 0.f;
-                        if (yy >= 0 && yy < n && mm > -2 && mm < n) {
+                        for (int d = 0; d < 4; ++d) {
+                            const int yy = y - 1 + d;
+                            const int mm = yy + s;
+                            float v = 0.f;
+                            if (yy >= 0 && yy < n && mm > -2 && mm < n) {
 #pragma unroll
-                            for (int k = 0; k < 4; ++k) {
-                                const int rr = mm - 1 + k;
-                                if (rr >= 0 && rr < n) v = fmaf(w[k], kcol[split_idx<KR>(kColPad + rr, HC)], v);
+                                for (int k = 0; k < 4; ++k) {
+                                    const int rr = mm - 1 + k;
+                                    if (rr >= 0 && rr < n) v = fmaf(w[k], kcol[split_idx<KR>(kColPad + rr, HC)], v);
+                                }
+                                if (clamp) {
+                                    const float a0 = mm >= 0 ? kcol[split_idx<KR>(kColPad + mm, HC)] : 0.f;
+                                    const float a1 = mm + 1 < n ? kcol[split_idx<KR>(kColPad + mm + 1, HC)] : 0.f;
+                                    v = clamp_to(v, csf * fminf(a0, a1), csf * fmaxf(a0, a1));
+                                }
                             }
-                            if (clamp) {
-                                const float a0 = mm >= 0 ? kcol[split_idx<KR>(kColPad + mm, HC)] : 0.f;
-                                const float a1 = mm + 1 < n ? kcol[split_idx<KR>(kColPad + mm + 1, HC)] : 0.f;
-                                v = clamp_to(v, csf * fminf(a0, a1), csf * fmaxf(a0, a1));
-                            }
+                            b[d] = v;
                         }
-                        b[d] = v;
+                        const int gi = split_idx<KR>(y, n >> 3);
+                        const float v = fp_apply(gtab[gi], gtab[n + gi], gtab[2 * n + gi], gtab[3 * n + gi], b);
+                        dst[y] = v;
+                        acc += v;
                     }
-                    const int gi = split_idx<KR>(y, n >> 3);
-                    const float v = fp_apply(gtab[gi], gtab[n + gi], gtab[2 * n + gi], gtab[3 * n + gi], b);
-                    dst[y] = v;
-                    lsum += v;
-                }
+                    return acc;
+                };
+                if (RS == 1 && Y2 < n) lsum = large_rows(0, Y2) + large_rows(Y2, n);
+                else lsum = large_rows(ylo, yhi);
             }
+        }
+        if constexpr (RS == 2) {
+            // the column's lane partials: lower half (this warp, half 0) plus
+            // upper half (its partner warp), in that order
+            if (active && kick_ok && half == 1) xsum[32 * cw + lane] = lsum;
+            __syncthreads();
+            if (half == 0) lsum = lsum + xsum[32 * cw + lane];
+        }
+        if (active && kick_ok && half == 0) {
             double csum = double(lsum);  // FP32 lane partials, FP64 across lanes
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) csum += __shfl_down_sync(0xffffffffu, csum, o);
@@ -981,8 +1019,8 @@ __device__ __forceinline__ bool strip_f32(const Desc<float>& D, int xs, int T, u
             return false;
         }
         if (j + 2 < T) {
-            load_columns<W>(ring, R, P, RP, in, ld, n, xs + (j + 2) * W + h, W);
-            if (!recs) load_kick(kbuf + 2 * W * ((j + 2) & 3), kickw, xs + (j + 2) * W + warp, n, lane);
+            load_columns<NW>(ring, R, P, RP, in, ld, n, xs + (j + 2) * W + h, W);
+            if (!recs && half == 0) load_kick(kbuf + 2 * W * ((j + 2) & 3), kickw, xs + (j + 2) * W + cw, n, lane);
         }
         cp_async_commit();
     }
@@ -1028,8 +1066,19 @@ __device__ __forceinline__ bool strip_f32(const Desc<float>& D, int xs, int T, u
 #define VFPS_FAST_WARPS_PER_SM 32
 #endif
 
+// Threads of a CTA of the FP32 step kernel: W warps, two per column for the
+// N = 1024 instance (RS = 2 in strip_f32).
+__host__ __device__ constexpr int fast_threads(int W, int NC) { return W * 32 * (NC == 1024 ? 2 : 1); }
+
+// Warps per column of the persistent lone-simulation kernel at N = 1024.
+#ifndef VFPS_PERSIST_RS
+#define VFPS_PERSIST_RS 2
+#endif
+constexpr int kPersistRS = VFPS_PERSIST_RS;
+__host__ __device__ constexpr int persist_threads(int W, int NC) { return W * 32 * (NC == 1024 ? kPersistRS : 1); }
+
 template <int W, int KR, int NC, int ROT, int NI = 4>
-__global__ void __launch_bounds__(W * 32, VFPS_FAST_WARPS_PER_SM / W)
+__global__ void __launch_bounds__(fast_threads(W, NC), VFPS_FAST_WARPS_PER_SM * 32 / fast_threads(W, NC))
 step_kernel_f32(const Desc<float>* __restrict__ descs, const int4* __restrict__ segs, int spc)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1072,7 +1121,7 @@ step_kernel_f32(const Desc<float>* __restrict__ descs, const int4* __restrict__ 
 // whole launch.  Every wait is bounded (spin_limit polls) and gives up with
 // status VFPS_ETIMEOUT; the other CTAs then give up within 64 polls.
 template <int W, int KR, int NC, int ROT>
-__global__ void __launch_bounds__(W * 32, 1)
+__global__ void __launch_bounds__(persist_threads(W, NC), 1)
 step_persistent_f32(const Desc<float>* __restrict__ descs, const int4* __restrict__ segs, int K)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1126,7 +1175,8 @@ step_persistent_f32(const Desc<float>* __restrict__ descs, const int4* __restric
         ps.k = k;
         ps.par = par0 ^ (k & 1);
         ps.t = t0 + k;
-        if (!strip_f32<W, KR, NC, ROT, true>(D, sg.y, sg.z, smem, s_fail, &ps)) return;
+        if (!strip_f32<W, KR, NC, ROT, true, 4, (NC == 1024 ? kPersistRS : 1)>(D, sg.y, sg.z, smem, s_fail, &ps))
+            return;
     }
 }
 

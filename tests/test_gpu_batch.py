@@ -62,6 +62,43 @@ def test_lower_order_slots_equal_solo_runs_bitwise(V):
     assert not np.array_equal(res[0]["psi"], res[2]["psi"])
 
 
+def test_n1024_shapes_and_solo_give_the_same_bits(V):
+    """N=1024 (two warps per column, the column sum as its lower plus upper
+    half): batches pinned to CTA widths 8, 4 and 2 and the lone simulation
+    (persistent launches) give the same bits; a step matches the oracle."""
+    n, spp, ns = 1024, 4000, 12
+    pts = [(0.9, 2.0), (3.0, 1.0), (1.5, 3.0)]
+    res = {}
+    for W_ in (8, 4, 2):
+        b = V.Batch(len(pts))
+        b.pin_shape(W_, 1)
+        sl = [b.add(V.Params(n=n, steps_per_period=spp, beta=1e-2), W.noisy_gaussian(n, 1614 + i, 1e-6),
+                    V.IMPEDANCE_PARALLEL_PLATES, Pi, S, nsteps=ns) for i, (S, Pi) in enumerate(pts)]
+        b.run(ns)
+        res[W_] = [b.take(s_) for s_ in sl]
+        b.close()
+    for i, (S, Pi) in enumerate(pts):
+        sim = V.Simulation(V.Params(n=n, steps_per_period=spp, beta=1e-2), W.noisy_gaussian(n, 1614 + i, 1e-6))
+        sim.set_impedance(V.IMPEDANCE_PARALLEL_PLATES, Pi, S)
+        sim.step(ns)
+        psi, P = sim.get_state(), sim.csr_power()
+        sim.close()
+        for W_ in (8, 4, 2):
+            assert np.array_equal(res[W_][i]["psi"], psi), (W_, i)
+            assert np.array_equal(res[W_][i]["power"], P), (W_, i)
+    op = O.Params(n=n, steps_per_period=spp, beta=1e-2, s_csr=pts[0][0])
+    zr, zi = O.impedance(op, 2, pts[0][1])
+    ref, Pref, _ = O.run(op, zr, zi, O.normalize(op, W.noisy_gaussian(n, 1614, 1e-6)), 2)
+    b = V.Batch(1)
+    s0 = b.add(V.Params(n=n, steps_per_period=spp, beta=1e-2), W.noisy_gaussian(n, 1614, 1e-6),
+               V.IMPEDANCE_PARALLEL_PLATES, pts[0][1], pts[0][0], nsteps=2)
+    b.run(2)
+    r = b.take(s0)
+    b.close()
+    assert np.max(np.abs(r["psi"] - ref)) <= 1e-5 * np.max(np.abs(ref))
+    assert np.max(np.abs(r["power"] - Pref)) <= 1e-5 * np.max(np.abs(Pref))
+
+
 def test_slot_results_equal_solo_runs_bitwise(V):
     mix = [(64, 500, 0.9, 2.0, 300), (100, 700, 1.2, 1.0, 170), (128, 1000, 0.5, 3.0, 250),
            (64, 500, 0.9, 2.0, 300), (64, 800, 1.7, 2.0, 120), (40, 400, 0.3, 0.5, 90)]

@@ -15,12 +15,16 @@ seeded starts; these tests run the CUDA path through the C ABI and compare.
   bursting), Gaussian start, against the oracle's same 40 periods: the
   frequency of the slow bursting line (the strongest below 0.5 cycles per
   period in periods 20-40, ~0.075: a bursting period of ~13 T_s) within 2 %,
-  the mean CSR power over periods 10-40 within 2 %, and the median
-  fluctuation envelope over periods 20-40 within 10 %.  The run is chaotic
-  from period 2 on and not stationary, so a mean is a statistic only over a
-  window of at least two bursting cycles (periods 10-40: 2.2 cycles; over
-  periods 20-40, 1.5 cycles, the two sides sample different phases of the
-  cycle and differ by 12 %).
+  the median fluctuation envelope over periods 20-40 within 10 %, and the
+  mean CSR power over periods 10-40 within the resolution of that window.
+  The run is chaotic from period 2 on and still relaxing (its per-period
+  mean falls ~3 % per period), so two runs from the same start share the
+  trend but not the bursting fluctuations about it: from the oracle's own
+  per-period means (detrended in log, their spread and autocorrelation ->
+  effective independent periods) the window mean of one run is uncertain by
+  ~3 %, the difference of two runs by ~4 %, and the test allows two
+  standard deviations of that difference (c5_mean_tolerance, ~8 %).  A 2 %
+  bound on this window would test the draw, not the method.
 * C3: the 63-point threshold scan (N = 256, S_csr in linspace(0.2, 1.5, 21)
   x Pi in {1, 2, 3}, 1000 steps/period, 20 periods) in one batch, plus a
   duplicate point as an in-batch determinism probe: the threshold per Pi
@@ -58,6 +62,28 @@ def V():
 def golden(name):
     with open(os.path.join(GOLDEN, f"oracle_{name}.json")) as f:
         return json.load(f)
+
+
+def c5_mean_tolerance(period_means, lo=10, hi=40):
+    """Two standard deviations of the difference between the mean of periods
+    lo..hi-1 of two independent chaotic runs, from one run's per-period means:
+    fit the relaxation trend (linear in log), take the residuals' spread and
+    their effective number of independent periods (positive autocorrelation
+    lags), and scale by sqrt 2 for the difference of two runs."""
+    m = np.asarray(period_means, dtype=np.float64)[lo:hi]
+    t = np.arange(lo, hi, dtype=np.float64)
+    A = np.vstack([np.ones_like(t), t]).T
+    coef, *_ = np.linalg.lstsq(A, np.log(m), rcond=None)
+    r = np.log(m) - A @ coef
+    x = r - r.mean()
+    rho = 0.0
+    for k in range(1, len(x) - 1):
+        c = float(np.dot(x[:-k], x[k:]) / np.dot(x, x))
+        if c <= 0.0:
+            break
+        rho += c
+    neff = len(x) / (1.0 + 2.0 * rho)
+    return 2.0 * np.sqrt(2.0) * r.std() / np.sqrt(neff)
 
 
 def envelope(stats):
@@ -148,5 +174,7 @@ def test_c5_large_grid_statistics_match_oracle(V):
           f"bursting line {slow_gpu:.5f} vs {slow_ref:.5f} cycles/period")
     assert A.is_bursting(P, spp, first=20, last=40)
     assert abs(slow_gpu - slow_ref) <= 0.02 * slow_ref, (slow_gpu, slow_ref)
-    assert abs(mean_gpu - mean_ref) <= 0.02 * mean_ref, (mean_gpu, mean_ref)
+    tol = c5_mean_tolerance(ref[:, 0])
+    assert 0.05 < tol < 0.12, tol  # the oracle run's own resolution of this window (~8 %)
+    assert abs(mean_gpu - mean_ref) <= tol * mean_ref, (mean_gpu, mean_ref, tol)
     assert abs(env_gpu - env_ref) <= 0.1 * env_ref, (env_gpu, env_ref)
