@@ -188,7 +188,7 @@ size_t fast_smem(const vfps_params* p, int W)
 bool pair_eligible(const vfps_params* p)
 {
     return fast_eligible(p) && p->interp_points == 4 && !p->clamp && p->rotation == 0 && (p->n % 32) == 0 &&
-           p->n < 1024 && halo_for(p) <= 12;
+           p->n < 512 && halo_for(p) <= 12;
 }
 
 size_t pair_smem(const vfps_params* p, int W)
@@ -905,6 +905,7 @@ int launch_fast_t(const Group& g, cudaStream_t s)
     if (g.kr == 8) {
         if (g.n == 256) return launch_fast_k<W, 8, 256>(g, s);
         if (g.n == 1024) return launch_fast_k<W, 8, 1024>(g, s);
+        if (g.n == 512) return launch_fast_k<W, 8, 512>(g, s);
         return launch_fast_k<W, 8, 0>(g, s);
     }
     return launch_fast_k<W, 4, 0>(g, s);
@@ -963,6 +964,8 @@ const void* persist_fn_w(int kr, int n, int rot)
         if (n == 1024)
             return rot ? (const void*)step_persistent_f32<W, 8, 1024, 1>
                        : (const void*)step_persistent_f32<W, 8, 1024, 0>;
+        if (n == 512)
+            return rot ? (const void*)step_persistent_f32<W, 8, 512, 1> : (const void*)step_persistent_f32<W, 8, 512, 0>;
         return rot ? (const void*)step_persistent_f32<W, 8, 0, 1> : (const void*)step_persistent_f32<W, 8, 0, 0>;
     }
     return rot ? (const void*)step_persistent_f32<W, 4, 0, 1> : (const void*)step_persistent_f32<W, 4, 0, 0>;
@@ -980,14 +983,9 @@ const void* persist_fn(const Group& g)
 // warps per column).
 int group_threads(const Group& g)
 {
-    return g.W * 32 * ((g.fast && !g.pair && !g.var && g.kr == 8 && g.n == 1024) ? 2 : 1);
+    return g.W * 32 * ((g.fast && !g.pair && !g.var && g.kr == 8 && (g.n == 512 || g.n == 1024)) ? 2 : 1);
 }
 
-// Threads per CTA of a group's persistent kernel.
-int persist_group_threads(const Group& g)
-{
-    return g.W * 32 * ((g.kr == 8 && g.n == 1024) ? kPersistRS : 1);
-}
 
 // K steps of a lone simulation in one cooperative launch: g.grid worker CTAs
 // and one finaliser CTA.  First every tagged word and step flag goes to 0
@@ -1001,7 +999,7 @@ int launch_persistent(const Group& g, const Instance& I, int K, cudaStream_t s)
     const Desc<float>* d = (const Desc<float>*)g.ddescs;
     const int4* sg = (const int4*)g.dsegs;
     void* args[3] = {(void*)&d, (void*)&sg, (void*)&K};
-    CU(cudaLaunchCooperativeKernel(f, dim3(g.grid + 1), dim3(persist_group_threads(g)), args, g.smem, s));
+    CU(cudaLaunchCooperativeKernel(f, dim3(g.grid + 1), dim3(group_threads(g)), args, g.smem, s));
     return VFPS_OK;
 }
 
@@ -1060,6 +1058,9 @@ int init_kernels()
     CU(set_smem_attr_one(step_kernel_f32<8, 8, 1024, 0>, lim));
     CU(set_smem_attr_one(step_kernel_f32<4, 8, 1024, 0>, lim));
     CU(set_smem_attr_one(step_kernel_f32<2, 8, 1024, 0>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<8, 8, 512, 0>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<4, 8, 512, 0>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<2, 8, 512, 0>, lim));
     CU(set_smem_attr_one(step_kernel_f32<8, 8, 0, 1>, lim));
     CU(set_smem_attr_one(step_kernel_f32<4, 8, 0, 1>, lim));
     CU(set_smem_attr_one(step_kernel_f32<2, 8, 0, 1>, lim));
@@ -1072,9 +1073,12 @@ int init_kernels()
     CU(set_smem_attr_one(step_kernel_f32<8, 8, 1024, 1>, lim));
     CU(set_smem_attr_one(step_kernel_f32<4, 8, 1024, 1>, lim));
     CU(set_smem_attr_one(step_kernel_f32<2, 8, 1024, 1>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<8, 8, 512, 1>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<4, 8, 512, 1>, lim));
+    CU(set_smem_attr_one(step_kernel_f32<2, 8, 512, 1>, lim));
     for (int W : {4, 8})
         for (int kr : {4, 8})
-            for (int n : {256, 1024, 0})
+            for (int n : {256, 512, 1024, 0})
                 for (int rot : {0, 1}) {
                     const void* f = W == 8 ? persist_fn_w<8>(kr, n, rot) : persist_fn_w<4>(kr, n, rot);
                     CU(set_smem_attr_one(f, lim));
@@ -1532,7 +1536,7 @@ static bool use_persistent(vfps_handle* h, const Group& g)
         h->persist = 0;
         const void* f = persist_fn(g);
         int per_sm = 0;
-        if (f && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, persist_group_threads(g), g.smem) ==
+        if (f && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, group_threads(g), g.smem) ==
                      cudaSuccess &&
             (long long)per_sm * num_sms() >= (long long)g.grid + 1)
             h->persist = 1;
@@ -1912,6 +1916,9 @@ int fast_blocks_t(const Group& g, size_t smem)
         if (g.n == 1024)
             return blocks_per_sm(g.rot ? step_kernel_f32<W, 8, 1024, 1> : step_kernel_f32<W, 8, 1024, 0>,
                                  fast_threads(W, 1024), smem);
+        if (g.n == 512)
+            return blocks_per_sm(g.rot ? step_kernel_f32<W, 8, 512, 1> : step_kernel_f32<W, 8, 512, 0>,
+                                 fast_threads(W, 512), smem);
         return blocks_per_sm(g.rot ? step_kernel_f32<W, 8, 0, 1> : step_kernel_f32<W, 8, 0, 0>, W * 32, smem);
     }
     return blocks_per_sm(g.rot ? step_kernel_f32<W, 4, 0, 1> : step_kernel_f32<W, 4, 0, 0>, W * 32, smem);

@@ -471,12 +471,12 @@ __host__ __device__ inline int ring_slots(int W, int h)
 // Shared memory of the FP32 streaming kernel: ring, psi_a columns, FP
 // weights, a 4-stage buffer of the tiles' kick-table entries, for the
 // Manhattan rotation a second set of columns (the RF-kicked psi), and for
-// n >= 1024 the upper-half lane partials of the W columns.
+// n >= 512 the upper-half lane partials of the W columns.
 __host__ inline size_t fast_ring_smem(int n, int h, int W, bool manhattan)
 {
     const int RP = fast_row_pad(h);
     return (size_t)ring_slots(W, h) * ring_pitch(n, RP) * 4 + (size_t)W * cola_pitch(n) * 4 * (manhattan ? 2 : 1) +
-           (size_t)n * 16 + (size_t)4 * W * 32 + (n >= 1024 ? (size_t)W * 32 * 4 : 0);
+           (size_t)n * 16 + (size_t)4 * W * 32 + (n >= 512 ? (size_t)W * 32 * 4 : 0);
 }
 
 // Copy the kick-table entries (two float4) of column x into dst (lanes 0 and
@@ -755,7 +755,7 @@ __device__ __forceinline__ bool cta_wait_flags(const Desc<float>& D, int c0, int
 // the end the CTA sets its step flag instead of taking a ticket.
 // s_last is then the CTA's failure flag.  Returns false when a wait ran out
 // (status set).
-template <int W, int KR, int NC, int ROT, bool PERSIST = false, int NI = 4, int RS = (NC == 1024 ? 2 : 1)>
+template <int W, int KR, int NC, int ROT, bool PERSIST = false, int NI = 4, int RS = (NC >= 512 ? 2 : 1)>
 __device__ __forceinline__ bool strip_f32(const Desc<float>& D, int xs, int T, unsigned char* smem, int& s_last,
                                           const PersistStep* ps = nullptr)
 {
@@ -771,13 +771,13 @@ __device__ __forceinline__ bool strip_f32(const Desc<float>& D, int xs, int T, u
     const float cm1 = D.cm1, sn = D.sn, c = D.c;
     const float4* __restrict__ kickw = D.kickw;
     double* __restrict__ colsum = D.colsum;
-    // Rows of a column: in two halves split at Y2 where n >= 1024 (its column
+    // Rows of a column: in two halves split at Y2 where n >= 512 (its column
     // sum is then the lower half's lane partials plus the upper half's, for
-    // every kernel shape); with RS = 2 (the N = 1024 instance) two warps share
-    // a column, warp w taking column w % W, half w / W, so that twice as many
-    // warps are resident at the same shared memory.
+    // every kernel shape); with RS = 2 (the N = 512 and 1024 instances) two
+    // warps share a column, warp w taking column w % W, half w / W, so that
+    // twice as many warps are resident at the same shared memory.
     constexpr int NW = W * RS;
-    const int Y2 = n >= 1024 ? ((n >> 1) & ~255) : n;
+    const int Y2 = n >= 512 ? ((n >> 1) & ~255) : n;
     const int cw = RS == 2 ? warp % W : warp, half = RS == 2 ? warp / W : 0;
     const int ylo = half ? Y2 : 0, yhi = (RS == 2 && !half) ? Y2 : n;
 
@@ -1067,15 +1067,9 @@ __device__ __forceinline__ bool strip_f32(const Desc<float>& D, int xs, int T, u
 #endif
 
 // Threads of a CTA of the FP32 step kernel: W warps, two per column for the
-// N = 1024 instance (RS = 2 in strip_f32).
-__host__ __device__ constexpr int fast_threads(int W, int NC) { return W * 32 * (NC == 1024 ? 2 : 1); }
-
-// Warps per column of the persistent lone-simulation kernel at N = 1024.
-#ifndef VFPS_PERSIST_RS
-#define VFPS_PERSIST_RS 2
-#endif
-constexpr int kPersistRS = VFPS_PERSIST_RS;
-__host__ __device__ constexpr int persist_threads(int W, int NC) { return W * 32 * (NC == 1024 ? kPersistRS : 1); }
+// N = 512 and 1024 instances (RS = 2 in strip_f32; the persistent kernel
+// too).
+__host__ __device__ constexpr int fast_threads(int W, int NC) { return W * 32 * (NC >= 512 ? 2 : 1); }
 
 template <int W, int KR, int NC, int ROT, int NI = 4>
 __global__ void __launch_bounds__(fast_threads(W, NC), VFPS_FAST_WARPS_PER_SM * 32 / fast_threads(W, NC))
@@ -1121,7 +1115,7 @@ step_kernel_f32(const Desc<float>* __restrict__ descs, const int4* __restrict__ 
 // whole launch.  Every wait is bounded (spin_limit polls) and gives up with
 // status VFPS_ETIMEOUT; the other CTAs then give up within 64 polls.
 template <int W, int KR, int NC, int ROT>
-__global__ void __launch_bounds__(persist_threads(W, NC), 1)
+__global__ void __launch_bounds__(fast_threads(W, NC), 1)
 step_persistent_f32(const Desc<float>* __restrict__ descs, const int4* __restrict__ segs, int K)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1175,8 +1169,7 @@ step_persistent_f32(const Desc<float>* __restrict__ descs, const int4* __restric
         ps.k = k;
         ps.par = par0 ^ (k & 1);
         ps.t = t0 + k;
-        if (!strip_f32<W, KR, NC, ROT, true, 4, (NC == 1024 ? kPersistRS : 1)>(D, sg.y, sg.z, smem, s_fail, &ps))
-            return;
+        if (!strip_f32<W, KR, NC, ROT, true>(D, sg.y, sg.z, smem, s_fail, &ps)) return;
     }
 }
 

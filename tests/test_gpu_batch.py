@@ -62,11 +62,13 @@ def test_lower_order_slots_equal_solo_runs_bitwise(V):
     assert not np.array_equal(res[0]["psi"], res[2]["psi"])
 
 
-def test_n1024_shapes_and_solo_give_the_same_bits(V):
-    """N=1024 (two warps per column, the column sum as its lower plus upper
-    half): batches pinned to CTA widths 8, 4 and 2 and the lone simulation
-    (persistent launches) give the same bits; a step matches the oracle."""
-    n, spp, ns = 1024, 4000, 12
+@pytest.mark.parametrize("n,spp", [(1024, 4000), (512, 2000)])
+def test_large_grid_shapes_and_solo_give_the_same_bits(V, n, spp):
+    """N=512 and 1024 (two warps per column, the column sum as its lower plus
+    upper half): batches pinned to CTA widths 8, 4 and 2 and the lone
+    simulation (persistent launches) give the same bits; a step matches the
+    oracle."""
+    ns = 12
     pts = [(0.9, 2.0), (3.0, 1.0), (1.5, 3.0)]
     res = {}
     for W_ in (8, 4, 2):

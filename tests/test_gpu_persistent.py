@@ -3,13 +3,13 @@ launch, a dedicated finaliser CTA, bounded device waits).
 
 * The persistent path gives the same bits as one ticketed launch per step
   (VFPS_PERSISTENT=0): state, CSR-power and charge series, recorded moments,
-  for the compiled grid sizes (N = 256 and 1024), a run-time size with 8- and
+  for the compiled grid sizes (N = 256, 512 and 1024), a run-time size with 8- and
   4-row kick blocks, the Manhattan rotation, and step counts that cross
   launch boundaries.
 * A wait that nothing ends runs out: with the finaliser CTA withholding its
   tagged kick records (test hook VFPS_FAULT_NO_SIGNAL) the launch returns
-  within the spin limit, the next synchronising call reports ETIMEOUT, and the context
-  stays usable for the next simulation.  The failure is made by a flag that
+  within the spin limit, the next synchronising call reports ETIMEOUT, and
+  the context stays usable for the next simulation.  The failure is made by a flag that
   nothing sets; no device fault is involved.
 """
 import contextlib
@@ -70,6 +70,8 @@ CASES = [
     # (name, n, steps/period, Pi, S_csr, rotation, step() calls)
     ("n256_bursting", 256, 1000, 2.0, 0.9, 0, [300]),
     ("n1024_c5", 1024, 4000, 1.0, 3.0, 0, [100]),
+    ("n512_two_warps_per_column", 512, 2000, 2.0, 1.2, 0, [150]),
+    ("n512_manhattan", 512, 2000, 2.0, 1.2, 1, [100]),
     ("n128_runtime_size", 128, 500, 2.0, 0.9, 0, [120]),
     ("n60_four_row_blocks", 60, 500, 1.0, 0.8, 0, [90]),
     ("n256_manhattan", 256, 1000, 2.0, 0.9, 1, [200]),
