@@ -121,3 +121,33 @@ def test_bounded_wait_runs_out_with_etimeout(V):
     psi_b, P_b, _, _, _ = run(V, p, 2.0, 0.9, [40], False)
     assert mode_a
     assert np.array_equal(P_a, P_b) and np.array_equal(psi_a, psi_b)
+
+
+@pytest.mark.parametrize("n,spp,S,Pi", [(256, 1000, 0.9, 2.0), (1024, 4000, 3.0, 1.0)])
+def test_concurrent_persistent_simulations_keep_their_bits(V, n, spp, S, Pi):
+    """Two lone simulations stepping at once on their own streams (at N=1024
+    their two grids of one-per-SM CTAs cannot be resident together, so the
+    cooperative launches take turns): no wait runs out, and each ends with
+    the bits of its solo run."""
+    import torch
+
+    def make(stream, seed):
+        sim = V.Simulation(V.Params(n=n, steps_per_period=spp, beta=1e-2), W.noisy_gaussian(n, seed, 1e-6), stream)
+        sim.set_impedance(V.IMPEDANCE_PARALLEL_PLATES, Pi, S)
+        return sim
+
+    a, b = make(torch.cuda.Stream(), 1), make(torch.cuda.Stream(), 2)
+    try:
+        assert a.persistent and b.persistent
+        for _ in range(4):
+            a.step(300)
+            b.step(300)
+        got = [(a.get_state(), a.csr_power()), (b.get_state(), b.csr_power())]
+    finally:
+        a.close()
+        b.close()
+    for seed, (psi, P) in zip((1, 2), got):
+        sim = make(None, seed)
+        sim.step(1200)
+        assert np.array_equal(psi, sim.get_state()) and np.array_equal(P, sim.csr_power()), seed
+        sim.close()
