@@ -101,6 +101,28 @@ def test_large_grid_shapes_and_solo_give_the_same_bits(V, n, spp):
     assert np.max(np.abs(r["power"] - Pref)) <= 1e-5 * np.max(np.abs(Pref))
 
 
+def test_maximum_size_slots_equal_solo_runs(V):
+    """n = 2048 (the largest grid): batch slots pinned to CTA widths 4 and 2
+    equal the solo run bit for bit."""
+    n, spp, ns = 2048, 4000, 6
+    ref = None
+    sim = V.Simulation(V.Params(n=n, steps_per_period=spp, beta=1e-2), W.noisy_gaussian(n, 7, 1e-3))
+    sim.set_impedance(V.IMPEDANCE_PARALLEL_PLATES, 2.0, 1.5)
+    sim.step(ns)
+    ref = (sim.get_state(), sim.csr_power())
+    sim.close()
+    for W_ in (4, 2):
+        b = V.Batch(2)
+        b.pin_shape(W_, 1)
+        sl = [b.add(V.Params(n=n, steps_per_period=spp, beta=1e-2), W.noisy_gaussian(n, 7, 1e-3),
+                    V.IMPEDANCE_PARALLEL_PLATES, 2.0, 1.5, nsteps=ns) for _ in range(2)]
+        b.run(ns)
+        for s_ in sl:
+            r = b.take(s_)
+            assert np.array_equal(r["psi"], ref[0]) and np.array_equal(r["power"], ref[1]), W_
+        b.close()
+
+
 def test_slot_results_equal_solo_runs_bitwise(V):
     mix = [(64, 500, 0.9, 2.0, 300), (100, 700, 1.2, 1.0, 170), (128, 1000, 0.5, 3.0, 250),
            (64, 500, 0.9, 2.0, 300), (64, 800, 1.7, 2.0, 120), (40, 400, 0.3, 0.5, 90)]

@@ -183,6 +183,25 @@ def test_full_size_1024_sampled_rows(V):
     sim.close()
 
 
+def test_maximum_size_2048_two_steps(V):
+    """The largest grid the library takes (n = 2048, FFT length 4096): two steps
+    of a noisy Gaussian with the wake on, FP32 (run-time grid size, column
+    sums split into lower and upper rows) and FP64, against the oracle; the
+    CSR power of both steps too."""
+    n = 2048
+    psi0 = W.noisy_gaussian(n, 2048, 1e-3)
+    op = O.Params(n=n, steps_per_period=4000, beta=1e-2, s_csr=1.5)
+    zr, zi = O.impedance(op, 2, 2.0)
+    ref, Pref, _ = O.run(op, zr, zi, O.normalize(op, psi0), 2)
+    for precision, tol in ((0, 1e-5), (1, 1e-11)):
+        sim, _, _, _ = make(V, n, precision, spp=4000, beta=1e-2, model=2, Pi=2.0, S=1.5, psi=psi0)
+        sim.step(2)
+        assert rel_linf(sim.get_state(), ref) < tol, precision
+        P = sim.csr_power()
+        assert P.shape == (2,) and np.max(np.abs(P - Pref)) <= 10 * tol * np.max(np.abs(Pref)), (P, Pref)
+        sim.close()
+
+
 def test_state_roundtrip_and_counters(V):
     n = 40
     psi0 = W.blobs(n, 9)
