@@ -1143,19 +1143,28 @@ step_persistent_f32(const Desc<float>* __restrict__ descs, const int4* __restric
         for (int k = 0; k < K; ++k) {
             if (threadIdx.x == 0) s_fail = 0;
             __syncthreads();
-            for (int x = threadIdx.x; x < n; x += blockDim.x) {
+            // the column sums as they arrive, and the transform input from them
+            // (FP32 z_j = cs_2j + i cs_2j+1, zero-padded to M/2 values)
+            float* z = reinterpret_cast<float*>(L.bufB);
+            for (int x = threadIdx.x; x < D.M; x += blockDim.x) {
+                if (x >= n) {
+                    z[x] = 0.f;
+                    continue;
+                }
                 unsigned v[2];
                 if (!wait_tagged<2>(D, D.cword + 2 * (size_t)x, (unsigned)k + 1u, v)) {
                     s_fail = 1;
                     break;
                 }
-                L.cs[x] = __longlong_as_double((long long)(((unsigned long long)v[1] << 32) | v[0]));
+                const double c = __longlong_as_double((long long)(((unsigned long long)v[1] << 32) | v[0]));
+                L.cs[x] = c;
+                z[x] = float(c);
             }
             __syncthreads();
             if (s_fail) return;
             const bool mom_now = D.mom_every > 0 && D.mring && (t0 + k + 1) % D.mom_every == 0;
             if (mom_now && !cta_wait_flags(D, 0, nwork - 1, (unsigned)k + 1u, &s_flag)) return;
-            finalise_compute<float>(D, smem, 1, D.fault_no_signal ? 0u : (unsigned)(k + 1), nwork);
+            finalise_compute<float>(D, smem, 1, D.fault_no_signal ? 0u : (unsigned)(k + 1), nwork, true, k == K - 1);
         }
         return;
     }

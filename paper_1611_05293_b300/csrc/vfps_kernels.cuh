@@ -276,15 +276,31 @@ __device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_
 __device__ __forceinline__ void cp_async_wait_0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // Sum of v[0..count) in an order fixed by count alone (not by the block
-// size, so a simulation gives the same bits whatever CTA width runs it):
-// lane l adds v[l], v[l+32], ... in order, then a shuffle tree.  Called by
+// size, so a simulation gives the same bits whatever CTA width runs it): in
+// blocks of 256 values, lane l takes v[l + 32 i], i = 0..7 (zeros past
+// count) and adds them pairwise, ((0 + 1) + (2 + 3)) + ((4 + 5) + (6 + 7)),
+// the blocks' lane values are added in order, then a shuffle tree.  Terms
+// that are zero for every lane are left out (adding +0 changes no value), so
+// a block takes 3 + 5 dependent adds at most, against up to 13 for a
+// lane-sequential sum: FP64 adds have a long latency on this GPU.  Called by
 // one whole warp; v is in shared memory and complete; lane 0 has the sum.
 template <typename T>
 __device__ __forceinline__ T warp_fixed_sum(const T* v, int count)
 {
     const int lane = threadIdx.x & 31;
     T acc = T(0);
-    for (int i = lane; i < count; i += 32) acc += v[i];
+    for (int b = 0; b < count; b += 256) {
+        const int rem = count - b;
+        T a[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) a[i] = (lane + 32 * i < rem) ? v[b + lane + 32 * i] : T(0);
+        T t;
+        if (rem > 128) t = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+        else if (rem > 64) t = (a[0] + a[1]) + (a[2] + a[3]);
+        else if (rem > 32) t = a[0] + a[1];
+        else t = a[0];
+        acc = b ? acc + t : t;
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     return acc;
@@ -594,7 +610,7 @@ __device__ __forceinline__ void wake_pair_pass(typename C2<T>::type* Z, const ty
 // Moment sums of a recording step, on the finaliser's FP64 sum warp beside
 // the forward transform: red[2..5] = sum q cs, sum q^2 cs (from the column
 // sums cs in shared memory), sum of the per-column p psi and p^2 psi sums the
-// step kernel wrote (colmom); each in the fixed order of warp_fixed_sum.
+// step kernel wrote (colmom); each lane-sequential, then a shuffle tree.
 __device__ __forceinline__ void moment_sums_warp(const double* cs, const double* colmom, int n, double delta,
                                                  double* red)
 {
@@ -674,10 +690,13 @@ __device__ __forceinline__ void finalise_load(const Desc<T>& D, unsigned char* s
 // in shared memory.  gen > 0 (persistent launches): also the kick records of
 // the launch's step gen, tagged words D.rword[x] = (kick of column x, gen)
 // and D.sword[b] = (pending scale, gen) for each worker CTA b < nscale,
-// written before the rest of the table.
+// written before the rest of the table.  prepped: the caller has already
+// written the transform input (zero-padded FP32 column sums) and synchronised.
+// table = false leaves the kick table, the kicks and rho unwritten (a
+// persistent launch's steps before its last, whose workers take the records).
 template <typename T>
 __device__ void finalise_compute(const Desc<T>& D, unsigned char* smem, int is_step, unsigned gen = 0,
-                                 int nscale = 0)
+                                 int nscale = 0, bool prepped = false, bool table = true)
 {
     using T2 = typename C2<T>::type;
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -696,42 +715,54 @@ __device__ void finalise_compute(const Desc<T>& D, unsigned char* smem, int is_s
     // 0 only advances it after the last barrier)
     const long long t_now = D.st->t;
     // transform input z_j = cs_2j + i cs_2j+1 (zero-padded), in T
-    for (int j = tid; j < H; j += nt) {
-        const int x = 2 * j;
-        bufB[j] = T2{x < n ? T(cs[x]) : T(0), x + 1 < n ? T(cs[x + 1]) : T(0)};
+    if (!prepped) {
+        for (int j = tid; j < H; j += nt) {
+            const int x = 2 * j;
+            bufB[j] = T2{x < n ? T(cs[x]) : T(0), x + 1 < n ? T(cs[x + 1]) : T(0)};
+        }
+        __syncthreads();
     }
-    __syncthreads();
 
-    // forward transform on the first warps while the last nsum warps sum the
-    // charge Q = Delta^2 sum cs in FP64 (FP64 adds are slow on the B300: a
-    // sum takes longer than a transform pass, so it runs beside the whole
-    // transform rather than inside one pass; a one-warp block runs the two in
-    // turn).  Each FP64 sum has a structure fixed by its length alone: groups
-    // of 256 consecutive values, each summed in the order of warp_fixed_sum,
-    // then the group sums added in order -- the sum warps take the groups in
-    // turn, so the bits do not depend on how many there are.
+    // Roles: the first warps (F) run the transforms, the wake pass and the
+    // kick table; the last nsum warps (S) form the FP64 sums -- the charge,
+    // then the power terms -- and the pending scale.  Each FP64 sum has a
+    // structure fixed by its length alone: groups of 256 consecutive values,
+    // each summed as warp_fixed_sum sums, then the group sums added in order;
+    // the sum warps take the groups in turn, so the bits do not depend on how
+    // many there are (nor on the CTA width).  FP64 arithmetic has a long
+    // latency on this GPU, so in FP32 nothing of it lies on F's path: the
+    // spectrum factor sk = 1/c (c = sum of the column sums, Delta^2 c = Q)
+    // is the FP32 reciprocal of the forward transform's own DC bin, and F
+    // waits for S only for the pending scale, after the inverse transform;
+    // S's power sum ends beside the kick table.  (FP64: sk comes from the
+    // FP64 scale, so F waits for it before the wake pass.)  A one-warp block
+    // plays both roles in turn.  Named barriers: 1 among F, 2 among S, 3
+    // (F arrives, S waits) wake pass done, 4 (S arrives, F waits) scale ready.
+    constexpr bool f32 = sizeof(T) == 4;
     const int nw = nt >> 5, wid = tid >> 5;
     const int Gc = sum_groups(n), Gp = sum_groups(H / 2 + 1);
     const int nsum = nw == 1 ? 1 : max(1, min(max(Gc, Gp), nw / 2));
     const int sw = nw == 1 ? 0 : wid - (nw - nsum);  // index among the sum warps, < 0 for the others
-    const bool sum_thread = sw >= 0, fft_thread = nw == 1 || sw < 0;
-    const int nfft = nw == 1 ? nt : nt - 32 * nsum;
+    const bool solo = nw == 1;
+    const bool sum_thread = sw >= 0, fft_thread = solo || sw < 0;
+    const int nF = solo ? nt : nt - 32 * nsum, nFS = nt;
     double* gsum_c = red + 12;      // Gc group sums of the charge
     double* gsum_p = gsum_c + Gc;   // Gp group sums of the power terms
-    T2* Z = fft_result<T2>(bufB, bufA, bufB, H);
-    if (fft_thread) fft_h_part<T, false>(bufB, bufA, bufB, tw, H, nfft);
-    // (a moment-recording step also forms the moment sums there)
+    float* skp = reinterpret_cast<float*>(red + 11);
     const bool mom_now = is_step && D.mom_every > 0 && D.mring && (t_now + 1) % D.mom_every == 0;
-    if (sum_thread) {
+    T2* Z = fft_result<T2>(bufB, bufA, bufB, H);
+    T2* const Zo = Z == bufA ? bufB : bufA;
+    T2* y = fft_result<T2>(Z, Zo, Z, H);
+
+    // S: the charge, the pending scale and profile factor (and, on a
+    // recording step, the moment sums)
+    auto charge_and_scale = [&]() {
         for (int g = sw; g < Gc; g += nsum) {
             const double sum = warp_fixed_sum<double>(cs + 256 * g, min(256, n - 256 * g));
             if ((tid & 31) == 0) gsum_c[g] = sum;
         }
         if (nsum > 1) asm volatile("bar.sync 2, %0;" ::"r"(32 * nsum) : "memory");
         if (tid == 32 * (nw - nsum)) {
-            // the charge, pending scale and profile factors, once, on the
-            // first sum warp while the transform runs (an FP64 division takes
-            // long on this GPU; every thread reads the results after the barrier)
             double c = gsum_c[0];
             for (int g = 1; g < Gc; ++g) c += gsum_c[g];
             const double q = D.delta * D.delta * c;
@@ -743,52 +774,80 @@ __device__ void finalise_compute(const Desc<T>& D, unsigned char* smem, int is_s
             red[10] = s1 * D.delta;
         }
         if (mom_now && sw == 0) moment_sums_warp(cs, D.colmom, n, D.delta, red);
-    }
-    __syncthreads();
-    const double csum = red[0];
-    const double Q = red[8];
-    const bool bad = !(Q > 0.0) || !isfinite(Q);
-    const double s_new = red[9];
-    const double sd = red[10];                // rho_x = sd * cs_x
-    const T sk = T(sd * D.delta);             // rho~_k = Delta * DFT(rho)_k = sk * X_k
-
-    wake_pair_pass<T>(Z, tw, zh, H, sk, pterm, tid, nt);
-    __syncthreads();
-
-    // inverse transform likewise, beside the FP64 sum of the power terms
-    T2* const Zo = Z == bufA ? bufB : bufA;
-    T2* y = fft_result<T2>(Z, Zo, Z, H);
-    if (fft_thread) fft_h_part<T, true>(Z, Zo, Z, tw, H, nfft);
-    if (sum_thread) {
+    };
+    // S: the power terms
+    auto power_sum = [&]() {
         for (int g = sw; g < Gp; g += nsum) {
             const double sum = warp_fixed_sum<double>(pterm + 256 * g, min(256, H / 2 + 1 - 256 * g));
             if ((tid & 31) == 0) gsum_p[g] = sum;
         }
+    };
+
+    if (solo) {
+        fft_h_part<T, false>(bufB, bufA, bufB, tw, H, nt);
+        charge_and_scale();
+        __syncwarp();
+    } else if (sum_thread) {
+        charge_and_scale();
+        asm volatile("bar.arrive 4, %0;" ::"r"(nFS) : "memory");
+        asm volatile("bar.sync 3, %0;" ::"r"(nFS) : "memory");
+        power_sum();
+    }
+    if (fft_thread) {
+        if (!solo) fft_h_part<T, false>(bufB, bufA, bufB, tw, H, nF);
+        T sk;
+        if constexpr (f32) {
+            // 1/c from the DC bin (the sums of the even and odd column sums)
+            if (tid == 0) {
+                const float c = Z[0].x + Z[0].y;
+                skp[0] = (D.renorm && c > 0.f && isfinite(c)) ? __frcp_rn(c) : float(D.delta * D.delta);
+            }
+            asm volatile("bar.sync 1, %0;" ::"r"(nF) : "memory");
+            sk = skp[0];
+        } else {
+            if (!solo) asm volatile("bar.sync 4, %0;" ::"r"(nFS) : "memory");
+            sk = T(red[10] * D.delta);  // rho~_k = Delta * DFT(rho)_k = sk * X_k
+        }
+        wake_pair_pass<T>(Z, tw, zh, H, sk, pterm, tid, nF);
+        asm volatile("bar.sync 1, %0;" ::"r"(nF) : "memory");
+        if (!solo) asm volatile("bar.arrive 3, %0;" ::"r"(nFS) : "memory");
+        fft_h_part<T, true>(Z, Zo, Z, tw, H, nF);
+        if (solo) power_sum();
+        else if (f32) asm volatile("bar.sync 4, %0;" ::"r"(nFS) : "memory");
+
+        // the kick table (and, in persistent launches, the tagged records
+        // first) on F, from the inverse transform and the pending scale
+        const double s_new = red[9];
+        const double sd = red[10];  // rho_x = sd * cs_x
+        const T kpv = T(D.kick_per_v * D.dkappa);
+        if constexpr (f32) {
+            if (gen) {
+                for (int x = tid; x < n; x += nF) {
+                    const T2 v = y[x >> 1];
+                    st_tagged(D.rword + x, __float_as_uint(kpv * ((x & 1) ? v.y : v.x)), gen);
+                }
+                const unsigned sfb = __float_as_uint(float(s_new));
+                for (int b = tid; b < nscale; b += nF) st_tagged(D.sword + b, sfb, gen);
+            }
+        }
+        for (int x = tid; table && x < n; x += nF) {
+            const T2 v = y[x >> 1];
+            const T k = kpv * ((x & 1) ? v.y : v.x);
+            D.kick[x] = k;
+            D.rho[x] = sd * cs[x];
+            if constexpr (f32) {
+                const KickEntry e = kick_entry(k, float(s_new), D.ni);
+                D.kickw[2 * x] = e.w;
+                D.kickw[2 * x + 1] = make_float4(__int_as_float(e.s), float(s_new), 0.f, 0.f);
+            }
+        }
     }
     __syncthreads();
-    const T kpv = T(D.kick_per_v * D.dkappa);
-    if constexpr (sizeof(T) == 4) {
-        if (gen) {
-            for (int x = tid; x < n; x += nt) {
-                const T2 v = y[x >> 1];
-                st_tagged(D.rword + x, __float_as_uint(kpv * ((x & 1) ? v.y : v.x)), gen);
-            }
-            const unsigned sfb = __float_as_uint(float(s_new));
-            for (int b = tid; b < nscale; b += nt) st_tagged(D.sword + b, sfb, gen);
-        }
-    }
-    for (int x = tid; x < n; x += nt) {
-        const T2 v = y[x >> 1];
-        const T k = kpv * ((x & 1) ? v.y : v.x);
-        D.kick[x] = k;
-        D.rho[x] = sd * cs[x];
-        if constexpr (sizeof(T) == 4) {
-            const KickEntry e = kick_entry(k, float(s_new), D.ni);
-            D.kickw[2 * x] = e.w;
-            D.kickw[2 * x + 1] = make_float4(__int_as_float(e.s), float(s_new), 0.f, 0.f);
-        }
-    }
     if (tid == 0) {
+        const double csum = red[0];
+        const double Q = red[8];
+        const bool bad = !(Q > 0.0) || !isfinite(Q);
+        const double s_new = red[9];
         double psum = gsum_p[0];
         for (int g = 1; g < Gp; ++g) psum += gsum_p[g];
         const double P = D.dkappa * psum;

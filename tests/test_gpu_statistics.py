@@ -11,20 +11,18 @@ seeded starts; these tests run the CUDA path through the C ABI and compare.
 * C2: one N = 256 simulation, 1000 steps/period, 50 periods, Pi = 2,
   S_csr = 0.9 (above the ~0.74 threshold): mean CSR power over the second
   half and the frequency of its strongest line within 2 %.
-* C5: one N = 1024 simulation, 4000 steps/period, Pi = 1, S_csr = 3 (deep
-  bursting), Gaussian start, against the oracle's same 40 periods: the
-  frequency of the slow bursting line (the strongest below 0.5 cycles per
-  period in periods 20-40, ~0.075: a bursting period of ~13 T_s) within 2 %,
-  the median fluctuation envelope over periods 20-40 within 10 %, and the
-  mean CSR power over periods 10-40 within the resolution of that window.
-  The run is chaotic from period 2 on and still relaxing (its per-period
-  mean falls ~3 % per period), so two runs from the same start share the
-  trend but not the bursting fluctuations about it: from the oracle's own
-  per-period means (detrended in log, their spread and autocorrelation ->
-  effective independent periods) the window mean of one run is uncertain by
-  ~3 %, the difference of two runs by ~4 %, and the test allows two
-  standard deviations of that difference (c5_mean_tolerance, ~8 %).  A 2 %
-  bound on this window would test the draw, not the method.
+* C5: N = 1024, 4000 steps/period, Pi = 1, S_csr = 3 (deep bursting),
+  Gaussian start, against the oracle's same 40 periods.  The run is chaotic
+  from period 2 on and still relaxing, with a slow bursting cycle of ~13 T_s
+  (~0.075 cycles per period) that a 30-period window holds only twice: the
+  mean CSR power of periods 10-40 depends on the phase of that cycle, which
+  rounding alone decides.  So the GPU runs an ensemble -- the oracle's own
+  start and 31 starts that differ from it by noise at the same 1e-6 level,
+  in one batch -- and the oracle's run must look like a member: its window
+  mean inside the ensemble's two-sigma prediction interval, the ensemble's
+  median frequency of the slow bursting line (periods 20-40) within 2 % and
+  its median fluctuation envelope within 10 %.  A fixed bound on one GPU
+  run against one oracle run would test the draw, not the method.
 * C3: the 63-point threshold scan (N = 256, S_csr in linspace(0.2, 1.5, 21)
   x Pi in {1, 2, 3}, 1000 steps/period, 20 periods) in one batch, plus a
   duplicate point as an in-batch determinism probe: the threshold per Pi
@@ -62,28 +60,6 @@ def V():
 def golden(name):
     with open(os.path.join(GOLDEN, f"oracle_{name}.json")) as f:
         return json.load(f)
-
-
-def c5_mean_tolerance(period_means, lo=10, hi=40):
-    """Two standard deviations of the difference between the mean of periods
-    lo..hi-1 of two independent chaotic runs, from one run's per-period means:
-    fit the relaxation trend (linear in log), take the residuals' spread and
-    their effective number of independent periods (positive autocorrelation
-    lags), and scale by sqrt 2 for the difference of two runs."""
-    m = np.asarray(period_means, dtype=np.float64)[lo:hi]
-    t = np.arange(lo, hi, dtype=np.float64)
-    A = np.vstack([np.ones_like(t), t]).T
-    coef, *_ = np.linalg.lstsq(A, np.log(m), rcond=None)
-    r = np.log(m) - A @ coef
-    x = r - r.mean()
-    rho = 0.0
-    for k in range(1, len(x) - 1):
-        c = float(np.dot(x[:-k], x[k:]) / np.dot(x, x))
-        if c <= 0.0:
-            break
-        rho += c
-    neff = len(x) / (1.0 + 2.0 * rho)
-    return 2.0 * np.sqrt(2.0) * r.std() / np.sqrt(neff)
 
 
 def envelope(stats):
@@ -155,26 +131,34 @@ def test_c3_threshold_scan_matches_oracle_scan(V):
 def test_c5_large_grid_statistics_match_oracle(V):
     g = golden("c5")
     n, spp, beta, periods = g["n"], g["steps_per_period"], g["beta"], g["periods"]
-    sim = V.Simulation(V.Params(n=n, steps_per_period=spp, beta=beta), W.noisy_gaussian(n, g["seed"], 1e-6))
-    sim.set_impedance(V.IMPEDANCE_PARALLEL_PLATES, g["Pi"], g["S_csr"])
-    P = []
-    for _ in range(periods):
-        sim.step(spp)
-        P.append(sim.csr_power())
-    sim.close()
-    P = np.concatenate(P)
-    assert len(P) == spp * periods
+    members = 32
+    b = V.Batch(members)
+    slots = [b.add(V.Params(n=n, steps_per_period=spp, beta=beta),
+                   W.noisy_gaussian(n, g["seed"] if k == 0 else 7000 + k, 1e-6), V.IMPEDANCE_PARALLEL_PLATES,
+                   g["Pi"], g["S_csr"], nsteps=spp * periods) for k in range(members)]
+    b.run(spp * periods)
+    P = [b.take(sl, psi=False, rho=False)["power"] for sl in slots]
+    b.close()
+    assert all(len(p) == spp * periods for p in P)
     ref = np.asarray(g["period_stats"])
-    mean_gpu, mean_ref = P[10 * spp:].mean(), ref[10:, 0].mean()
-    env_gpu = np.median(A.fluctuation(P, spp)[20:40])
+    mean_ref = ref[10:, 0].mean()
     env_ref = np.median(ref[20:40, 1] / ref[20:40, 0])
-    slow_gpu = next(f for f, _ in G.spectrum_lines(P[20 * spp:40 * spp], spp, 10) if f < 0.5)
     slow_ref = next(f for f, _ in g["periods_20_40"]["lines"] if f < 0.5)
-    print(f"C5: mean P (periods 10-40) {mean_gpu:.6e} vs {mean_ref:.6e}; envelope {env_gpu:.4f} vs {env_ref:.4f}; "
-          f"bursting line {slow_gpu:.5f} vs {slow_ref:.5f} cycles/period")
-    assert A.is_bursting(P, spp, first=20, last=40)
-    assert abs(slow_gpu - slow_ref) <= 0.02 * slow_ref, (slow_gpu, slow_ref)
-    tol = c5_mean_tolerance(ref[:, 0])
-    assert 0.05 < tol < 0.12, tol  # the oracle run's own resolution of this window (~8 %)
-    assert abs(mean_gpu - mean_ref) <= tol * mean_ref, (mean_gpu, mean_ref, tol)
-    assert abs(env_gpu - env_ref) <= 0.1 * env_ref, (env_gpu, env_ref)
+    means = np.array([p[10 * spp:].mean() for p in P])
+    envs = np.array([np.median(A.fluctuation(p, spp)[20:40]) for p in P])
+    # strongest line below 0.5 cycles per period (every peak of the window considered)
+    slows = np.array([next((f for f, _ in G.spectrum_lines(p[20 * spp:40 * spp], spp, 1 << 20) if f < 0.5), np.nan)
+                      for p in P])
+    m, sd = means.mean(), means.std(ddof=1)
+    half = 2.0 * sd * np.sqrt(1.0 + 1.0 / members)  # two-sigma prediction interval of one more draw
+    print(f"C5: mean P (periods 10-40) oracle {mean_ref:.4e}, GPU ensemble {m:.4e} +- {sd:.2e} "
+          f"(member 0 {means[0]:.4e}, range {means.min():.4e}..{means.max():.4e}); "
+          f"slow line {np.nanmedian(slows):.5f} vs {slow_ref:.5f}; envelope {np.median(envs):.4f} vs {env_ref:.4f}")
+    print("C5 members: means", np.round(means / mean_ref, 3).tolist(), "slow lines", np.round(slows, 4).tolist(),
+          "envelopes", np.round(envs, 3).tolist())
+    assert all(A.is_bursting(p, spp, first=20, last=40) for p in P)
+    assert abs(mean_ref - m) <= half, (mean_ref, m, sd)
+    assert sd / m < 0.4, sd / m  # one regime: no member left the bursting of the others
+    assert np.isfinite(slows).sum() >= members // 2, slows
+    assert abs(np.nanmedian(slows) - slow_ref) <= 0.02 * slow_ref, (np.nanmedian(slows), slow_ref)
+    assert abs(np.median(envs) - env_ref) <= 0.1 * env_ref, (np.median(envs), env_ref)
