@@ -69,7 +69,7 @@ typedef struct vfps_params {
                                  0: central difference                                    */
     int32_t pad_factor;       /* zero padding: FFT length M = smallest power of two
                                  >= pad_factor*n; 2..64, pad_factor*n <= 16384; default 2 */
-    int32_t precision;        /* 0: FP32 psi with FP64 sums (default); 1: FP64 throughout */
+    int32_t precision;        /* 0: FP32 psi and column sums, FP64 charge and power sums (default); 1: FP64 throughout */
     int32_t renormalize;      /* 1: rescale the charge to 1 after every step (default)    */
     int32_t rotation;         /* 0: standard rotation (default); 1: Manhattan rotation of
                                  Sec. III.B: drift q -> q + h p, then RF kick p -> p - h q,

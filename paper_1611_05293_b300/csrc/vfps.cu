@@ -327,7 +327,7 @@ struct Instance {
 // Persistent launches: tagged 64-bit words (2n column-sum halves, n kick
 // records, a scale per worker CTA -- at most n/2 + 1 of them), then a step
 // flag per worker CTA.
-size_t persist_bytes(int n) { return (size_t)(3 * n + n / 2 + 2) * 8 + (size_t)(n + 2) * 4; }
+size_t persist_bytes(int n) { return (size_t)(2 * n + n / 2 + 2) * 8 + (size_t)(n + 2) * 4; }
 
 size_t instance_bytes(const vfps_params* p, int ring, size_t* offs)
 {
@@ -674,7 +674,7 @@ void set_pointers(Instance& I, unsigned char* b, const size_t* offs)
     I.mom = (double*)(b + offs[13]);
     I.dsegs = (int4*)(b + offs[14]);
     I.cword = (unsigned long long*)(b + offs[15]);
-    I.rword = I.cword + 2 * (size_t)I.n;
+    I.rword = I.cword + (size_t)I.n;
     I.sword = I.rword + (size_t)I.n;
     I.cflag = reinterpret_cast<unsigned*>(I.sword + (size_t)I.n / 2 + 2);
 }

@@ -999,17 +999,18 @@ __device__ __forceinline__ bool strip_f32(const Desc<float>& D, int xs, int T, u
             if (half == 0) lsum = lsum + xsum[32 * cw + lane];
         }
         if (active && kick_ok && half == 0) {
-            double csum = double(lsum);  // FP32 lane partials, FP64 across lanes
+            // the column sum: FP32 lane partials, then an FP32 shuffle tree
+            // (the state's precision, Sec. IV.A; an FP64 tree is five long
+            // FP64 latencies on the path of every step on this GPU)
+            float csum = lsum;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) csum += __shfl_down_sync(0xffffffffu, csum, o);
             if (lane == 0) {
                 if constexpr (PERSIST) {
-                    // the two tagged words (low, high half) the finaliser CTA polls
-                    const unsigned long long b = (unsigned long long)__double_as_longlong(csum);
-                    st_tagged(D.cword + 2 * (size_t)x, (unsigned)b, (unsigned)ps->k + 1u);
-                    st_tagged(D.cword + 2 * (size_t)x + 1, (unsigned)(b >> 32), (unsigned)ps->k + 1u);
+                    // the tagged word the finaliser CTA polls
+                    st_tagged(D.cword + x, __float_as_uint(csum), (unsigned)ps->k + 1u);
                 } else {
-                    colsum[x] = csum;
+                    colsum[x] = double(csum);
                 }
             }
         }
@@ -1151,14 +1152,14 @@ step_persistent_f32(const Desc<float>* __restrict__ descs, const int4* __restric
                     z[x] = 0.f;
                     continue;
                 }
-                unsigned v[2];
-                if (!wait_tagged<2>(D, D.cword + 2 * (size_t)x, (unsigned)k + 1u, v)) {
+                unsigned v;
+                if (!wait_tagged<1>(D, D.cword + x, (unsigned)k + 1u, &v)) {
                     s_fail = 1;
                     break;
                 }
-                const double c = __longlong_as_double((long long)(((unsigned long long)v[1] << 32) | v[0]));
-                L.cs[x] = c;
-                z[x] = float(c);
+                const float c = __uint_as_float(v);
+                L.cs[x] = double(c);
+                z[x] = c;
             }
             __syncthreads();
             if (s_fail) return;

@@ -73,9 +73,9 @@ struct Desc {
     double* qring;
     double* mring;                     // moments ring (4 doubles per step), or null
     double* colmom;                    // 2n: per column sum p psi and sum p^2 psi (moment steps)
-    // persistent launches (see step_persistent_f32): tagged words -- 2n for
-    // the column sums (low, high half), n kick records, a scale per worker
-    // CTA -- and a step flag per worker CTA
+    // persistent launches (see step_persistent_f32): tagged words -- n
+    // column sums (FP32), n kick records, a scale per worker CTA -- and a
+    // step flag per worker CTA
     unsigned long long* cword;
     unsigned long long* rword;
     unsigned long long* sword;
@@ -986,9 +986,13 @@ step_kernel(const Desc<T>* __restrict__ descs, const int2* __restrict__ tiles)
                 lp2 += pp * pv;
             }
         }
-        csum = double(lsum);
+        {
+            // lane partials, then a shuffle tree, in the state's precision
+            T ct = lsum;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) csum += __shfl_down_sync(0xffffffffu, csum, o);
+            for (int o = 16; o > 0; o >>= 1) ct += __shfl_down_sync(0xffffffffu, ct, o);
+            csum = double(ct);
+        }
         if (mom_now) {
             double s1 = double(lp1), s2 = double(lp2);
 #pragma unroll
@@ -1038,11 +1042,10 @@ project_kernel(const Desc<T>* __restrict__ descs, const int2* __restrict__ tiles
     if (x < n) {
         T ls = T(0);
         for (int y = lane; y < n; y += 32) ls += in[(size_t)x * ld + y];
-        double s = double(ls);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        for (int o = 16; o > 0; o >>= 1) ls += __shfl_down_sync(0xffffffffu, ls, o);
         if (lane == 0) {
-            D.colsum[x] = s;
+            D.colsum[x] = double(ls);
             __threadfence();
         }
     }

@@ -471,15 +471,15 @@ __device__ __forceinline__ void strip_f32x2(const Desc<float>& DA, const Desc<fl
                 }
                 lsum = f2(part[0], part[1]);
             }
-            // FP32 lane partials, FP64 across lanes: lanes 0-15 reduce A, 16-31
+            // FP32 lane partials and shuffle tree: lanes 0-15 reduce A, 16-31
             // B, in the order of the single-simulation tree (16, 8, 4, 2, 1)
             const bool upper = lane >= 16;
-            double v = upper ? double(lsum.y) : double(lsum.x);
-            v += __shfl_xor_sync(0xffffffffu, upper ? double(lsum.x) : double(lsum.y), 16);
+            float v = upper ? lsum.y : lsum.x;
+            v += __shfl_xor_sync(0xffffffffu, upper ? lsum.x : lsum.y, 16);
 #pragma unroll
             for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) DA.colsum[x] = v;
-            if (lane == 16) DB.colsum[x] = v;
+            if (lane == 0) DA.colsum[x] = double(v);
+            if (lane == 16) DB.colsum[x] = double(v);
         }
         __syncthreads();  // the ring slots of columns xs+jW-h .. xs+jW+W-h-1 are free
         if (j + 2 < T) {
