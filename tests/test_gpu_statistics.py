@@ -81,6 +81,8 @@ def test_c2_bursting_statistics_match_oracle(V):
     assert A.is_bursting(P, spp, first=periods // 2), "C2 must be above threshold"
     assert abs(half.mean() - ref["mean"]) <= 0.02 * ref["mean"], (half.mean(), ref["mean"])
     f_gpu, f_ref = G.spectrum_lines(half, spp)[0][0], ref["lines"][0][0]
+    print(f"C2: mean P {half.mean():.6e} vs {ref['mean']:.6e} ({abs(half.mean() / ref['mean'] - 1):.2e}); "
+          f"strongest line {f_gpu:.5f} vs {f_ref:.5f} ({abs(f_gpu / f_ref - 1):.1e})")
     assert abs(f_gpu - f_ref) <= 0.02 * f_ref, (f_gpu, f_ref)
 
 
@@ -114,6 +116,7 @@ def test_c3_threshold_scan_matches_oracle_scan(V):
         gpu = [A.is_bursting(P[i], spp, first=10, last=20) for i in idx]
         ora = [A.envelope_bursting(envelope(pts[i]["period_stats"]), 10, 20) for i in idx]
         th_g, th_o = A.threshold(S, gpu), A.threshold(S, ora)
+        print(f"C3 Pi={Pi}: threshold {th_g} (oracle {th_o}), flags differing {sum(a != b_ for a, b_ in zip(gpu, ora))} of {len(S)}")
         assert th_g is not None and th_o is not None, (Pi, gpu, ora)
         assert abs(th_g - th_o) <= step + 1e-9, (Pi, th_g, th_o)
         assert abs(th_g - (0.5 + 0.12 * Pi)) <= 2 * step + 1e-9, (Pi, th_g)
